@@ -1,0 +1,206 @@
+"""Recursive two-means (2MN) ordering and the HSS cluster tree.
+
+TEST INFRASTRUCTURE ONLY.  Follows the paper's Section 4.2 (split the
+points into two groups, make each group contiguous, recurse on both
+groups while a group is larger than the leaf size) and Section 4.3
+("Recursive two-means": pick one point at random, pick a second one with
+probability growing with its distance from the first, then alternate
+nearest-representative assignment and centre updates until no point
+changes side).  Nodes are numbered in postorder, as in Figure 2.
+
+The paper fixes no arithmetic, so this oracle takes the following
+reading, chosen so that any correct implementation reaches the same
+permutation bit for bit:
+
+1. Coordinates are quantized once: q = round_half_even(x * 2^k) with the
+   largest k for which every squared distance between points (or centres)
+   inside the hull, summed over all n points, stays below 2^63.
+   Distances, sums and centres are then exact 64-bit integers.
+2. The centre of a group is floor((2 * sum q + cnt) / (2 * cnt)) per
+   coordinate (the mean rounded half up).
+3. Seeding of the node covering rows [b, b + m): Philox4x64-10 words
+   (w0, w1) at counter (b, m, 0, 0) (``rng.cluster_words``).  First
+   representative: row b + floor(w0 * m / 2^64).  Second: drawn with
+   probability proportional to the SQUARED distance to the first (the
+   k-means++ weight; the paper says "proportional to the distance",
+   squared is taken so the draw stays in exact integers): target =
+   floor(w1 * total / 2^64), pick the first row whose inclusive prefix sum
+   of squared distances exceeds target.  If all points coincide (total 0)
+   the node is split into halves.
+4. A point goes to group 0 iff its squared distance to centre 0 is <= its
+   squared distance to centre 1.
+5. Iterate: assign; stop if no label changed (the first assignment always
+   counts as a change); stop if a group is empty; recompute both centres;
+   stop after MAX_ITER centre updates.
+6. If a group is empty at the end, split at floor(m / 2) in the current
+   order (the NP rule of Section 4.3).
+7. Stable partition, group 0 first; children in that order; recurse while
+   m > leaf.
+"""
+from __future__ import annotations
+
+import math
+import sys
+
+import numpy as np
+
+from .rng import cluster_words, mulhi64
+
+MAX_ITER = 100
+
+
+def quant_exponent(X32: np.ndarray) -> int:
+    """k such that q = rint(x * 2^k) keeps every sum of squared distances < 2^63."""
+    X = np.asarray(X32, dtype=np.float32)
+    n, d = X.shape
+    L = (4 * d * n - 1).bit_length()          # ceil(log2(4 d n))
+    t = (63 - L) // 2
+    maxabs = float(np.max(np.abs(X))) if X.size else 0.0
+    if maxabs == 0.0:
+        return 0
+    e = math.frexp(maxabs)[1]                 # maxabs < 2^e
+    return t - e
+
+
+def quantize(X32: np.ndarray):
+    X = np.asarray(X32, dtype=np.float32)
+    if not np.all(np.isfinite(X)):
+        raise ValueError("non-finite coordinate")
+    k = quant_exponent(X)
+    q = np.rint(X.astype(np.float64) * math.ldexp(1.0, k)).astype(np.int64)
+    return q, k
+
+
+def _centre(qs: np.ndarray) -> np.ndarray:
+    cnt = qs.shape[0]
+    s = qs.sum(axis=0, dtype=np.int64)
+    return (2 * s + cnt) // (2 * cnt)
+
+
+def split_node(q: np.ndarray, seed: int, begin: int):
+    """Two-means labels (0/1, int8) of the m rows q (m x d) of one node.
+
+    Returns (labels, n_centre_updates, halved).
+    """
+    m = q.shape[0]
+    w0, w1 = cluster_words(seed, begin, m)
+    first = mulhi64(w0, m)
+    c0 = q[first].copy()
+    dist = ((q - c0) ** 2).sum(axis=1)
+    du = dist.astype(np.uint64)
+    total = int(du.sum(dtype=np.uint64))
+    halves = (np.arange(m) >= m // 2).astype(np.int8)
+    if total == 0:
+        return halves, 0, True
+    target = mulhi64(w1, total)
+    prefix = np.cumsum(du, dtype=np.uint64)
+    second = int(np.searchsorted(prefix, np.uint64(target), side="right"))
+    c1 = q[second].copy()
+
+    labels = None
+    it = 0
+    while True:
+        d0 = ((q - c0) ** 2).sum(axis=1)
+        d1 = ((q - c1) ** 2).sum(axis=1)
+        new = (d0 > d1).astype(np.int8)
+        changed = labels is None or bool(np.any(new != labels))
+        labels = new
+        if not changed:
+            break
+        cnt1 = int(labels.sum())
+        cnt0 = m - cnt1
+        if cnt0 == 0 or cnt1 == 0:
+            break
+        c0 = _centre(q[labels == 0])
+        c1 = _centre(q[labels == 1])
+        it += 1
+        if it == MAX_ITER:
+            break
+    cnt1 = int(labels.sum())
+    if cnt1 == 0 or cnt1 == m:
+        return halves, it, True
+    return labels, it, False
+
+
+class Tree:
+    """Binary cluster tree in postorder (Figure 2 numbering).
+
+    begin/end: row range in the permuted order; left/right: child ids or
+    -1 for a leaf; parent: -1 for the root; level: depth (root 0).
+    """
+
+    def __init__(self):
+        self.begin, self.end, self.left, self.right, self.parent, self.level = ([] for _ in range(6))
+
+    def add(self, b, e, l, r, lev):
+        i = len(self.begin)
+        self.begin.append(b); self.end.append(e); self.left.append(l)
+        self.right.append(r); self.parent.append(-1); self.level.append(lev)
+        if l >= 0:
+            self.parent[l] = i
+            self.parent[r] = i
+        return i
+
+    def arrays(self):
+        return {k: np.asarray(getattr(self, k), dtype=np.int32)
+                for k in ("begin", "end", "left", "right", "parent", "level")}
+
+    @property
+    def n_nodes(self):
+        return len(self.begin)
+
+
+def two_means_tree(X32: np.ndarray, leaf: int, seed: int):
+    """Recursive two-means ordering.
+
+    Returns (perm, tree, stats): perm[new] = old row index; tree in
+    postorder; stats holds the per-node centre-update counts.
+    """
+    if leaf < 1:
+        raise ValueError("leaf must be >= 1")
+    q, k = quantize(X32)
+    n = q.shape[0]
+    perm = np.arange(n, dtype=np.int64)
+    tree = Tree()
+    iters = {}
+
+    def build(b, e, lev):
+        m = e - b
+        if m <= leaf:
+            return tree.add(b, e, -1, -1, lev)
+        labels, it, halved = split_node(q[b:e], seed, b)
+        order = np.concatenate([np.nonzero(labels == 0)[0], np.nonzero(labels == 1)[0]])
+        q[b:e] = q[b:e][order]
+        perm[b:e] = perm[b:e][order]
+        c0 = int(np.count_nonzero(labels == 0))
+        l = build(b, b + c0, lev + 1)
+        r = build(b + c0, e, lev + 1)
+        nid = tree.add(b, e, l, r, lev)
+        iters[nid] = (it, halved)
+        return nid
+
+    old = sys.getrecursionlimit()
+    sys.setrecursionlimit(max(old, 4 * n // max(leaf, 1) + 1000))
+    try:
+        if n > 0:
+            build(0, n, 0)
+    finally:
+        sys.setrecursionlimit(old)
+    return perm.astype(np.int32), tree, {"centre_updates": iters, "quant_exp": k}
+
+
+def natural_tree(n: int, leaf: int):
+    """No preprocessing (NP, Section 4.3): natural order, halves (+-1)."""
+    tree = Tree()
+
+    def build(b, e, lev):
+        if e - b <= leaf:
+            return tree.add(b, e, -1, -1, lev)
+        mid = b + (e - b) // 2
+        l = build(b, mid, lev + 1)
+        r = build(mid, e, lev + 1)
+        return tree.add(b, e, l, r, lev)
+
+    if n > 0:
+        build(0, n, 0)
+    return np.arange(n, dtype=np.int32), tree

@@ -1,0 +1,119 @@
+"""Pins of the oracle's recursive two-means (Sections 4.2-4.3): a worked
+example, the Lloyd fixed point on tiny inputs checked by brute force, the
+tree invariants, and the integer bounds of the quantization."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cluster
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "two_means_1d.txt")
+
+
+def _tree_ok(perm, tree, n, leaf):
+    a = tree.arrays()
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    root = tree.n_nodes - 1
+    assert a["begin"][root] == 0 and a["end"][root] == n and a["parent"][root] == -1
+    for i in range(tree.n_nodes):
+        l, r = a["left"][i], a["right"][i]
+        if l < 0:
+            assert 0 < a["end"][i] - a["begin"][i] <= leaf or n == 0
+        else:
+            assert a["end"][i] - a["begin"][i] > leaf
+            assert l < i and r < i and l < r                     # postorder
+            assert a["begin"][l] == a["begin"][i] and a["end"][r] == a["end"][i]
+            assert a["end"][l] == a["begin"][r]
+            assert a["parent"][l] == i and a["parent"][r] == i
+            assert a["level"][l] == a["level"][i] + 1
+
+
+def test_golden_two_groups():
+    lines = {l.split(":")[0]: l.split(":")[1] for l in open(GOLD) if ":" in l and not l.startswith("#")}
+    pts = np.array(lines["points"].split(), float)[:, None].astype(np.float32)
+    leaf = int(lines["leaf"])
+    g1, g2 = [set(float(v) for v in s.split()) for s in lines["groups"].split("|")]
+    for seed in range(20):
+        perm, tree, _ = cluster.two_means_tree(pts, leaf, seed)
+        assert tree.n_nodes == 3
+        a = tree.arrays()
+        first = set(pts[perm[a["begin"][0]:a["end"][0]], 0].tolist())
+        second = set(pts[perm[a["begin"][1]:a["end"][1]], 0].tolist())
+        assert {frozenset(first), frozenset(second)} == {frozenset(g1), frozenset(g2)}
+
+
+def test_lloyd_fixed_point_brute_force():
+    """The final split of every non-halved node is a Lloyd fixed point: each
+    point is no farther from its own centre than from the other (tie to
+    group 0) and each centre is the rounded mean of its group."""
+    rng = np.random.default_rng(0)
+    for trial in range(40):
+        n = int(rng.integers(3, 13))
+        X = rng.normal(size=(n, 2)).astype(np.float32)
+        q, _ = cluster.quantize(X)
+        labels, it, halved = cluster.split_node(q, seed=trial, begin=0)
+        if halved or it == cluster.MAX_ITER:
+            continue
+        c = [None, None]
+        for g in (0, 1):
+            pts = q[labels == g]
+            c[g] = np.array([(2 * int(s) + len(pts)) // (2 * len(pts)) for s in pts.sum(0)])
+        for i in range(n):
+            d0 = sum((int(q[i, k]) - int(c[0][k])) ** 2 for k in range(2))
+            d1 = sum((int(q[i, k]) - int(c[1][k])) ** 2 for k in range(2))
+            assert labels[i] == (0 if d0 <= d1 else 1)
+
+
+def test_quantization_bounds():
+    """Every squared distance between points or centres of the hull, summed
+    over all n points, stays below 2^63; the exponent is the largest with
+    that property."""
+    for n, d in ((1000, 8), (65536, 8), (7, 1), (3000, 54)):
+        X = np.zeros((n, d), np.float32)
+        X[0, 0] = -3.75
+        X[-1, -1] = 2.5
+        k = cluster.quant_exponent(X)
+        qmax = abs(np.rint(-3.75 * 2.0 ** k))
+        assert n * d * (2 * qmax) ** 2 <= 2 ** 63
+        assert n * d * (4 * qmax) ** 2 > 2 ** 63 / 16     # one more bit would not fit
+
+
+def test_tree_invariants_mixture():
+    X, *_ = synth.mixture(3000, 8, 8, 0.7, 3)
+    X = X.astype(np.float32)
+    for leaf in (16, 64, 128):
+        perm, tree, st = cluster.two_means_tree(X, leaf, 7)
+        _tree_ok(perm, tree, 3000, leaf)
+
+
+def test_identical_points_are_halved():
+    X = np.ones((40, 3), np.float32)
+    perm, tree, st = cluster.two_means_tree(X, 8, 1)
+    _tree_ok(perm, tree, 40, 8)
+    assert np.array_equal(perm, np.arange(40))
+    a = tree.arrays()
+    assert sorted((a["end"] - a["begin"])[a["left"] < 0].tolist()) == [5] * 8
+
+
+def test_deterministic_and_seeded():
+    X, *_ = synth.mixture(2000, 5, 6, 0.7, 8)
+    X = X.astype(np.float32)
+    p1, _, _ = cluster.two_means_tree(X, 50, 3)
+    p2, _, _ = cluster.two_means_tree(X, 50, 3)
+    p3, _, _ = cluster.two_means_tree(X, 50, 4)
+    assert np.array_equal(p1, p2)
+    assert not np.array_equal(p1, p3)
+
+
+def test_natural_tree():
+    perm, tree = cluster.natural_tree(100, 16)
+    _tree_ok(perm, tree, 100, 16)
+
+
+def test_nonfinite_rejected():
+    X = np.zeros((10, 2), np.float32)
+    X[3, 1] = np.nan
+    with pytest.raises(ValueError):
+        cluster.two_means_tree(X, 4, 0)
