@@ -1,0 +1,236 @@
+/*
+ * krrhss: Gaussian-kernel ridge regression through a randomized HSS
+ * approximation of K + lambda I, on one GB300 GPU (sm_103a).
+ *
+ * Method (arXiv:1803.10274, "A Study of Clustering Techniques and
+ * Hierarchical Matrix Formats for Kernel Ridge Regression"):
+ *   Algorithm 1 (Section 2): order the training points (step 0), form the
+ *   Gaussian kernel K_ij = exp(-||x_i - x_j||^2 / (2 h^2)) (Eq. (1), step 1),
+ *   solve (K + lambda I) w = y (step 2), predict sign(w^T K'(i)) (steps 3-4).
+ *   Step 0 is recursive two-means (Sections 4.2-4.3).  Step 2 uses an HSS
+ *   approximation (Section 3.1) built by randomized sampling from products
+ *   with K and selected entries of K (Section 1.1, "partially matrix-free"),
+ *   then a ULV factorization and solve (Section 3.1).
+ *
+ * Conventions shared by every call:
+ *   - Matrices are row-major; "device" pointers are CUDA global memory of
+ *     the current device, "host" pointers are ordinary host memory.
+ *   - The caller owns every buffer it passes.  Opaque handles (krr_ctx,
+ *     krr_hss) are owned by the library and freed by their destroy call.
+ *   - All device work is enqueued on the context's stream.  A call returns
+ *     after enqueueing unless its description says it synchronizes.
+ *   - Return value: KRR_OK or a krr_status error code; krr_last_error()
+ *     gives a message for the calling thread.  No C++ exception crosses
+ *     this interface.
+ *   - Device-side failures (a wait that ran past its limit, a zero pivot)
+ *     are latched in the context and reported by the next synchronizing
+ *     call.
+ */
+#ifndef KRRHSS_H
+#define KRRHSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KRR_OK = 0,
+    KRR_ERR_INVALID_ARG = 1,     /* bad size, pointer, option or layout   */
+    KRR_ERR_NONFINITE_INPUT = 2, /* NaN or Inf in X                       */
+    KRR_ERR_OOM = 3,             /* device allocation failed              */
+    KRR_ERR_SINGULAR = 4,        /* zero pivot in a ULV block factorization */
+    KRR_ERR_RANK_BUDGET = 5,     /* ranks not revealed within r_max samples */
+    KRR_ERR_TIMEOUT = 6,         /* a device wait ran past its limit       */
+    KRR_ERR_CUDA = 7,            /* CUDA runtime/driver error              */
+    KRR_ERR_NOT_IMPLEMENTED = 8,
+    KRR_ERR_NO_CONVERGENCE = 9   /* refinement did not reach the tolerance */
+} krr_status;
+
+/* Arithmetic of the compression / factor / solve path. */
+typedef enum {
+    KRR_MIXED = 0, /* kernel products on tcgen05 tensor cores: FP16 operands
+                      (split into hi/lo parts for the distances), FP32
+                      accumulation; other steps in FP32                     */
+    KRR_FP64 = 1   /* every step in FP64 on the CUDA cores                  */
+} krr_precision;
+
+/* Optional device-memory allocator (e.g. a framework's caching allocator).
+ * alloc(bytes, user) returns device memory aligned to 256 bytes or NULL;
+ * free(ptr, user) releases it.  Both are called on the context's stream
+ * order.  Pass NULL to krr_create to use cudaMallocAsync/cudaFreeAsync. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} krr_allocator;
+
+typedef struct krr_ctx krr_ctx;
+typedef struct krr_hss krr_hss;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t
+ * (NULL = the legacy default stream).  The allocator struct is copied. */
+int krr_create(krr_ctx **ctx, const krr_allocator *alloc, void *stream);
+void krr_destroy(krr_ctx *ctx);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *krr_last_error(void);
+
+/* Wait for the context's stream and return (and clear) any latched device
+ * error.  Synchronizes. */
+int krr_sync(krr_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Feature standardization (Section 5.2: zero mean, unit standard
+ * deviation per column; test data use the training statistics; a column
+ * with zero spread is divided by 1).
+ *   X   device float, n x d, standardized in place (training set)
+ *   Xt  device float, m x d, in place with X's statistics (may be NULL, m=0)
+ *   mean, std  device double[d] outputs (may be NULL)
+ * Statistics are accumulated in FP64.
+ * ------------------------------------------------------------------- */
+int krr_standardize(krr_ctx *ctx, float *X, int64_t n, int32_t d, float *Xt,
+                    int64_t m, double *mean, double *std);
+
+/* ---------------------------------------------------------------------
+ * Recursive two-means ordering (Algorithm 1 step 0; Sections 4.2-4.3).
+ *   X      device float, n x d, read only
+ *   leaf   split while a node holds more than `leaf` rows (>= 1)
+ *   seed   seeds the counter-based draws of the first and second
+ *          representatives (Philox4x64-10, counter (begin, size, 0, 0))
+ *   perm   device int32[n] output: perm[new] = old row
+ *   tree   host int32 arrays of capacity max_nodes (>= 2*ceil(n/1)-1 is
+ *          always enough; 2*n is safe): node begin/end (row range in the
+ *          new order), left/right child (-1 at a leaf), parent (-1 at the
+ *          root), level (root 0).  Nodes are numbered in postorder
+ *          (Figure 2), so the root is node n_nodes-1.
+ *   n_nodes host output
+ * Arithmetic is exact (quantized 64-bit integer coordinates), so the
+ * result does not depend on thread scheduling.  Synchronizes.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int32_t *begin, *end, *left, *right, *parent, *level;
+} krr_tree_arrays;
+
+int krr_cluster(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
+                int32_t leaf, uint64_t seed, int32_t *perm,
+                int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes);
+
+/* ---------------------------------------------------------------------
+ * Fused kernel-times-block product (the HSS sampling step, Section 1.1
+ * and Section 3.1: the randomized construction needs A R for a block R of
+ * random vectors; Section 5.6 shows it dominates construction time):
+ *     S(i, :) = sum_j w_ij K(xa_i, xb_j) R(j, :)  + lambda * R(i, :)
+ * without storing K.  w_ij = 0 when leaf_a and leaf_b are both given and
+ * leaf_a[i] == leaf_b[j] (the product restricted to the off-diagonal leaf
+ * blocks, which is what the compression samples), else 1.  lambda must be
+ * 0 unless Xa and Xb are the same rows (ma == nb).
+ *   Xa device float ma x d;  Xb device float nb x d
+ *   R  device float nb x r (row stride ldr >= r)
+ *   S  device float ma x r output (row stride lds >= r), overwritten
+ *   leaf_a, leaf_b  device int32[ma], int32[nb] or both NULL
+ * KRR_MIXED: R is rounded to FP16; distances use an FP16 hi/lo split with
+ * FP32 accumulation on tcgen05 tensor cores, exp2 on the SFU, K rounded to
+ * FP16, K R accumulated in FP32 in tensor memory.  Requires d <= 40,
+ * 1 <= r and max |x|^2 / h^2 small enough for FP16 (else INVALID_ARG).
+ * ------------------------------------------------------------------- */
+int krr_sample(krr_ctx *ctx, const float *Xa, int64_t ma, const float *Xb,
+               int64_t nb, int32_t d, double h, double lambda, const float *R,
+               int32_t r, int64_t ldr, const int32_t *leaf_a,
+               const int32_t *leaf_b, float *S, int64_t lds);
+
+/* Same product in FP64 on the CUDA cores (the "plain" comparator):
+ * Xa, Xb device double; R, S device double.  No size limit on d. */
+int krr_sample_f64(krr_ctx *ctx, const double *Xa, int64_t ma,
+                   const double *Xb, int64_t nb, int32_t d, double h,
+                   double lambda, const double *R, int32_t r, int64_t ldr,
+                   const int32_t *leaf_a, const int32_t *leaf_b, double *S,
+                   int64_t lds);
+
+/* Columns [col0, col0 + r) of the method's random block, N(0,1) by
+ * Philox4x64-10 (key (seed, 0x52), counter (row, col/4, 0, 0)) and
+ * Box-Muller, as FP32 (KRR_MIXED: rounded to FP16 and widened back, so
+ * the tensor-core path uses it exactly) or FP64.  out: device, n x r with
+ * row stride ld.  col0 must be a multiple of 4. */
+int krr_random_block(krr_ctx *ctx, int64_t n, int32_t r, int32_t col0,
+                     uint64_t seed, int precision, void *out, int64_t ld);
+
+/* ---------------------------------------------------------------------
+ * HSS compression / factorization / solve / prediction.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    double h;          /* Gaussian width (Eq. (1))                          */
+    double lambda;     /* ridge parameter (> 0)                             */
+    double eps_c;      /* relative tolerance of the interpolative
+                          decompositions: a pivot is kept while
+                          |R_jj| > eps_c |R_11|                             */
+    double eps_abs;    /* absolute pivot floor (0 = none)                   */
+    int32_t leaf;      /* leaf size of the two-means tree                   */
+    int32_t r0;        /* initial number of random columns (multiple of 16) */
+    int32_t p;         /* oversampling: ranks must stay <= r - p            */
+    int32_t r_max;     /* cap on random columns                             */
+    uint64_t seed;     /* seeds clustering and the random block             */
+    int32_t precision; /* krr_precision                                     */
+    int32_t reserved;
+} krr_options;
+
+/* Fill opts with defaults: eps_c 0.03, eps_abs 0, leaf 128, r0 64, p 10,
+ * r_max 2048, seed 1, KRR_MIXED; h and lambda set to 1. */
+void krr_default_options(krr_options *opts);
+
+/* Cluster X (device float n x d, original order, already standardized if
+ * wanted) and build the HSS approximation of K + lambda I in that order.
+ * Synchronizes (the adaptive sampling reads ranks back per level). */
+int hss_compress(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
+                 const krr_options *opts, krr_hss **out);
+
+/* Change lambda without recompressing (Section 5.3: only the diagonal
+ * changes).  Invalidates the factorization; call hss_factor again. */
+int hss_update_lambda(krr_hss *H, double lambda);
+
+/* ULV factorization of the HSS matrix (Section 3.1), level by level. */
+int hss_factor(krr_hss *H);
+
+/* Solve (K + lambda I) alpha = y.
+ *   y      device double, n x nrhs (row stride ldy), original row order
+ *   alpha  device double, n x nrhs (row stride lda), original row order
+ *   tol    stop refinement when max_c ||(K+lambda I) a_c - y_c|| / ||y_c||
+ *          <= tol (the residual uses the fused product, exact up to the
+ *          precision mode); tol <= 0: one ULV solve, no refinement
+ *   max_refine  cap on refinement steps
+ *   resid  host double[1] out (may be NULL): final relative residual
+ *          (max over columns), or -1 when no refinement ran
+ * Each refinement step is one fused product with the current iterate and
+ * one ULV solve (the HSS factor as a preconditioner).  Synchronizes when
+ * tol > 0. */
+int hss_solve(krr_hss *H, const double *y, int32_t nrhs, int64_t ldy,
+              double *alpha, int64_t lda, double tol, int32_t max_refine,
+              double *resid);
+
+/* Decision values out = K(Xt, X) alpha (Algorithm 1 steps 3-4; the label
+ * is sign(out) with sign(0) = +1).  Xt device float m x d (standardized
+ * like X), alpha device double n x nrhs (original order), out device
+ * double m x nrhs. */
+int krr_predict(krr_hss *H, const float *Xt, int64_t m, const double *alpha,
+                int32_t nrhs, int64_t lda, double *out, int64_t ldo);
+
+typedef struct {
+    int64_t n;
+    int32_t n_nodes, n_levels, max_rank, samples, rounds, refine_steps;
+    int64_t memory_bytes; /* D, U and B generators (Section 4.2 metric) */
+    double t_cluster_ms, t_sample_ms, t_compress_ms, t_factor_ms, t_solve_ms;
+} krr_hss_stats;
+
+int hss_stats(const krr_hss *H, krr_hss_stats *st);
+
+/* Row order of the compressed matrix: perm[new] = old (device int32[n]). */
+const int32_t *hss_permutation(const krr_hss *H);
+
+void hss_destroy(krr_hss *H);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRRHSS_H */

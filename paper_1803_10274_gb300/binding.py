@@ -1,0 +1,195 @@
+"""Functions with the names of the C entry points, taking torch tensors.
+
+Argument marshalling only: shapes and dtypes are checked, pointers are
+passed to the C library, errors become KRRError.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import KRR_FP64, KRR_MIXED, KRRError, check, lib
+
+__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "krr_standardize", "krr_cluster", "krr_sample",
+           "krr_sample_f64", "krr_random_block", "HSS", "hss_compress", "default_options", "lib"]
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, name, dims=2):
+    if t is None:
+        return
+    if not (t.is_cuda and t.dtype == dtype and t.dim() == dims):
+        raise ValueError("%s must be a %d-D CUDA %s tensor" % (name, dims, dtype))
+    if dims == 2 and t.stride(1) != 1:
+        raise ValueError("%s must be row-major (unit column stride)" % name)
+
+
+class Context:
+    """A krr_ctx bound to torch's current stream and caching allocator."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True):
+        self.stream = stream or torch.cuda.current_stream()
+        self.device = torch.cuda.current_device()
+        self._keep = []
+        al = None
+        if torch_allocator:
+            dev, st = self.device, self.stream
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
+                except Exception:
+                    return None
+
+            def _free(p, user):
+                torch.cuda.caching_allocator_delete(p)
+
+            al = _lib.krr_allocator(_lib.krr_allocator._fields_[0][1](_alloc),
+                                    _lib.krr_allocator._fields_[1][1](_free), None)
+            self._keep.append(al)
+        h = ctypes.c_void_p()
+        check(lib().krr_create(ctypes.byref(h), ctypes.byref(al) if al else None,
+                               ctypes.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+
+    def sync(self):
+        check(lib().krr_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().krr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def krr_standardize(ctx, X, Xt=None, mean=None, std=None):
+    _need(X, torch.float32, "X")
+    _need(Xt, torch.float32, "Xt")
+    n, d = X.shape
+    m = 0 if Xt is None else Xt.shape[0]
+    check(lib().krr_standardize(ctx.h, _ptr(X), n, d, _ptr(Xt), m, _ptr(mean), _ptr(std)))
+
+
+def krr_cluster(ctx, X, leaf, seed):
+    """Returns (perm (device int32), tree dict of host int32 numpy arrays)."""
+    import numpy as np
+    _need(X, torch.float32, "X")
+    n, d = X.shape
+    perm = torch.empty(n, dtype=torch.int32, device=X.device)
+    cap = max(2 * n, 1)
+    arrs = {k: np.zeros(cap, np.int32) for k in ("begin", "end", "left", "right", "parent", "level")}
+    ta = _lib.krr_tree_arrays(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for k, v in arrs.items()})
+    nn = ctypes.c_int32()
+    check(lib().krr_cluster(ctx.h, _ptr(X), n, d, leaf, seed, _ptr(perm), cap, ta, ctypes.byref(nn)))
+    return perm, {k: v[:nn.value].copy() for k, v in arrs.items()}
+
+
+def krr_sample(ctx, Xa, Xb, h, lam, R, leaf_a=None, leaf_b=None, S=None):
+    _need(Xa, torch.float32, "Xa")
+    _need(Xb, torch.float32, "Xb")
+    _need(R, torch.float32, "R")
+    ma, d = Xa.shape
+    nb, r = R.shape
+    if S is None:
+        S = torch.empty(ma, r, dtype=torch.float32, device=Xa.device)
+    _need(S, torch.float32, "S")
+    check(lib().krr_sample(ctx.h, _ptr(Xa), ma, _ptr(Xb), nb, d, h, lam, _ptr(R), r, R.stride(0),
+                           _ptr(leaf_a), _ptr(leaf_b), _ptr(S), S.stride(0)))
+    return S
+
+
+def krr_sample_f64(ctx, Xa, Xb, h, lam, R, leaf_a=None, leaf_b=None, S=None):
+    _need(Xa, torch.float64, "Xa")
+    _need(Xb, torch.float64, "Xb")
+    _need(R, torch.float64, "R")
+    ma, d = Xa.shape
+    nb, r = R.shape
+    if S is None:
+        S = torch.empty(ma, r, dtype=torch.float64, device=Xa.device)
+    _need(S, torch.float64, "S")
+    check(lib().krr_sample_f64(ctx.h, _ptr(Xa), ma, _ptr(Xb), nb, d, h, lam, _ptr(R), r, R.stride(0),
+                               _ptr(leaf_a), _ptr(leaf_b), _ptr(S), S.stride(0)))
+    return S
+
+
+def krr_random_block(ctx, n, r, col0, seed, precision=KRR_MIXED, device=None):
+    dt = torch.float64 if precision == KRR_FP64 else torch.float32
+    out = torch.empty(n, r, dtype=dt, device=device or torch.device("cuda", ctx.device))
+    check(lib().krr_random_block(ctx.h, n, r, col0, seed, precision, _ptr(out), out.stride(0)))
+    return out
+
+
+def default_options(**kw):
+    o = _lib.krr_options()
+    lib().krr_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, "lam" if k == "lambda_" else k, v)
+    return o
+
+
+class HSS:
+    """Owner of a krr_hss handle."""
+
+    def __init__(self, ctx, handle, n):
+        self.ctx, self.h, self.n = ctx, handle, n
+
+    def factor(self):
+        check(lib().hss_factor(self.h))
+
+    def update_lambda(self, lam):
+        check(lib().hss_update_lambda(self.h, lam))
+
+    def solve(self, y, tol=0.0, max_refine=20):
+        """alpha (n x nrhs float64, original order) and the final residual."""
+        _need(y, torch.float64, "y")
+        alpha = torch.empty_like(y)
+        res = ctypes.c_double(-1.0)
+        check(lib().hss_solve(self.h, _ptr(y), y.shape[1], y.stride(0), _ptr(alpha), alpha.stride(0), tol,
+                              max_refine, ctypes.byref(res)))
+        return alpha, res.value
+
+    def predict(self, Xt, alpha):
+        _need(Xt, torch.float32, "Xt")
+        _need(alpha, torch.float64, "alpha")
+        out = torch.empty(Xt.shape[0], alpha.shape[1], dtype=torch.float64, device=Xt.device)
+        check(lib().krr_predict(self.h, _ptr(Xt), Xt.shape[0], _ptr(alpha), alpha.shape[1], alpha.stride(0),
+                                _ptr(out), out.stride(0)))
+        return out
+
+    def stats(self):
+        st = _lib.krr_hss_stats()
+        check(lib().hss_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def permutation(self):
+        p = lib().hss_permutation(self.h)
+        return p
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hss_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hss_compress(ctx, X, opts):
+    _need(X, torch.float32, "X")
+    n, d = X.shape
+    h = ctypes.c_void_p()
+    check(lib().hss_compress(ctx.h, _ptr(X), n, d, ctypes.byref(opts), ctypes.byref(h)))
+    return HSS(ctx, h, n)

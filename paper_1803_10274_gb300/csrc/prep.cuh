@@ -1,0 +1,44 @@
+// Declarations of the data-preparation kernels (prep.cu) and of the
+// launchers of the fused products (sample_tc.cu, sample_f64.cu).
+#pragma once
+#include "common.cuh"
+
+namespace krr {
+
+int standardize(Ctx *c, float *X, int64_t n, int d, float *Xt, int64_t m, double *mean, double *stdv);
+template <class Tin, class Tout>
+int gather_rows(Ctx *c, const Tin *src, int64_t lds, const int32_t *perm, int64_t n, int cols, Tout *dst,
+                int64_t ldd);
+template <class Tin, class Tout>
+int scatter_rows(Ctx *c, const Tin *src, int64_t lds, const int32_t *perm, int64_t n, int cols, Tout *dst,
+                 int64_t ldd);
+int widen(Ctx *c, const float *src, int64_t n, double *dst);
+int augment(Ctx *c, const float *X, int64_t rows, int d, double h, int role, __half *out, int kpad);
+int transpose_half(Ctx *c, const float *R, int64_t n, int r, int64_t ldr, __half *RT, int rpad, int64_t ldrt);
+template <class T>
+int add_lambda(Ctx *c, T *S, int64_t lds, const T *R, int64_t ldr, int64_t n, int r, double lambda, bool round16);
+int random_block(Ctx *c, int64_t n, int r, int col0, uint64_t seed, int precision, void *out, int64_t ld);
+
+// Augmented-operand geometry of the tensor-core product for feature
+// dimension d: 3d + 6 used FP16 elements, padded to 64-element chunks.
+inline int aug_used(int d) { return 3 * d + 6; }
+inline int aug_kmma(int d) { return int(cdiv(aug_used(d), 16)); }
+inline int aug_chunks(int d) { return int(cdiv(aug_used(d), 64)); }
+inline int aug_kpad(int d) { return 64 * aug_chunks(d); }
+constexpr int kMaxMixedDim = 40;
+
+int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
+                     const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
+                     const int32_t *leaf_b, float *S, int64_t lds);
+int launch_sample_f64(Ctx *c, const double *Xa, int64_t ma, const double *Xb, int64_t nb, int d, double h,
+                      const double *R, int r, int64_t ldr, const int32_t *leaf_a, const int32_t *leaf_b, double *S,
+                      int64_t lds);
+
+// Mixed-precision product on already-prepared operands: S = W o K R over
+// any number of columns (split into launches of <= 256 columns).  S is
+// zeroed here.  RT holds r_total rows (ldrt each).
+int sample_mixed_prepared(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int d,
+                          const __half *RT, int r_total, int64_t ldrt, const int32_t *leaf_a,
+                          const int32_t *leaf_b, float *S, int64_t lds);
+
+}  // namespace krr
