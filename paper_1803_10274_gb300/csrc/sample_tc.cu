@@ -40,7 +40,6 @@ constexpr int kBN = 128;             // K columns of a tile
 constexpr int kChunk = 64;           // FP16 elements per 128-byte swizzled row
 constexpr int kChunkBytes = 128 * 128;
 constexpr int kMaxStages = 6;
-constexpr int kDistCol0 = 256;       // tensor-memory columns of the two distance buffers
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
 
 struct Params {
@@ -52,6 +51,8 @@ struct Params {
     int kmma;     // K=16 MMA steps of the distance GEMM
     int nstage;
     int s_bufs;   // S accumulators in tensor memory (1 or 2)
+    int ndist;    // distance / K buffers in tensor memory (2 or 3)
+    int dist_col0;
     uint32_t off_a, off_stage, stage_bytes, off_bar;
     const int32_t *leaf_a, *leaf_b;
     float *S;
@@ -66,17 +67,117 @@ enum {
     BAR_AFULL = BAR_EMPTY + kMaxStages,
     BAR_AEMPTY = BAR_AFULL + 2,
     BAR_DFULL = BAR_AEMPTY + 2,
-    BAR_PFULL = BAR_DFULL + 2,
-    BAR_SFULL = BAR_PFULL + 2,
+    BAR_PFULL = BAR_DFULL + 3,
+    BAR_SFULL = BAR_PFULL + 3,
     BAR_SEMPTY = BAR_SFULL + 2,
     BAR_DRAIN = BAR_SEMPTY + 2,
     BAR_COUNT = BAR_DRAIN + 1
 };
 
-__device__ __forceinline__ bool first_in_seg(int64_t t, int64_t t0, int64_t nct) { return t == t0 || (t % nct) == 0; }
-__device__ __forceinline__ bool last_in_seg(int64_t t, int64_t t1, int64_t nct) {
-    return t == t1 - 1 || (t % nct) == nct - 1;
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
 }
+
+// K = 2^e for 32 exponents, rounded to FP16 and packed in pairs.
+__device__ __forceinline__ void exp_pack(const uint32_t (&v)[32], uint32_t (&pk)[16]) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        pk[c] = pack_h2(ptx::ex2_approx(__uint_as_float(v[2 * c])), ptx::ex2_approx(__uint_as_float(v[2 * c + 1])));
+}
+
+// Zero the FP16 halves whose bit is set in m (only tiles that cross a
+// leaf of the cluster tree).
+__device__ __forceinline__ void mask_pack(uint32_t (&pk)[16], uint32_t m) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        const uint32_t lo = (m >> (2 * c)) & 1u, hi = (m >> (2 * c + 1)) & 1u;
+        pk[c] &= (lo ? 0xFFFF0000u : 0xFFFFFFFFu) & (hi ? 0x0000FFFFu : 0xFFFFFFFFu);
+    }
+}
+
+// Bits of the columns whose leaf equals row i's leaf, for a tile whose
+// leaf ranges overlap (rows and columns are in the same cluster order).
+__device__ __forceinline__ void tile_mask(const Params &P, int rt, int ct, int g, int64_t i, uint32_t &mlo,
+                                       uint32_t &mhi) {
+    const int64_t ia = int64_t(rt) * kBM, ib = min(ia + kBM - 1, P.ma - 1);
+    const int64_t ja = int64_t(ct) * kBN, jb = min(ja + kBN - 1, P.nb - 1);
+    const int32_t lo = max(__ldg(P.leaf_a + ia), __ldg(P.leaf_b + ja));
+    const int32_t hi = min(__ldg(P.leaf_a + ib), __ldg(P.leaf_b + jb));
+    mlo = mhi = 0;
+    if (lo > hi) return;
+    const int32_t li = __ldg(P.leaf_a + min(i, P.ma - 1));
+    const int64_t j0 = int64_t(ct) * kBN + 64 * g;
+#pragma unroll 1
+    for (int c = 0; c < 32; ++c) {
+        if (j0 + c < P.nb && __ldg(P.leaf_b + j0 + c) == li) mlo |= 1u << c;
+        if (j0 + 32 + c < P.nb && __ldg(P.leaf_b + j0 + 32 + c) == li) mhi |= 1u << c;
+    }
+}
+
+// Add this warpgroup's half of the row-tile accumulator into S and hand
+// the tensor-memory buffer back to the MMA issuer.
+__device__ __forceinline__ void flush_s(const Params &P, uint64_t *bars, volatile int *abort_flag, uint32_t tmem,
+                                     uint32_t lane_off, int64_t seg, int g, int rh, int64_t i) {
+    using namespace ptx;
+    const int lane = threadIdx.x & 31;
+    const int sb = P.s_bufs == 2 ? int(seg & 1) : 0;
+    const uint32_t par = P.s_bufs == 2 ? uint32_t((seg >> 1) & 1) : uint32_t(seg & 1);
+    if (!warp_wait(&bars[BAR_SFULL + sb], par, abort_flag, kWaitBudget, P.status, 8)) return;
+    tc_fence_after();
+    for (int cc = 0; cc < rh; cc += 32) {
+        uint32_t sv[32];
+        tmem_ld32(tmem + lane_off + uint32_t(sb * P.r + g * rh + cc), sv);
+        tmem_wait_ld();
+        if (i < P.ma) {
+            float *dst = P.S + i * P.lds;
+            const int cbase = g * rh + cc;
+            for (int c = 0; c < 32; ++c)
+                if (cbase + c < P.r_valid) atomicAdd(dst + cbase + c, __uint_as_float(sv[c]));
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bars[BAR_SEMPTY + sb]);
+}
+
+// Position in a CTA's range of tile steps, advanced incrementally (no
+// integer division in the loops): tile (rt, ct), shared-memory stage and
+// distance-buffer rings with their phase bits, row-tile segment count.
+struct Cursor {
+    int loc, rt, ct, stage, db, seg;
+    uint32_t sphase, dphase;
+    bool first, last;
+    __device__ __forceinline__ void init(int64_t t0, int nct) {
+        loc = 0;
+        rt = int(t0 / nct);
+        ct = int(t0 % nct);
+        stage = db = 0;
+        sphase = dphase = 0;
+        seg = 0;
+    }
+    // flags of the current tile; `first` opens a new row-tile segment
+    __device__ __forceinline__ void flags(int nloc, int nct) {
+        first = (loc == 0) || (ct == 0);
+        last = (loc == nloc - 1) || (ct == nct - 1);
+    }
+    __device__ __forceinline__ void next(int nct, int NS, int ND) {
+        ++loc;
+        if (++ct == nct) {
+            ct = 0;
+            ++rt;
+        }
+        if (++stage == NS) {
+            stage = 0;
+            sphase ^= 1u;
+        }
+        if (++db == ND) {
+            db = 0;
+            dphase ^= 1u;
+        }
+    }
+};
 
 __global__ void __launch_bounds__(kThreads, 1)
     sample_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -89,12 +190,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int64_t nct = P.n_col_tiles;
-    const int64_t T = P.n_row_tiles * nct;
+    const int nct = int(P.n_col_tiles);
+    const int64_t T = P.n_row_tiles * P.n_col_tiles;
     const int64_t t0 = T * blockIdx.x / gridDim.x;
-    const int64_t t1 = T * (blockIdx.x + 1) / gridDim.x;
-    const int64_t nloc = t1 - t0;
-    const int NS = P.nstage;
+    const int nloc = int(T * (blockIdx.x + 1) / gridDim.x - t0);
+    const int NS = P.nstage, ND = P.ndist;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -104,10 +204,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars[BAR_AFULL + b], 1);
             mbar_init(&bars[BAR_AEMPTY + b], 1);
-            mbar_init(&bars[BAR_DFULL + b], 1);
-            mbar_init(&bars[BAR_PFULL + b], 8);
             mbar_init(&bars[BAR_SFULL + b], 1);
             mbar_init(&bars[BAR_SEMPTY + b], 8);
+        }
+        for (int b = 0; b < 3; ++b) {
+            mbar_init(&bars[BAR_DFULL + b], 1);
+            mbar_init(&bars[BAR_PFULL + b], 8);
         }
         mbar_init(&bars[BAR_DRAIN], 1);
         *abort_flag = 0;
@@ -130,195 +232,160 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0 && lane == 0 && nloc > 0) {
         // ------------------------------------------------ TMA producer
-        int stage = 0;
-        uint32_t ph = 0;
-        int64_t seg = -1;
-        int64_t issued = 0;
-        for (int64_t t = t0; t < t1; ++t) {
-            const int64_t rt = t / nct, ct = t % nct;
-            if (first_in_seg(t, t0, nct)) {
-                ++seg;
-                const int ab = int(seg & 1);
+        Cursor c;
+        c.init(t0, nct);
+        int issued = 0, a_issued = -1;
+        for (; c.loc < nloc; c.next(nct, NS, 1)) {
+            c.flags(nloc, nct);
+            if (c.first) {
+                const int seg = c.seg++;
+                const int ab = seg & 1;
                 if (!mbar_wait(&bars[BAR_AEMPTY + ab], uint32_t((seg >> 1) & 1) ^ 1u, abort_flag, kWaitBudget,
                                P.status, 1))
                     break;
                 mbar_expect_tx(&bars[BAR_AFULL + ab], a_bytes);
-                for (int c = 0; c < P.nchunk; ++c)
-                    tma_load_2d(smem + P.off_a + ab * a_bytes + c * kChunkBytes, &tmA, &bars[BAR_AFULL + ab],
-                                c * kChunk, int(rt * kBM));
+                for (int ch = 0; ch < P.nchunk; ++ch)
+                    tma_load_2d(smem + P.off_a + ab * a_bytes + ch * kChunkBytes, &tmA, &bars[BAR_AFULL + ab],
+                                ch * kChunk, c.rt * kBM);
+                a_issued = seg;
             }
-            if (!mbar_wait(&bars[BAR_EMPTY + stage], ph ^ 1u, abort_flag, kWaitBudget, P.status, 2)) break;
-            uint8_t *st = smem + P.off_stage + stage * P.stage_bytes;
-            mbar_expect_tx(&bars[BAR_FULL + stage], P.stage_bytes);
-            for (int c = 0; c < P.nchunk; ++c)
-                tma_load_2d(st + c * kChunkBytes, &tmB, &bars[BAR_FULL + stage], c * kChunk, int(ct * kBN));
-            tma_load_2d(st + a_bytes, &tmR, &bars[BAR_FULL + stage], int(ct * kBN), 0);
-            tma_load_2d(st + a_bytes + P.r * 128, &tmR, &bars[BAR_FULL + stage], int(ct * kBN + 64), 0);
+            if (!mbar_wait(&bars[BAR_EMPTY + c.stage], c.sphase ^ 1u, abort_flag, kWaitBudget, P.status, 2)) break;
+            uint8_t *st = smem + P.off_stage + c.stage * P.stage_bytes;
+            mbar_expect_tx(&bars[BAR_FULL + c.stage], P.stage_bytes);
+            for (int ch = 0; ch < P.nchunk; ++ch)
+                tma_load_2d(st + ch * kChunkBytes, &tmB, &bars[BAR_FULL + c.stage], ch * kChunk, c.ct * kBN);
+            tma_load_2d(st + a_bytes, &tmR, &bars[BAR_FULL + c.stage], c.ct * kBN, 0);
+            tma_load_2d(st + a_bytes + P.r * 128, &tmR, &bars[BAR_FULL + c.stage], c.ct * kBN + 64, 0);
             ++issued;
-            if (++stage == NS) {
-                stage = 0;
-                ph ^= 1u;
-            }
         }
         // Drain: wait (bounded) until every load issued has landed, so no
         // TMA write is in flight when the CTA exits.
-        for (int64_t k = 0; k < (issued < NS ? issued : NS); ++k) {
-            int64_t u = issued - 1 - k;  // use index of that fill
-            int s = int(u % NS);
-            uint32_t parity = uint32_t((u / NS) & 1);
-            if (!mbar_try_wait(&bars[BAR_FULL + s], parity)) {
-                const long long c0 = clock64();
-                while (!mbar_try_wait(&bars[BAR_FULL + s], parity) && clock64() - c0 < kWaitBudget) {
-                }
-            }
+        for (int k = 0; k < (issued < NS ? issued : NS); ++k) {
+            const int u = issued - 1 - k;
+            mbar_wait_bounded(&bars[BAR_FULL + (u % NS)], uint32_t((u / NS) & 1), kWaitBudget);
         }
+        if (a_issued >= 0) mbar_wait_bounded(&bars[BAR_AFULL + (a_issued & 1)], uint32_t((a_issued >> 1) & 1), kWaitBudget);
     } else if (warp == 1 && lane == 0 && nloc > 0) {
         // ------------------------------------------------ MMA issuer
+        // The distance GEMM of tile loc + ND - 1 is issued before waiting for
+        // the epilogue of tile loc, so the tensor core always has the next
+        // distances queued.  MMAs from this thread execute in issue order,
+        // so a distance buffer is rewritten only after the product that
+        // read its K values.
         const uint32_t idesc_d = idesc_f16_f32(kBM, kBN);
         const uint32_t idesc_p = idesc_f16_f32(kBM, P.r);
-        int64_t seg_next = -1;  // segment of the tile whose distance GEMM was issued last
-        int64_t seg_cur = -1;
+        Cursor cd, cp;  // distance-side and product-side positions
+        cd.init(t0, nct);
+        cp.init(t0, nct);
         bool ok = true;
-        auto stage_of = [&](int64_t loc) { return int(loc % NS); };
-        auto phase_of = [&](int64_t loc) { return uint32_t((loc / NS) & 1); };
-        auto issue_dist = [&](int64_t loc) -> bool {
-            const int64_t t = t0 + loc;
-            if (first_in_seg(t, t0, nct)) {
-                ++seg_next;
-                if (!mbar_wait(&bars[BAR_AFULL + (seg_next & 1)], uint32_t((seg_next >> 1) & 1), abort_flag,
+        auto issue_dist = [&]() -> bool {
+            cd.flags(nloc, nct);
+            if (cd.first) {
+                ++cd.seg;
+                if (!mbar_wait(&bars[BAR_AFULL + ((cd.seg - 1) & 1)], uint32_t(((cd.seg - 1) >> 1) & 1), abort_flag,
                                kWaitBudget, P.status, 3))
                     return false;
             }
-            const int s = stage_of(loc);
-            if (!mbar_wait(&bars[BAR_FULL + s], phase_of(loc), abort_flag, kWaitBudget, P.status, 4)) return false;
+            if (!mbar_wait(&bars[BAR_FULL + cd.stage], cd.sphase, abort_flag, kWaitBudget, P.status, 4)) return false;
             tc_fence_after();
-            const uint32_t a_base = smem_u32(smem + P.off_a + (seg_next & 1) * a_bytes);
-            const uint32_t b_base = smem_u32(smem + P.off_stage + s * P.stage_bytes);
-            const uint32_t d_tmem = tmem + kDistCol0 + uint32_t(loc & 1) * kBN;
+            const uint32_t a_base = smem_u32(smem + P.off_a + ((cd.seg - 1) & 1) * a_bytes);
+            const uint32_t b_base = smem_u32(smem + P.off_stage + cd.stage * P.stage_bytes);
+            const uint32_t d_tmem = tmem + uint32_t(P.dist_col0 + cd.db * kBN);
             for (int k = 0; k < P.kmma; ++k) {
                 const uint32_t off = (k >> 2) * kChunkBytes + (k & 3) * 32;
                 mma_ss(d_tmem, sdesc_k_sw128(a_base + off), sdesc_k_sw128(b_base + off), idesc_d, k > 0);
             }
-            tc_commit(&bars[BAR_DFULL + (loc & 1)]);
-            if (last_in_seg(t, t1, nct)) tc_commit(&bars[BAR_AEMPTY + (seg_next & 1)]);
+            tc_commit(&bars[BAR_DFULL + cd.db]);
+            if (cd.last) tc_commit(&bars[BAR_AEMPTY + ((cd.seg - 1) & 1)]);
+            cd.next(nct, NS, ND);
             return true;
         };
-        ok = issue_dist(0);
-        for (int64_t loc = 0; ok && loc < nloc; ++loc) {
-            const int64_t t = t0 + loc;
-            if (loc + 1 < nloc && !issue_dist(loc + 1)) break;
-            if (first_in_seg(t, t0, nct)) {
-                ++seg_cur;
-                const int sb = int(seg_cur % P.s_bufs);
-                if (!mbar_wait(&bars[BAR_SEMPTY + sb], uint32_t((seg_cur / P.s_bufs) & 1) ^ 1u, abort_flag,
+        for (int k = 0; ok && k < ND - 1 && k < nloc; ++k) ok = issue_dist();
+        for (; ok && cp.loc < nloc; cp.next(nct, NS, ND)) {
+            if (cd.loc < nloc && !issue_dist()) break;
+            cp.flags(nloc, nct);
+            if (cp.first) {
+                const int seg = cp.seg++;
+                const uint32_t par = P.s_bufs == 2 ? uint32_t((seg >> 1) & 1) : uint32_t(seg & 1);
+                if (!mbar_wait(&bars[BAR_SEMPTY + (P.s_bufs == 2 ? (seg & 1) : 0)], par ^ 1u, abort_flag,
                                kWaitBudget, P.status, 5))
                     break;
             }
-            const int sb = int(seg_cur % P.s_bufs);
-            const int b = int(loc & 1);
-            if (!mbar_wait(&bars[BAR_PFULL + b], uint32_t((loc >> 1) & 1), abort_flag, kWaitBudget, P.status, 6))
-                break;
+            const int sb = P.s_bufs == 2 ? ((cp.seg - 1) & 1) : 0;
+            if (!mbar_wait(&bars[BAR_PFULL + cp.db], cp.dphase, abort_flag, kWaitBudget, P.status, 6)) break;
             tc_fence_after();
-            const int s = stage_of(loc);
-            const uint32_t r_base = smem_u32(smem + P.off_stage + s * P.stage_bytes + a_bytes);
+            const uint32_t r_base = smem_u32(smem + P.off_stage + cp.stage * P.stage_bytes + a_bytes);
             const uint32_t s_tmem = tmem + uint32_t(sb * P.r);
-            const uint32_t p_tmem = tmem + kDistCol0 + uint32_t(b) * kBN;
-            const bool first = first_in_seg(t, t0, nct);
+            const uint32_t p_tmem = tmem + uint32_t(P.dist_col0 + cp.db * kBN);
+#pragma unroll
             for (int k = 0; k < 8; ++k) {
+                // K of warpgroup k/4 sits in its first 32 columns, 8 columns per 16 K
                 const uint32_t a_t = p_tmem + uint32_t((k >> 2) * 64 + (k & 3) * 8);
                 const uint32_t roff = uint32_t((k >> 2) * P.r * 128 + (k & 3) * 32);
-                mma_ts(s_tmem, a_t, sdesc_k_sw128(r_base + roff), idesc_p, (first && k == 0) ? 0u : 1u);
+                mma_ts(s_tmem, a_t, sdesc_k_sw128(r_base + roff), idesc_p, (cp.first && k == 0) ? 0u : 1u);
             }
-            tc_commit(&bars[BAR_EMPTY + s]);
-            if (last_in_seg(t, t1, nct)) tc_commit(&bars[BAR_SFULL + sb]);
+            tc_commit(&bars[BAR_EMPTY + cp.stage]);
+            if (cp.last) tc_commit(&bars[BAR_SFULL + sb]);
         }
         // Drain: every MMA issued has completed before tensor memory is freed.
         tc_commit(&bars[BAR_DRAIN]);
-        if (!mbar_try_wait(&bars[BAR_DRAIN], 0)) {
-            const long long c0 = clock64();
-            while (!mbar_try_wait(&bars[BAR_DRAIN], 0) && clock64() - c0 < kWaitBudget) {
-            }
-        }
+        mbar_wait_bounded(&bars[BAR_DRAIN], 0, kWaitBudget);
     } else if (warp >= 4 && nloc > 0) {
         // ------------------------------------------------ epilogue
-        const int q = warp & 3;          // lane quarter of tensor memory
-        const int g = (warp - 4) >> 2;   // 64-column half of the tile
+        // Warpgroup g owns columns [64 g, 64 g + 64) of every tile, read as
+        // two 32-column chunks; thread (warp quarter q, lane) owns row
+        // 32 q + lane.  The tensor-memory load of chunk 1 is in flight while
+        // chunk 0 is exponentiated, and the next tile's chunk 0 is requested
+        // right after this tile's K is handed over.  K for chunk k is written
+        // (FP16 pairs) into columns [64 g + 16 k, +16), already read.
+        const int q = warp & 3;
+        const int g = (warp - 4) >> 2;
         const uint32_t lane_off = uint32_t(32 * q) << 16;
-        int64_t seg = -1;
-        const bool masked = P.leaf_a != nullptr;
         const int rh = P.r >> 1;
-        for (int64_t loc = 0; loc < nloc; ++loc) {
-            const int64_t t = t0 + loc;
-            const int64_t rt = t / nct, ct = t % nct;
-            if (first_in_seg(t, t0, nct)) ++seg;
-            const int b = int(loc & 1);
-            if (!mbar_wait(&bars[BAR_DFULL + b], uint32_t((loc >> 1) & 1), abort_flag, kWaitBudget, P.status, 7))
-                break;
+        Cursor c;
+        c.init(t0, nct);
+        uint32_t va[32], vb[32];
+        bool ok = warp_wait(&bars[BAR_DFULL + 0], 0u, abort_flag, kWaitBudget, P.status, 7);
+        if (ok) {
             tc_fence_after();
-            const uint32_t base = tmem + lane_off + kDistCol0 + uint32_t(b) * kBN + uint32_t(64 * g);
-            uint32_t v0[32], v1[32];
-            tmem_ld32(base, v0);
-            tmem_ld32(base + 32, v1);
-            tmem_wait_ld();
-            const int64_t i = rt * kBM + 32 * q + lane;
-            bool tile_masked = false;
-            int32_t li = 0;
-            const int64_t j0 = ct * kBN + 64 * g;
-            if (masked) {
-                const int64_t ia = rt * kBM, ib = min(rt * kBM + kBM - 1, P.ma - 1);
-                const int64_t ja = ct * kBN, jb = min(ct * kBN + kBN - 1, P.nb - 1);
-                const int32_t lo = max(__ldg(P.leaf_a + ia), __ldg(P.leaf_b + ja));
-                const int32_t hi = min(__ldg(P.leaf_a + ib), __ldg(P.leaf_b + jb));
-                tile_masked = lo <= hi;
-                li = __ldg(P.leaf_a + min(i, P.ma - 1));
-            }
-            uint32_t pk[32];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                float e0 = ex2_approx(__uint_as_float(v0[2 * c]));
-                float e1 = ex2_approx(__uint_as_float(v0[2 * c + 1]));
-                float f0 = ex2_approx(__uint_as_float(v1[2 * c]));
-                float f1 = ex2_approx(__uint_as_float(v1[2 * c + 1]));
-                if (tile_masked) {
-                    const int64_t ja = j0 + 2 * c, jb2 = j0 + 32 + 2 * c;
-                    if (ja < P.nb && __ldg(P.leaf_b + ja) == li) e0 = 0.f;
-                    if (ja + 1 < P.nb && __ldg(P.leaf_b + ja + 1) == li) e1 = 0.f;
-                    if (jb2 < P.nb && __ldg(P.leaf_b + jb2) == li) f0 = 0.f;
-                    if (jb2 + 1 < P.nb && __ldg(P.leaf_b + jb2 + 1) == li) f1 = 0.f;
-                }
-                __half2 h0 = __floats2half2_rn(e0, e1);
-                __half2 h1 = __floats2half2_rn(f0, f1);
-                pk[c] = *reinterpret_cast<uint32_t *>(&h0);
-                pk[16 + c] = *reinterpret_cast<uint32_t *>(&h1);
-            }
-            tmem_st32(base, pk);
+            tmem_ld32(tmem + lane_off + uint32_t(P.dist_col0 + 64 * g), va);
+        }
+        for (; ok && c.loc < nloc; c.next(nct, 1, ND)) {
+            c.flags(nloc, nct);
+            if (c.first) ++c.seg;
+            const uint32_t base = tmem + lane_off + uint32_t(P.dist_col0 + c.db * kBN + 64 * g);
+            const int64_t i = int64_t(c.rt) * kBM + 32 * q + lane;
+            uint32_t mlo = 0, mhi = 0;
+            if (P.leaf_a != nullptr) tile_mask(P, c.rt, c.ct, g, i, mlo, mhi);
+            tmem_wait_ld_regs(va);                 // chunk 0 of this tile
+            tmem_ld32(base + 32, vb);              // chunk 1 in flight
+            uint32_t pk[16];
+            exp_pack(va, pk);
+            if (mlo) mask_pack(pk, mlo);
+            tmem_st16(base, pk);
+            tmem_wait_ld_regs(vb);                 // chunk 1 of this tile
+            exp_pack(vb, pk);
+            if (mhi) mask_pack(pk, mhi);
+            tmem_st16(base + 16, pk);
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bars[BAR_PFULL + b]);
-            if (last_in_seg(t, t1, nct)) {
-                const int sb = int(seg % P.s_bufs);
-                if (!mbar_wait(&bars[BAR_SFULL + sb], uint32_t((seg / P.s_bufs) & 1), abort_flag, kWaitBudget,
-                               P.status, 8))
-                    break;
-                tc_fence_after();
-                for (int cc = 0; cc < rh; cc += 32) {
-                    uint32_t sv[32];
-                    tmem_ld32(tmem + lane_off + uint32_t(sb * P.r + g * rh + cc), sv);
-                    tmem_wait_ld();
-                    if (i < P.ma) {
-                        float *dst = P.S + i * P.lds;
-                        const int cbase = g * rh + cc;
-#pragma unroll
-                        for (int c = 0; c < 32; ++c)
-                            if (cbase + c < P.r_valid) atomicAdd(dst + cbase + c, __uint_as_float(sv[c]));
-                    }
+            if (lane == 0) mbar_arrive(&bars[BAR_PFULL + c.db]);
+            // K of this tile is handed over before waiting for the next
+            // tile's distances, so the MMA issuer never waits on that wait.
+            if (c.loc + 1 < nloc) {
+                const int nd = c.db + 1 == ND ? 0 : c.db + 1;
+                const uint32_t np = c.db + 1 == ND ? (c.dphase ^ 1u) : c.dphase;
+                if (!warp_wait(&bars[BAR_DFULL + nd], np, abort_flag, kWaitBudget, P.status, 7))
+                    ok = false;
+                else {
+                    tc_fence_after();
+                    tmem_ld32(tmem + lane_off + uint32_t(P.dist_col0 + nd * kBN + 64 * g), va);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bars[BAR_SEMPTY + sb]);
             }
+            if (c.last) flush_s(P, bars, abort_flag, tmem, lane_off, c.seg - 1, g, rh, i);
         }
+        tmem_wait_ld();
     }
 
     tc_fence_before();
@@ -393,7 +460,13 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     P.r_valid = r_valid;
     P.nchunk = nchunk;
     P.kmma = kmma;
-    P.s_bufs = (2 * rpad <= tc::kDistCol0) ? 2 : 1;
+    // Tensor memory (512 columns): S accumulators first, then 128-column
+    // distance / K buffers.
+    P.s_bufs = (2 * rpad <= 128) ? 2 : 1;
+    P.dist_col0 = P.s_bufs * rpad;
+    if (P.dist_col0 < 128) P.dist_col0 = 128;
+    P.ndist = (512 - P.dist_col0) / 128;
+    if (P.ndist > 3) P.ndist = 3;
     const uint32_t a_bytes = nchunk * tc::kChunkBytes;
     P.off_a = 0;
     P.off_stage = 2 * a_bytes;

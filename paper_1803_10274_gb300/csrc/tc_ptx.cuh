@@ -41,21 +41,54 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking probe of a phase (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase with the given parity to complete, at most `budget`
-// SM clock cycles.  On expiry the CTA-wide abort flag is raised and the
-// device status latches KRR_ERR_TIMEOUT; every later wait returns at once.
+// SM clock cycles.  The wait spins on test_wait (a suspended try_wait
+// wakes up too late for a pipeline that hands off every microsecond) and
+// stays inline so no call saves the caller's live registers.  On expiry
+// the CTA-wide abort flag is raised and the device status latches
+// KRR_ERR_TIMEOUT; every later wait returns at once.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           long long budget, DevStatus *st, int where) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (true) {
-        if (*abort_flag) return false;
-        if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > budget) {
-            *abort_flag = 1;
-            dev_fail(st, KRR_ERR_TIMEOUT, where);
-            return false;
+    uint32_t k = 0;
+    while (!mbar_test_wait(bar, parity)) {
+        if ((++k & 255u) == 0u) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > budget) {
+                *abort_flag = 1;
+                dev_fail(st, KRR_ERR_TIMEOUT, where);
+                return false;
+            }
         }
+    }
+    return true;
+}
+// mbar_wait for a whole warp: every lane gets the same verdict, so the
+// warp's control flow stays converged even if a wait times out.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          long long budget, DevStatus *st, int where) {
+    const bool ok = mbar_wait(bar, parity, abort_flag, budget, st, where);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Bounded wait without a status report (drain paths at kernel exit).
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long budget) {
+    const long long t0 = clock64();
+    while (!mbar_test_wait(bar, parity) && clock64() - t0 < budget) {
     }
 }
 
@@ -144,6 +177,25 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
         : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+#define KRR_RW32(v)                                                                                     \
+    "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),     \
+        "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),        \
+        "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]),      \
+        "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]),      \
+        "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+// Wait for outstanding tensor-memory loads; the registers of v are tied to
+// the wait so the compiler cannot move their uses above it.
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : KRR_RW32(v)::"memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor for a K-major operand stored as rows of
