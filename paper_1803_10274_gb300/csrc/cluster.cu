@@ -1,0 +1,530 @@
+// Recursive two-means ordering (paper Sections 4.2-4.3, Algorithm 1 step 0)
+// on the GPU, level by level: every node of a tree level is split at once.
+//
+// Arithmetic is exact so that any schedule reaches the same permutation:
+// coordinates are quantized once to 64-bit integers q = rint(x 2^k) with k
+// the largest exponent for which every squared distance inside the data
+// hull, summed over all n points, stays below 2^63; distances, sums and
+// centres are integers and sums are accumulated with integer atomics
+// (associative, so order-free).
+//
+// Per node covering rows [b, b + m) (m > leaf):
+//   * seeds: Philox4x64-10 words (w0, w1) at counter (b, m, 0, 0), key
+//     (seed, 0x43).  First representative: row b + floor(w0 m / 2^64).
+//     Second: drawn with probability proportional to the squared distance
+//     to the first (first row whose inclusive prefix sum of squared
+//     distances exceeds floor(w1 total / 2^64)); all-identical points are
+//     split in halves.
+//   * Lloyd: a point joins group 0 iff d0 <= d1; stop when no label
+//     changed (the first assignment counts as a change), when a group is
+//     empty, or after 100 centre updates; centre = floor((2 sum + cnt) /
+//     (2 cnt)) per coordinate.  An empty group at the end means halves.
+//   * stable partition, group 0 first; children recurse while size > leaf.
+// Nodes are numbered in postorder (Figure 2) on the host at the end.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace krr {
+namespace {
+
+constexpr int kMaxIter = 100;
+constexpr int kMaxD = 64;
+constexpr int kTB = 256;
+
+__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {  // b > 0
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// max |x| (as float bits) and a non-finite flag
+__global__ void absmax_kernel(const float *X, int64_t cnt, unsigned int *maxbits, int *nonfinite) {
+    unsigned int m = 0;
+    int bad = 0;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < cnt; k += int64_t(gridDim.x) * blockDim.x) {
+        const float v = X[k];
+        if (!isfinite(v)) bad = 1;
+        m = max(m, __float_as_uint(fabsf(v)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(maxbits, m);
+        if (bad) atomicOr(nonfinite, 1);
+    }
+}
+
+__global__ void quantize_kernel(const float *X, int64_t cnt, double scale, int64_t *q) {
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k < cnt) q[k] = __double2ll_rn(double(X[k]) * scale);
+}
+
+struct NodeState {
+    int64_t c0[kMaxD], c1[kMaxD];
+    int64_t sum0[kMaxD], sum1[kMaxD];
+    unsigned long long cnt1;
+    int it, done, changed, halved, first;
+};
+
+// One block per node: seeds and initial state.
+__global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const int64_t *nsize, NodeState *ns,
+                            uint64_t seed) {
+    const int v = blockIdx.x;
+    const int64_t b = nbeg[v], m = nsize[v];
+    NodeState &S = ns[v];
+    __shared__ unsigned long long warp_tot[kTB / 32];
+    __shared__ unsigned long long s_total;
+    __shared__ int64_t s_second;
+    const U64x4 w = philox4x64_10(uint64_t(b), uint64_t(m), 0, 0, seed, kStreamCluster);
+    const int64_t first = b + int64_t(__umul64hi(w.v[0], uint64_t(m)));
+    const int64_t *c0 = q + first * d;
+    auto dist0 = [&](int64_t i) -> unsigned long long {
+        int64_t s = 0;
+        for (int k = 0; k < d; ++k) {
+            const int64_t t = q[i * d + k] - c0[k];
+            s += t * t;
+        }
+        return (unsigned long long)s;
+    };
+    // pass 1: total of squared distances
+    unsigned long long part = 0;
+    for (int64_t i = b + threadIdx.x; i < b + m; i += blockDim.x) part += dist0(i);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int k = 0; k < kTB / 32; ++k) t += warp_tot[k];
+        s_total = t;
+        s_second = -1;
+    }
+    __syncthreads();
+    const unsigned long long total = s_total;
+    if (total == 0) {
+        if (threadIdx.x == 0) {
+            S.done = 1;
+            S.halved = 1;
+            S.it = 0;
+            S.first = 0;
+        }
+        return;
+    }
+    const unsigned long long target = __umul64hi(w.v[1], total);
+    // pass 2: the first row whose inclusive prefix sum exceeds target
+    unsigned long long carry = 0;
+    for (int64_t base = b; base < b + m; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const unsigned long long di = i < b + m ? dist0(i) : 0ull;
+        // inclusive block scan
+        unsigned long long x = di;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+        __syncthreads();
+        unsigned long long wpre = 0;
+        for (int k = 0; k < (threadIdx.x >> 5); ++k) wpre += warp_tot[k];
+        const unsigned long long incl = carry + wpre + x;
+        if (i < b + m && incl > target && incl - di <= target) s_second = i;
+        unsigned long long btot = 0;
+        for (int k = 0; k < kTB / 32; ++k) btot += warp_tot[k];
+        carry += btot;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int64_t sec = s_second;
+        for (int k = 0; k < d; ++k) {
+            S.c0[k] = c0[k];
+            S.c1[k] = q[sec * d + k];
+            S.sum0[k] = S.sum1[k] = 0;
+        }
+        S.cnt1 = 0;
+        S.it = 0;
+        S.done = 0;
+        S.changed = 0;
+        S.halved = 0;
+        S.first = 1;
+    }
+}
+
+// Assign each point of a still-running node to its nearer centre and
+// accumulate the new groups' sums and counts.
+__global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t *node_of, NodeState *ns,
+                              int8_t *label) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    __shared__ int s_uniform;
+    __shared__ int32_t s_node;
+    const int32_t v = i < n ? node_of[i] : -1;
+    if (threadIdx.x == 0) {
+        const int64_t last = min(int64_t(blockIdx.x) * blockDim.x + blockDim.x - 1, n - 1);
+        s_node = v;
+        s_uniform = (v >= 0 && node_of[last] == v) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool uniform = s_uniform != 0;
+    bool active = v >= 0 && !ns[v].done;
+    int lab = 0;
+    if (active) {
+        const NodeState &S = ns[v];
+        int64_t d0 = 0, d1 = 0;
+        for (int k = 0; k < d; ++k) {
+            const int64_t x = q[i * d + k];
+            const int64_t a = x - S.c0[k], bb = x - S.c1[k];
+            d0 += a * a;
+            d1 += bb * bb;
+        }
+        lab = d0 > d1 ? 1 : 0;
+        if (S.first || label[i] != lab) ns[v].changed = 1;
+        label[i] = int8_t(lab);
+    }
+    if (uniform) {
+        // all points of this block belong to one node: reduce, then one atomic per value
+        if (ns[s_node].done) return;
+        __shared__ long long red[kTB / 32];
+        for (int k = -1; k < 2 * d; ++k) {
+            long long val;
+            if (k < 0)
+                val = lab;
+            else if (k < d)
+                val = (active && lab == 0) ? q[i * d + k] : 0;
+            else
+                val = (active && lab == 1) ? q[i * d + (k - d)] : 0;
+            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                long long t = 0;
+                for (int w = 0; w < kTB / 32; ++w) t += red[w];
+                NodeState &S = ns[s_node];
+                if (k < 0)
+                    atomicAdd(&S.cnt1, (unsigned long long)t);
+                else if (k < d)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&S.sum0[k]), (unsigned long long)t);
+                else
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&S.sum1[k - d]), (unsigned long long)t);
+            }
+            __syncthreads();
+        }
+    } else if (active) {
+        NodeState &S = ns[v];
+        if (lab) atomicAdd(&S.cnt1, 1ull);
+        int64_t *sum = lab ? S.sum1 : S.sum0;
+        for (int k = 0; k < d; ++k)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&sum[k]), (unsigned long long)q[i * d + k]);
+    }
+}
+
+// One thread per node: stop test, centre update, accumulator reset.
+__global__ void update_kernel(int nn, int d, const int64_t *nsize, NodeState *ns, int *n_running) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    NodeState &S = ns[v];
+    if (S.done) return;
+    const int64_t m = nsize[v];
+    const int64_t c1 = int64_t(S.cnt1), c0 = m - c1;
+    bool stop = false;
+    if (!S.changed) {
+        stop = true;
+    } else if (c0 == 0 || c1 == 0) {
+        stop = true;
+    } else {
+        for (int k = 0; k < d; ++k) {
+            S.c0[k] = floor_div(2 * S.sum0[k] + c0, 2 * c0);
+            S.c1[k] = floor_div(2 * S.sum1[k] + c1, 2 * c1);
+        }
+        S.it += 1;
+        if (S.it == kMaxIter) stop = true;
+    }
+    if (stop) {
+        S.done = 1;
+        if (c0 == 0 || c1 == 0) S.halved = 1;
+    } else {
+        S.cnt1 = 0;
+        for (int k = 0; k < d; ++k) S.sum0[k] = S.sum1[k] = 0;
+        S.changed = 0;
+        S.first = 0;
+        atomicAdd(n_running, 1);
+    }
+}
+
+// Final labels (halves where required) and the per-point "goes left" flag.
+__global__ void finalize_labels_kernel(int64_t n, const int32_t *node_of, const int64_t *nbeg, const int64_t *nsize,
+                                       const NodeState *ns, int8_t *label, int32_t *zero_flag) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    if (v < 0) {
+        zero_flag[i] = 0;
+        return;
+    }
+    int lab = label[i];
+    if (ns[v].halved) {
+        lab = (i - nbeg[v]) >= nsize[v] / 2 ? 1 : 0;
+        label[i] = int8_t(lab);
+    }
+    zero_flag[i] = lab == 0 ? 1 : 0;
+}
+
+// Exclusive prefix sum of int32 flags (three-phase: block sums, scan of
+// block sums in one block, add back).
+__global__ void scan_blocks_kernel(const int32_t *in, int64_t n, int64_t *out, int64_t *bsum) {
+    __shared__ int64_t wsum[kTB / 32];
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t x = i < n ? in[i] : 0;
+    const int64_t own = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int64_t pre = 0;
+    for (int w = 0; w < (threadIdx.x >> 5); ++w) pre += wsum[w];
+    if (i < n) out[i] = pre + x - own;
+    if (threadIdx.x == blockDim.x - 1) bsum[blockIdx.x] = pre + x;
+}
+__global__ void scan_sums_kernel(int64_t *bsum, int64_t nb) {
+    // single block, sequential chunks
+    __shared__ int64_t carry;
+    __shared__ int64_t wsum[kTB / 32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int64_t x = i < nb ? bsum[i] : 0;
+        const int64_t own = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = x;
+        __syncthreads();
+        int64_t pre = 0;
+        for (int w = 0; w < (threadIdx.x >> 5); ++w) pre += wsum[w];
+        int64_t tot = 0;
+        for (int w = 0; w < kTB / 32; ++w) tot += wsum[w];
+        if (i < nb) bsum[i] = carry + pre + x - own;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+__global__ void scan_add_kernel(int64_t *out, int64_t n, const int64_t *bsum, int64_t *total_out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += bsum[blockIdx.x];
+    if (i == n - 1 && total_out) *total_out = out[i];
+}
+
+// Stable partition of every active node; inactive rows copy through.
+__global__ void partition_kernel(int64_t n, int d, const int32_t *node_of, const int64_t *nbeg, const int64_t *nsize,
+                                 const int8_t *label, const int64_t *zscan, const int32_t *zflag, const int64_t *q,
+                                 const int32_t *perm, int64_t *q2, int32_t *perm2, int64_t *cnt0_out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    int64_t dst = i;
+    if (v >= 0) {
+        const int64_t b = nbeg[v];
+        const int64_t zb = zscan[b];
+        const int64_t last = b + nsize[v] - 1;
+        const int64_t c0 = zscan[last] + zflag[last] - zb;
+        const int64_t zi = zscan[i] - zb;
+        dst = label[i] == 0 ? b + zi : b + c0 + (i - b - zi);
+        if (i == b) cnt0_out[v] = c0;
+    }
+    for (int k = 0; k < d; ++k) q2[dst * d + k] = q[i * d + k];
+    perm2[dst] = perm[i];
+}
+
+__global__ void mark_nodes_kernel(int nn, const int64_t *nbeg, const int64_t *nsize, int32_t *node_of) {
+    // one block per node, threads stride its rows
+    const int v = blockIdx.x;
+    if (v >= nn) return;
+    for (int64_t i = nbeg[v] + threadIdx.x; i < nbeg[v] + nsize[v]; i += blockDim.x) node_of[i] = v;
+}
+
+}  // namespace
+
+int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, int32_t *perm_out,
+            std::vector<int32_t> &tb, std::vector<int32_t> &te, std::vector<int32_t> &tl, std::vector<int32_t> &tr,
+            std::vector<int32_t> &tp, std::vector<int32_t> &tv) {
+    tb.clear(); te.clear(); tl.clear(); tr.clear(); tp.clear(); tv.clear();
+    if (n == 0) return KRR_OK;
+    if (d > kMaxD) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_cluster: d > 64");
+    cudaStream_t st = c->stream;
+    // --- quantization
+    DBuf<unsigned int> mx(c, 1);
+    DBuf<int> bad(c, 1);
+    if (!mx.get() || !bad.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+    KRR_CUDA(cudaMemsetAsync(mx.get(), 0, 4, st));
+    KRR_CUDA(cudaMemsetAsync(bad.get(), 0, 4, st));
+    absmax_kernel<<<std::min<int64_t>(1024, cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, mx.get(), bad.get());
+    KRR_CUDA(cudaGetLastError());
+    unsigned int hmx = 0;
+    int hbad = 0;
+    KRR_CUDA(cudaMemcpyAsync(&hmx, mx.get(), 4, cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaMemcpyAsync(&hbad, bad.get(), 4, cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaStreamSynchronize(st));
+    if (hbad) return fail(KRR_ERR_NONFINITE_INPUT, "krr_cluster: NaN or Inf in X");
+    float maxabs;
+    std::memcpy(&maxabs, &hmx, 4);
+    int L = 0;
+    {
+        uint64_t v = uint64_t(4) * uint64_t(d) * uint64_t(n) - 1;
+        while (v) { ++L; v >>= 1; }
+    }
+    const int t = (63 - L) / 2;
+    int kexp = 0;
+    if (maxabs > 0.f) {
+        int e;
+        std::frexp(double(maxabs), &e);
+        kexp = t - e;
+    }
+    DBuf<int64_t> q(c, size_t(n) * d), q2(c, size_t(n) * d);
+    DBuf<int32_t> pa(c, n), pb(c, n), node_of(c, n), zflag(c, n);
+    DBuf<int8_t> label(c, n);
+    DBuf<int64_t> zscan(c, n), bsum(c, cdiv(n, kTB) + 1);
+    if (!q.get() || !q2.get() || !pa.get() || !pb.get() || !node_of.get() || !zflag.get() || !label.get() ||
+        !zscan.get() || !bsum.get())
+        return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+    quantize_kernel<<<unsigned(cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, std::ldexp(1.0, kexp), q.get());
+    KRR_CUDA(cudaGetLastError());
+    {
+        std::vector<int32_t> idp(n);
+        for (int64_t i = 0; i < n; ++i) idp[i] = int32_t(i);
+        KRR_CUDA(cudaMemcpyAsync(pa.get(), idp.data(), n * 4, cudaMemcpyHostToDevice, st));
+        KRR_CUDA(cudaStreamSynchronize(st));
+    }
+    int64_t *qc = q.get(), *qn = q2.get();
+    int32_t *pc = pa.get(), *pn = pb.get();
+
+    // --- tree, created level by level (ids in creation order; postorder at the end)
+    struct Node { int64_t b, m; int left, right, parent, level; };
+    std::vector<Node> nodes;
+    nodes.push_back({0, n, -1, -1, -1, 0});
+    std::vector<int> active;
+    if (n > leaf) active.push_back(0);
+    DBuf<int32_t> running(c, 1);
+    if (!running.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+    while (!active.empty()) {
+        const int nn = int(active.size());
+        std::vector<int64_t> hb(nn), hs(nn);
+        for (int k = 0; k < nn; ++k) {
+            hb[k] = nodes[active[k]].b;
+            hs[k] = nodes[active[k]].m;
+        }
+        DBuf<int64_t> db(c, nn), ds(c, nn), dcnt0(c, nn);
+        DBuf<NodeState> dns(c, nn);
+        if (!db.get() || !ds.get() || !dcnt0.get() || !dns.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(db.get(), hb.data(), nn * 8, cudaMemcpyHostToDevice, st));
+        KRR_CUDA(cudaMemcpyAsync(ds.get(), hs.data(), nn * 8, cudaMemcpyHostToDevice, st));
+        KRR_CUDA(cudaMemsetAsync(node_of.get(), 0xFF, n * 4, st));
+        mark_nodes_kernel<<<nn, kTB, 0, st>>>(nn, db.get(), ds.get(), node_of.get());
+        seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dns.get(), seed);
+        KRR_CUDA(cudaGetLastError());
+        for (int iter = 0; iter <= kMaxIter; ++iter) {
+            KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
+            assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(qc, d, n, node_of.get(), dns.get(), label.get());
+            update_kernel<<<unsigned(cdiv(nn, 128)), 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get());
+            KRR_CUDA(cudaGetLastError());
+            int hrun = 0;
+            KRR_CUDA(cudaMemcpyAsync(&hrun, running.get(), 4, cudaMemcpyDeviceToHost, st));
+            KRR_CUDA(cudaStreamSynchronize(st));
+            if (hrun == 0) break;
+        }
+        finalize_labels_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(n, node_of.get(), db.get(), ds.get(),
+                                                                        dns.get(), label.get(), zflag.get());
+        const int64_t nblk = cdiv(n, kTB);
+        scan_blocks_kernel<<<unsigned(nblk), kTB, 0, st>>>(zflag.get(), n, zscan.get(), bsum.get());
+        scan_sums_kernel<<<1, kTB, 0, st>>>(bsum.get(), nblk);
+        scan_add_kernel<<<unsigned(nblk), kTB, 0, st>>>(zscan.get(), n, bsum.get(), nullptr);
+        partition_kernel<<<unsigned(nblk), kTB, 0, st>>>(n, d, node_of.get(), db.get(), ds.get(), label.get(),
+                                                          zscan.get(), zflag.get(), qc, pc, qn, pn, dcnt0.get());
+        KRR_CUDA(cudaGetLastError());
+        std::vector<int64_t> hc0(nn);
+        KRR_CUDA(cudaMemcpyAsync(hc0.data(), dcnt0.get(), nn * 8, cudaMemcpyDeviceToHost, st));
+        KRR_CUDA(cudaStreamSynchronize(st));
+        std::swap(qc, qn);
+        std::swap(pc, pn);
+        std::vector<int> next;
+        for (int k = 0; k < nn; ++k) {
+            const int v = active[k];
+            const Node par = nodes[v];
+            const int64_t c0 = hc0[k];
+            const int li = int(nodes.size());
+            nodes.push_back({par.b, c0, -1, -1, v, par.level + 1});
+            nodes.push_back({par.b + c0, par.m - c0, -1, -1, v, par.level + 1});
+            nodes[v].left = li;
+            nodes[v].right = li + 1;
+            if (c0 > leaf) next.push_back(li);
+            if (par.m - c0 > leaf) next.push_back(li + 1);
+        }
+        active.swap(next);
+    }
+    KRR_CUDA(cudaMemcpyAsync(perm_out, pc, n * 4, cudaMemcpyDeviceToDevice, st));
+    KRR_CUDA(cudaStreamSynchronize(st));
+
+    // --- postorder numbering (left subtree, right subtree, node)
+    const int N = int(nodes.size());
+    std::vector<int> post(N, -1), order;
+    order.reserve(N);
+    std::vector<std::pair<int, int>> stack;
+    stack.push_back({0, 0});
+    while (!stack.empty()) {
+        auto &top = stack.back();
+        const Node &nd = nodes[top.first];
+        if (nd.left < 0 || top.second == 2) {
+            post[top.first] = int(order.size());
+            order.push_back(top.first);
+            stack.pop_back();
+        } else {
+            const int child = top.second == 0 ? nd.left : nd.right;
+            top.second += 1;
+            stack.push_back({child, 0});
+        }
+    }
+    tb.resize(N); te.resize(N); tl.resize(N); tr.resize(N); tp.resize(N); tv.resize(N);
+    for (int k = 0; k < N; ++k) {
+        const Node &nd = nodes[order[k]];
+        tb[k] = int32_t(nd.b);
+        te[k] = int32_t(nd.b + nd.m);
+        tl[k] = nd.left < 0 ? -1 : post[nd.left];
+        tr[k] = nd.right < 0 ? -1 : post[nd.right];
+        tp[k] = nd.parent < 0 ? -1 : post[nd.parent];
+        tv[k] = nd.level;
+    }
+    return KRR_OK;
+}
+
+}  // namespace krr
+
+using namespace krr;
+
+extern "C" int krr_cluster(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t leaf, uint64_t seed,
+                           int32_t *perm, int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes) {
+    if (!k || (n > 0 && (!X || !perm)) || n < 0 || d <= 0 || leaf < 1 || !n_nodes)
+        return fail(KRR_ERR_INVALID_ARG, "krr_cluster: bad arguments");
+    if (n > 0x7FFFFFFF) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: n too large");
+    std::vector<int32_t> tb, te, tl, tr, tp, tv;
+    KRR_TRY(cluster(&k->c, X, n, d, leaf, seed, perm, tb, te, tl, tr, tp, tv));
+    const int N = int(tb.size());
+    *n_nodes = N;
+    if (N > max_nodes) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: max_nodes too small");
+    if (N > 0 && (!tree.begin || !tree.end || !tree.left || !tree.right || !tree.parent || !tree.level))
+        return fail(KRR_ERR_INVALID_ARG, "krr_cluster: tree arrays are NULL");
+    for (int i = 0; i < N; ++i) {
+        tree.begin[i] = tb[i];
+        tree.end[i] = te[i];
+        tree.left[i] = tl[i];
+        tree.right[i] = tr[i];
+        tree.parent[i] = tp[i];
+        tree.level[i] = tv[i];
+    }
+    return KRR_OK;
+}

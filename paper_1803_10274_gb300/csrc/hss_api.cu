@@ -35,9 +35,5 @@ int krr_predict(krr_hss *, const float *, int64_t, const double *, int32_t, int6
 int hss_stats(const krr_hss *, krr_hss_stats *) { return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_stats"); }
 const int32_t *hss_permutation(const krr_hss *) { return nullptr; }
 void hss_destroy(krr_hss *) {}
-int krr_cluster(krr_ctx *, const float *, int64_t, int32_t, int32_t, uint64_t, int32_t *, int32_t, krr_tree_arrays,
-                int32_t *) {
-    return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_cluster");
-}
 
 }  // extern "C"
