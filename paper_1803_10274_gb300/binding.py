@@ -149,7 +149,7 @@ class HSS:
     def update_lambda(self, lam):
         check(lib().hss_update_lambda(self.h, lam))
 
-    def solve(self, y, tol=0.0, max_refine=20):
+    def solve(self, y, tol=0.0, max_refine=100):
         """alpha (n x nrhs float64, original order) and the final residual."""
         _need(y, torch.float64, "y")
         alpha = torch.empty_like(y)

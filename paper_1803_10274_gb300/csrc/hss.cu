@@ -1,0 +1,1152 @@
+// Randomized HSS compression of K + lambda I (paper Section 3.1 and its
+// ref. [2]: samples S = A R from the fused product plus selected entries
+// of A), the ULV-type factorization and solve, iterative refinement with
+// the exact fused product, and prediction (Algorithm 1 steps 2-4).
+//
+// Rows and columns are in two-means cluster order (Algorithm 1 step 0).
+// Levels of the tree are processed bottom-up by node height; one CTA owns
+// one node and works on global-memory (L2-resident) operands.
+//
+// Compression of a symmetric A with V = U (per node tau, rows I_tau):
+//   leaf:   S_loc = A(I, I^c) R(I^c, :)  -- the off-diagonal-block sample,
+//           which the fused product computes directly by skipping the
+//           same-leaf pairs; R_loc = R(I, :)
+//   parent: S_loc = [S_a(J_a) - B_ab Rhat_b ; S_b(J_b) - B_ab^T Rhat_a],
+//           R_loc = [Rhat_a ; Rhat_b],  B_ab = A(J_a, J_b)
+//   row ID of S_loc (pivoted QR of S_loc^T): skeleton J_tau, interpolation
+//   matrix T (k x (m-k)), redundant rows ~= T^T x skeleton rows;
+//   Rhat_tau = R_loc(J) + T R_loc(redundant).
+// Adaptive sampling: a node whose rank exceeds r - p asks for more random
+// columns; r doubles (up to r_max), the new columns are sampled and the
+// sweep restarts.
+//
+// Factorization (per non-root node, local order permuted to skeleton s
+// first, redundant r after; D is the node's diagonal block: K(I,I)+lambda I
+// at a leaf, [Dt_a, B_ab; B_ab^T, Dt_b] at a parent):
+//   the row/column operations E = [I 0; -T^T I] zero A(r, outside) exactly,
+//   D'_rs = D_rs - T^T D_ss,  D'_rr = D_rr - T^T D_sr - D'_rs T,
+//   LU of D'_rr,  Y = D'_rr^{-1} D'_rs,  Dt = D_ss - D'_rs^T Y  (to parent);
+// the root's merged block is LU-factored.  The solve runs the same
+// eliminations on the right-hand side up the tree and back-substitutes
+// down.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "dense.cuh"
+#include "prep.cuh"
+
+namespace krr {
+
+int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, int32_t *perm_out,
+            std::vector<int32_t> &tb, std::vector<int32_t> &te, std::vector<int32_t> &tl, std::vector<int32_t> &tr,
+            std::vector<int32_t> &tp, std::vector<int32_t> &tv);
+
+namespace {
+
+constexpr int kHoldOut = 16;  // sample columns held out of each ID for its error test
+constexpr double kTestFactor = 3.0;  // held-out error allowed, relative to eps_c
+
+// Per-node descriptor of one level (offsets are element offsets into the
+// HSS arenas; -1 when unused).
+struct NodeDesc {
+    int m, k, is_leaf, leaf_begin;
+    int ka, kb;          // children's ranks
+    int child_a, child_b;  // node ids
+    int64_t sloc;        // parent S_loc (m x r)
+    int64_t skel, rhat;  // outputs (k x r, capacity m x r)
+    int64_t w, rg;       // workspaces (m x r)
+    int64_t tmat;        // T (k x (m-k)), capacity m*m
+    int64_t piv;         // int arena, m
+    int64_t rows;        // int arena, m: global row ids in local order
+    int64_t jsk;         // int arena, m: skeleton global ids (first k)
+    int64_t norm;        // workspace m
+    int64_t bmat;        // B_ab (ka x kb) at parents
+    // factorization (capacity m*m each)
+    int64_t dmat, dtil, drs, drr, ymat;
+    int64_t ipiv;        // int arena, m
+    // solve workspaces (capacity m x nrhs_cap)
+    int64_t zvec, btil, xloc;
+};
+
+template <class T>
+struct Arena {
+    Ctx *c = nullptr;
+    DBuf<T> f;
+    DBuf<int32_t> i;
+};
+
+// ------------------------------------------------------------ kernels
+template <class T>
+__device__ __forceinline__ T kern(const T *xa, const T *xb, int d, T inv2h2) {
+    T s = T(0);
+    for (int q = 0; q < d; ++q) {
+        const T t = xa[q] - xb[q];
+        s += t * t;
+    }
+    return exp(-s * inv2h2);
+}
+
+// B_ab = K(J_a, J_b) for every parent of the level.
+template <class T>
+__global__ void extract_b_kernel(const NodeDesc *nd, const T *X, int d, T inv2h2, T *F, const int32_t *I,
+                                 const NodeDesc *all) {
+    const NodeDesc &N = nd[blockIdx.x];
+    if (N.is_leaf) return;
+    const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
+    const int ka = A.k, kb = B.k;
+    for (int e = threadIdx.x; e < ka * kb; e += blockDim.x) {
+        const int a = e / kb, b = e % kb;
+        const int ia = I[A.jsk + a], ib = I[B.jsk + b];
+        F[N.bmat + e] = kern(X + int64_t(ia) * d, X + int64_t(ib) * d, d, inv2h2);
+    }
+}
+
+// Build S_loc, R_loc (into rg) and global row ids of every node; then the
+// row ID, skeleton samples and Rhat.
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) id_kernel(NodeDesc *nd, const NodeDesc *all, const T *S, const T *R,
+                                                      int64_t ldsr, int r, T *F, int32_t *I, T eps, T eps_abs,
+                                                      int kmax, int *ranks, float *test_err, DevStatus *st) {
+    NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    T *W = F + N.w;
+    T *Rg = F + N.rg;
+    int32_t *rows = I + N.rows;
+    // local S_loc -> W, local R -> Rg (local order), row ids
+    if (N.is_leaf) {
+        for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) {
+            const int a = int(e / r), t = int(e % r);
+            const int64_t gi = N.leaf_begin + a;
+            W[e] = S[gi * ldsr + t];
+            Rg[e] = R[gi * ldsr + t];
+        }
+        for (int a = threadIdx.x; a < m; a += blockDim.x) rows[a] = N.leaf_begin + a;
+    } else {
+        const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
+        const int ka = A.k, kb = B.k;
+        T *Sl = F + N.sloc;
+        for (int64_t e = threadIdx.x; e < int64_t(ka) * r; e += blockDim.x) Sl[e] = F[A.skel + e];
+        for (int64_t e = threadIdx.x; e < int64_t(kb) * r; e += blockDim.x) Sl[int64_t(ka) * r + e] = F[B.skel + e];
+        __syncthreads();
+        // S_a(J_a) - B_ab Rhat_b ;  S_b(J_b) - B_ab^T Rhat_a
+        cta::gemm<T, false, false>(ka, r, kb, T(-1), F + N.bmat, kb, F + B.rhat, r, T(1), Sl, r);
+        cta::gemm<T, true, false>(kb, r, ka, T(-1), F + N.bmat, kb, F + A.rhat, r, T(1), Sl + int64_t(ka) * r, r);
+        for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) W[e] = Sl[e];
+        for (int64_t e = threadIdx.x; e < int64_t(ka) * r; e += blockDim.x) Rg[e] = F[A.rhat + e];
+        for (int64_t e = threadIdx.x; e < int64_t(kb) * r; e += blockDim.x) Rg[int64_t(ka) * r + e] = F[B.rhat + e];
+        for (int a = threadIdx.x; a < ka; a += blockDim.x) rows[a] = I[A.jsk + a];
+        for (int a = threadIdx.x; a < kb; a += blockDim.x) rows[ka + a] = I[B.jsk + a];
+    }
+    __syncthreads();
+    int32_t *piv = I + N.piv;
+    // the last kHoldOut sample columns are held out of the QR and measure
+    // the decomposition's error on fresh random directions
+    const int rid = r - kHoldOut;
+    const int k = cta::row_id<T>(m, rid, r, W, r, eps, eps_abs, piv, F + N.norm, F + N.tmat, kmax);
+    const T terr = cta::id_test_error<T>(m, k, W, r, F + N.tmat, rid, r);
+    if (threadIdx.x == 0) {
+        N.k = k;
+        ranks[blockIdx.x] = k;
+        test_err[blockIdx.x] = float(terr);
+    }
+    // skeleton ids and skeleton samples (from the unmodified S_loc)
+    const T *Sorig = N.is_leaf ? nullptr : F + N.sloc;
+    for (int a = threadIdx.x; a < k; a += blockDim.x) I[N.jsk + a] = rows[piv[a]];
+    for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += blockDim.x) {
+        const int a = int(e / r), t = int(e % r);
+        const int src = piv[a];
+        F[N.skel + e] = N.is_leaf ? S[(N.leaf_begin + int64_t(src)) * ldsr + t] : Sorig[int64_t(src) * r + t];
+    }
+    // R rows in pivot order into W (free now), then Rhat = R_s + T R_r
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) {
+        const int a = int(e / r), t = int(e % r);
+        W[e] = Rg[int64_t(piv[a]) * r + t];
+    }
+    __syncthreads();
+    T *Rh = F + N.rhat;
+    for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += blockDim.x) Rh[e] = W[e];
+    __syncthreads();
+    if (k > 0 && m > k)
+        cta::gemm<T, false, false>(k, r, m - k, T(1), F + N.tmat, m - k, W + int64_t(k) * r, r, T(1), Rh, r);
+}
+
+// Diagonal block of every node: K(I,I) + lambda I at leaves, the merged
+// [Dt_a, B; B^T, Dt_b] at parents; then (non-root) the elimination.
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) factor_kernel(NodeDesc *nd, const NodeDesc *all, const T *X, int d,
+                                                          T inv2h2, T lambda, T *F, int32_t *I, int is_root,
+                                                          DevStatus *st) {
+    NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    T *D = F + N.dmat;
+    if (N.is_leaf) {
+        for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) {
+            const int a = int(e / m), b = int(e % m);
+            T v = a == b ? T(1) : kern(X + (N.leaf_begin + int64_t(a)) * d, X + (N.leaf_begin + int64_t(b)) * d, d, inv2h2);
+            if (a == b) v += lambda;
+            D[e] = v;
+        }
+    } else {
+        const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
+        const int ka = A.k, kb = B.k;
+        for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) {
+            const int a = int(e / m), b = int(e % m);
+            T v;
+            if (a < ka && b < ka) v = F[A.dtil + int64_t(a) * ka + b];
+            else if (a >= ka && b >= ka) v = F[B.dtil + int64_t(a - ka) * kb + (b - ka)];
+            else if (a < ka) v = F[N.bmat + int64_t(a) * kb + (b - ka)];
+            else v = F[N.bmat + int64_t(b) * kb + (a - ka)];
+            D[e] = v;
+        }
+    }
+    __syncthreads();
+    if (is_root) {
+        if (!cta::lu<T>(m, D, m, I + N.ipiv) && threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 200);
+        return;
+    }
+    const int k = N.k, nr = m - k;
+    const int32_t *piv = I + N.piv;
+    // permute to (skeleton, redundant) order into drr's slot as scratch
+    T *Dp = F + N.drr;
+    for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) {
+        const int a = int(e / m), b = int(e % m);
+        Dp[e] = D[int64_t(piv[a]) * m + piv[b]];
+    }
+    __syncthreads();
+    // copy Dp back into D so D holds the permuted block; Dss = D[0:k,0:k],
+    // Dsr = D[0:k,k:], Drs = D[k:,0:k], Drr = D[k:,k:]
+    for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) D[e] = Dp[e];
+    __syncthreads();
+    const T *Tm = F + N.tmat;
+    T *Drs = F + N.drs;    // nr x k
+    T *Drr = F + N.drr;    // nr x nr
+    T *Y = F + N.ymat;     // nr x k
+    T *Dt = F + N.dtil;    // k x k
+    for (int64_t e = threadIdx.x; e < int64_t(nr) * k; e += blockDim.x) {
+        const int a = int(e / k), b = int(e % k);
+        Drs[e] = D[int64_t(k + a) * m + b];
+    }
+    for (int64_t e = threadIdx.x; e < int64_t(nr) * nr; e += blockDim.x) {
+        const int a = int(e / nr), b = int(e % nr);
+        Drr[e] = D[int64_t(k + a) * m + k + b];
+    }
+    __syncthreads();
+    if (k > 0 && nr > 0) {
+        // D'_rs = D_rs - T^T D_ss
+        cta::gemm<T, true, false>(nr, k, k, T(-1), Tm, nr, D, m, T(1), Drs, k);
+        // D'_rr = D_rr - T^T D_sr - D'_rs T
+        cta::gemm<T, true, false>(nr, nr, k, T(-1), Tm, nr, D + k, m, T(1), Drr, nr);
+        cta::gemm<T, false, false>(nr, nr, k, T(-1), Drs, k, Tm, nr, T(1), Drr, nr);
+    }
+    if (nr > 0 && !cta::lu<T>(nr, Drr, nr, I + N.ipiv)) {
+        if (threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 201);
+        return;
+    }
+    // Y = D'_rr^{-1} D'_rs ; Dt = D_ss - D'_rs^T Y
+    for (int64_t e = threadIdx.x; e < int64_t(nr) * k; e += blockDim.x) Y[e] = Drs[e];
+    for (int64_t e = threadIdx.x; e < int64_t(k) * k; e += blockDim.x) {
+        const int a = int(e / k), b = int(e % k);
+        Dt[e] = D[int64_t(a) * m + b];
+    }
+    __syncthreads();
+    if (nr > 0 && k > 0) {
+        cta::lu_solve<T>(nr, Drr, nr, I + N.ipiv, k, Y, k);
+        cta::gemm<T, true, false>(k, k, nr, T(-1), Drs, k, Y, k, T(1), Dt, k);
+    }
+}
+
+// Up-sweep of the solve: local b -> (z, btil).
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) solve_up_kernel(NodeDesc *nd, const NodeDesc *all, const T *yperm,
+                                                            int64_t ldy, int nrhs, T *F, const int32_t *I, int is_root) {
+    NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    T *b = F + N.xloc;  // local b (m x nrhs), reused for x in the down-sweep
+    if (N.is_leaf) {
+        for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
+            const int a = int(e / nrhs), c = int(e % nrhs);
+            b[e] = yperm[(N.leaf_begin + int64_t(a)) * ldy + c];
+        }
+    } else {
+        const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
+        for (int64_t e = threadIdx.x; e < int64_t(A.k) * nrhs; e += blockDim.x) b[e] = F[A.btil + e];
+        for (int64_t e = threadIdx.x; e < int64_t(B.k) * nrhs; e += blockDim.x) b[int64_t(A.k) * nrhs + e] = F[B.btil + e];
+    }
+    __syncthreads();
+    if (is_root) {
+        cta::lu_solve<T>(m, F + N.dmat, m, I + N.ipiv, nrhs, b, nrhs);
+        return;
+    }
+    const int k = N.k, nr = m - k;
+    const int32_t *piv = I + N.piv;
+    T *z = F + N.zvec;   // nr x nrhs
+    T *bt = F + N.btil;  // k x nrhs
+    for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
+        const int a = int(e / nrhs), c = int(e % nrhs);
+        const T v = b[int64_t(piv[a]) * nrhs + c];
+        if (a < k) bt[int64_t(a) * nrhs + c] = v;
+        else z[int64_t(a - k) * nrhs + c] = v;
+    }
+    __syncthreads();
+    if (nr > 0) {
+        if (k > 0) cta::gemm<T, true, false>(nr, nrhs, k, T(-1), F + N.tmat, nr, bt, nrhs, T(1), z, nrhs);
+        cta::lu_solve<T>(nr, F + N.drr, nr, I + N.ipiv, nrhs, z, nrhs);
+        if (k > 0) cta::gemm<T, true, false>(k, nrhs, nr, T(-1), F + N.drs, k, z, nrhs, T(1), bt, nrhs);
+    }
+}
+
+// Down-sweep: receive x's (k x nrhs), produce the local x.
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) solve_down_kernel(NodeDesc *nd, const NodeDesc *all, int nrhs, T *F,
+                                                              const int32_t *I, T *xperm, int64_t ldx) {
+    NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m, k = N.k, nr = m - k;
+    // x's arrives in btil (written by the parent's down step)
+    T *xs = F + N.btil;
+    T *z = F + N.zvec;
+    const int32_t *piv = I + N.piv;
+    if (nr > 0 && k > 0) {
+        // x'_r = z - Y x'_s ; then x_s = x'_s - T x'_r
+        cta::gemm<T, false, false>(nr, nrhs, k, T(-1), F + N.ymat, k, xs, nrhs, T(1), z, nrhs);
+        cta::gemm<T, false, false>(k, nrhs, nr, T(-1), F + N.tmat, nr, z, nrhs, T(1), xs, nrhs);
+    }
+    T *x = F + N.xloc;
+    for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
+        const int a = int(e / nrhs), c = int(e % nrhs);
+        const T v = a < k ? xs[int64_t(a) * nrhs + c] : z[int64_t(a - k) * nrhs + c];
+        x[int64_t(piv[a]) * nrhs + c] = v;
+    }
+    __syncthreads();
+    if (N.is_leaf) {
+        for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
+            const int a = int(e / nrhs), c = int(e % nrhs);
+            xperm[(N.leaf_begin + int64_t(a)) * ldx + c] = x[e];
+        }
+    }
+}
+
+template <class T>
+__global__ void root_leaf_out_kernel(const NodeDesc *nd, int nrhs, const T *F, T *xperm, int64_t ldx) {
+    const NodeDesc &N = nd[0];
+    for (int64_t e = threadIdx.x; e < int64_t(N.m) * nrhs; e += blockDim.x) {
+        const int a = int(e / nrhs), c = int(e % nrhs);
+        xperm[(N.leaf_begin + int64_t(a)) * ldx + c] = F[N.xloc + e];
+    }
+}
+
+// Hand the parent's local x to its children (x'_s slots).
+template <class T>
+__global__ void scatter_down_kernel(const NodeDesc *nd, const NodeDesc *all, int nrhs, T *F) {
+    const NodeDesc &N = nd[blockIdx.x];
+    if (N.is_leaf) return;
+    const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
+    const T *x = F + N.xloc;
+    for (int64_t e = threadIdx.x; e < int64_t(A.k) * nrhs; e += blockDim.x) F[A.btil + e] = x[e];
+    for (int64_t e = threadIdx.x; e < int64_t(B.k) * nrhs; e += blockDim.x) F[B.btil + e] = x[int64_t(A.k) * nrhs + e];
+}
+
+__global__ void leaf_id_kernel(int64_t n, const int32_t *begin, const int32_t *end, const int32_t *isleaf, int nn,
+                               int32_t *leaf_of) {
+    const int v = blockIdx.x;
+    if (v >= nn || !isleaf[v]) return;
+    for (int64_t i = begin[v] + threadIdx.x; i < end[v]; i += blockDim.x) leaf_of[i] = v;
+}
+
+// out(i, c) = hi(v) and lo(v): a value split into two FP16-exact parts
+// (stored as float), so a tensor-core product with [hi | lo] recovers the
+// FP32 precision of v.
+__global__ void split16_kernel(const double *v, int64_t n, int nr, int64_t ldv, float *out, int64_t ldo) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * nr) return;
+    const int64_t i = e / nr;
+    const int c = int(e % nr);
+    const double x = v[i * ldv + c];
+    const float hi = __half2float(__double2half(x));
+    const float lo = __half2float(__double2half(x - double(hi)));
+    out[i * ldo + c] = hi;
+    out[i * ldo + nr + c] = lo;
+}
+
+// res = y - (S_hi + S_lo) - lambda * a  (mixed) or y - S - lambda a (FP64);
+// also the per-column squared norms of res and y.
+template <class TS>
+__global__ void residual_kernel(const double *y, int64_t ldy, const TS *S, int64_t lds, int split, const double *a,
+                                int64_t lda, int64_t n, int nr, double lambda, double *res, int64_t ldr,
+                                double *norms) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * nr) return;
+    const int64_t i = e / nr;
+    const int c = int(e % nr);
+    double ka = double(S[i * lds + c]);
+    if (split) ka += double(S[i * lds + nr + c]);
+    const double yy = y[i * ldy + c];
+    const double rr = yy - ka - lambda * a[i * lda + c];
+    res[i * ldr + c] = rr;
+    atomicAdd(&norms[2 * c], rr * rr);
+    atomicAdd(&norms[2 * c + 1], yy * yy);
+}
+
+// out = S (+ S_lo) + lambda * V  (lambda only when V's rows are the rows of out)
+template <class TS>
+__global__ void combine_kernel(const TS *S, int64_t lds, int split, const double *V, int64_t ldv, double lambda,
+                               int64_t n, int nr, double *out, int64_t ldo) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * nr) return;
+    const int64_t i = e / nr;
+    const int c = int(e % nr);
+    double v = double(S[i * lds + c]);
+    if (split) v += double(S[i * lds + nr + c]);
+    if (lambda != 0.0) v += lambda * V[i * ldv + c];
+    out[i * ldo + c] = v;
+}
+
+// dots[i][c] += sum_rows A_i(row, c) * B(row, c) for blocks A_i = A + i * bstride
+__global__ void multidot_kernel(const double *A, int64_t bstride, int nb, const double *B, int64_t n, int nr,
+                                double *dots) {
+    extern __shared__ double sh[];
+    const int i = blockIdx.y;
+    for (int c = threadIdx.x; c < nr; c += blockDim.x) sh[c] = 0.0;
+    __syncthreads();
+    const double *Ai = A + int64_t(i) * bstride;
+    const int64_t tot = n * nr;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < tot; e += int64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&sh[e % nr], Ai[e] * B[e]);
+    __syncthreads();
+    for (int c = threadIdx.x; c < nr; c += blockDim.x) atomicAdd(&dots[i * nr + c], sh[c]);
+}
+
+// W(row, c) += sum_i coef[i][c] * A_i(row, c)   (coef already carries signs)
+__global__ void combo_kernel(double *W, const double *A, int64_t bstride, int nb, const double *coef, int64_t n,
+                             int nr) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * nr) return;
+    const int c = int(e % nr);
+    double s = W[e];
+    for (int i = 0; i < nb; ++i) s += coef[i * nr + c] * A[int64_t(i) * bstride + e];
+    W[e] = s;
+}
+
+// A(row, c) = B(row, c) * scale[c]
+__global__ void colscale_kernel(double *A, const double *B, const double *scale, int64_t n, int nr) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < n * nr) A[e] = B[e] * scale[e % nr];
+}
+
+template <class Tin, class Tout>
+__global__ void convert_kernel(const Tin *a, int64_t n, Tout *b) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = Tout(a[e]);
+}
+
+__global__ void axpy_kernel(double *a, const double *b, int64_t n) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < n) a[e] += b[e];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+struct HssImpl {
+    Ctx *c = nullptr;
+    krr_options opt{};
+    int64_t n = 0;
+    int d = 0;
+    // tree (postorder)
+    std::vector<int32_t> tb, te, tl, tr, tp, tv;
+    std::vector<int> height;
+    int root = -1, H = 0;
+    std::vector<std::vector<int>> by_height;  // node ids per height (root excluded from IDs)
+    DBuf<int32_t> perm, leaf_of;
+    DBuf<float> Xp32;     // permuted X (FP32)
+    DBuf<double> Xp64;    // permuted X (FP64, plain path)
+    DBuf<__half> XA, XB;  // augmented operands (mixed path)
+    int kpad = 0;
+    int64_t ldrt = 0;
+    // samples
+    int r = 0, r_cap = 0, rounds = 0;
+    DBuf<float> R32, S32;
+    DBuf<double> R64, S64;
+    DBuf<__half> RT;
+    // per-node data
+    std::vector<NodeDesc> desc;  // host copy (k filled after IDs)
+    DBuf<NodeDesc> ddesc;        // device copy of all nodes
+    DBuf<float> F32;
+    DBuf<double> F64;
+    DBuf<int32_t> IA;
+    int nrhs_cap = 0;
+    bool factored = false;
+    double lambda = 0;
+    int max_rank = 0, refine_steps = 0;
+    double max_test_err = 0;
+    double t_cluster = 0, t_sample = 0, t_compress = 0, t_factor = 0, t_solve = 0;
+    bool mixed() const { return opt.precision == KRR_MIXED; }
+};
+
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <class T>
+T *farena(HssImpl *H);
+template <>
+float *farena<float>(HssImpl *H) { return H->F32.get(); }
+template <>
+double *farena<double>(HssImpl *H) { return H->F64.get(); }
+
+// Lay out every node's arena slots given the ranks known so far (levels
+// up to `upto` final).  Capacities depend only on m, r and nrhs_cap.
+int layout(HssImpl *H, int nrhs_cap, size_t &fsize, size_t &isize) {
+    const int64_t r = H->r;
+    int64_t fo = 0, io = 0;
+    for (int h = 0; h <= H->H; ++h) {
+        for (int v : H->by_height[h]) {
+            NodeDesc &N = H->desc[v];
+            const int64_t m = N.m;
+            auto take = [&](int64_t cnt) { const int64_t o = fo; fo += (cnt + 63) & ~int64_t(63); return o; };
+            auto itake = [&](int64_t cnt) { const int64_t o = io; io += (cnt + 15) & ~int64_t(15); return o; };
+            N.sloc = N.is_leaf ? -1 : take(m * r);
+            N.skel = take(m * r);
+            N.rhat = take(m * r);
+            N.w = take(m * r);
+            N.rg = take(m * r);
+            N.tmat = take(m * m);
+            N.norm = take(m);
+            N.bmat = N.is_leaf ? -1 : take(int64_t(N.ka) * N.kb);
+            N.dmat = take(m * m);
+            N.dtil = take(m * m);
+            N.drs = take(m * m);
+            N.drr = take(m * m);
+            N.ymat = take(m * m);
+            N.zvec = take(m * nrhs_cap);
+            N.btil = take(m * nrhs_cap);
+            N.xloc = take(m * nrhs_cap);
+            N.piv = itake(m);
+            N.rows = itake(m);
+            N.jsk = itake(m);
+            N.ipiv = itake(m);
+        }
+    }
+    fsize = size_t(fo);
+    isize = size_t(io);
+    return KRR_OK;
+}
+
+template <class T>
+int sample_columns(HssImpl *H, int c0, int c1) {
+    Ctx *c = H->c;
+    const int dr = c1 - c0;
+    if (H->mixed()) {
+        KRR_TRY(random_block(c, H->n, dr, c0, H->opt.seed, KRR_MIXED, H->R32.get() + c0, H->r_cap));
+        KRR_TRY(transpose_half(c, H->R32.get() + c0, H->n, dr, H->r_cap, H->RT.get() + int64_t(c0) * H->ldrt,
+                               int(round_up(dr, 64)), H->ldrt));
+        KRR_TRY(sample_mixed_prepared(c, H->XA.get(), H->n, H->XB.get(), H->n, H->d,
+                                      H->RT.get() + int64_t(c0) * H->ldrt, dr, H->ldrt, H->leaf_of.get(),
+                                      H->leaf_of.get(), H->S32.get() + c0, H->r_cap));
+    } else {
+        KRR_TRY(random_block(c, H->n, dr, c0, H->opt.seed, KRR_FP64, H->R64.get() + c0, H->r_cap));
+        KRR_TRY(launch_sample_f64(c, H->Xp64.get(), H->n, H->Xp64.get(), H->n, H->d, H->opt.h,
+                                  H->R64.get() + c0, dr, H->r_cap, H->leaf_of.get(), H->leaf_of.get(),
+                                  H->S64.get() + c0, H->r_cap));
+    }
+    return KRR_OK;
+}
+
+// One bottom-up ID sweep with the current r.  Returns KRR_OK and sets
+// `need_more` when some node's rank exceeds r - p.
+template <class T>
+int id_sweep(HssImpl *H, bool &need_more) {
+    Ctx *c = H->c;
+    need_more = false;
+    const T *S = H->mixed() ? reinterpret_cast<const T *>(H->S32.get()) : reinterpret_cast<const T *>(H->S64.get());
+    const T *R = H->mixed() ? reinterpret_cast<const T *>(H->R32.get()) : reinterpret_cast<const T *>(H->R64.get());
+    const T inv2h2 = T(1.0 / (2.0 * H->opt.h * H->opt.h));
+    const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
+    const int kmax = H->r - kHoldOut - H->opt.p + 1;  // one past the budget: a rank there means "need more"
+    // Arenas are laid out once per level from the actual sizes; since the
+    // parents' m depend on the children's ranks, lay out level by level
+    // into a growing arena.
+    size_t fsize = 0, isize = 0;
+    // first pass: leaves only have known m; allocate generous capacity
+    // for parents by bounding m with min(sum of children's m, 2 (r - p)).
+    for (int h = 1; h <= H->H; ++h)
+        for (int v : H->by_height[h]) {
+            NodeDesc &N = H->desc[v];
+            N.ka = std::max(0, std::min(H->desc[N.child_a].m, kmax));
+            N.kb = std::max(0, std::min(H->desc[N.child_b].m, kmax));
+            N.m = N.ka + N.kb;
+        }
+    layout(H, H->nrhs_cap, fsize, isize);
+    T *F;
+    if (H->mixed()) {
+        if (H->F32.n < fsize && !H->F32.reset(c, fsize)) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        F = reinterpret_cast<T *>(H->F32.get());
+    } else {
+        if (H->F64.n < fsize && !H->F64.reset(c, fsize)) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        F = reinterpret_cast<T *>(H->F64.get());
+    }
+    if (H->IA.n < isize && !H->IA.reset(c, isize)) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+    if (!H->ddesc.get() && !H->ddesc.reset(c, H->desc.size())) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+    DBuf<int> dranks(c, H->desc.size());
+    DBuf<float> derr(c, H->desc.size());
+    if (!dranks.get() || !derr.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+    H->max_test_err = 0;
+    std::vector<NodeDesc> lvdesc;
+    H->max_rank = 0;
+    for (int h = 0; h <= H->H; ++h) {
+        std::vector<int> &lv = H->by_height[h];
+        // exact m for parents now that children are done
+        for (int v : lv) {
+            NodeDesc &N = H->desc[v];
+            if (!N.is_leaf) {
+                N.ka = H->desc[N.child_a].k;
+                N.kb = H->desc[N.child_b].k;
+                N.m = N.ka + N.kb;
+            }
+        }
+        KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), H->desc.size() * sizeof(NodeDesc),
+                                 cudaMemcpyHostToDevice, c->stream));
+        const int nn = int(lv.size());
+        if (nn == 0) continue;
+        lvdesc.resize(nn);
+        for (int a = 0; a < nn; ++a) lvdesc[a] = H->desc[lv[a]];
+        DBuf<NodeDesc> dl(c, nn);
+        if (!dl.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(dl.get(), lvdesc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
+        const bool is_root_level = (h == H->H);
+        if (h > 0)
+            extract_b_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), X, H->d, inv2h2, F, H->IA.get(),
+                                                                H->ddesc.get());
+        KRR_CUDA(cudaGetLastError());
+        if (is_root_level) break;  // the root needs B only
+        const size_t smem = size_t(H->r) * sizeof(T);
+        static bool attr = false;
+        if (!attr) {
+            KRR_CUDA(cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            attr = true;
+        }
+        id_kernel<T><<<nn, cta::kNT, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, H->r, F,
+                                                        H->IA.get(), T(H->opt.eps_c), T(H->opt.eps_abs), kmax,
+                                                        dranks.get(), derr.get(), c->status);
+        KRR_CUDA(cudaGetLastError());
+        std::vector<int> hr(nn);
+        std::vector<float> he(nn);
+        KRR_CUDA(cudaMemcpyAsync(hr.data(), dranks.get(), nn * 4, cudaMemcpyDeviceToHost, c->stream));
+        KRR_CUDA(cudaMemcpyAsync(he.data(), derr.get(), nn * 4, cudaMemcpyDeviceToHost, c->stream));
+        KRR_CUDA(cudaStreamSynchronize(c->stream));
+        for (int a = 0; a < nn; ++a) {
+            H->desc[lv[a]].k = hr[a];
+            H->max_rank = std::max(H->max_rank, hr[a]);
+            H->max_test_err = std::max(H->max_test_err, double(he[a]));
+            if (hr[a] > H->r - kHoldOut - H->opt.p) need_more = true;
+            if (double(he[a]) > kTestFactor * H->opt.eps_c) need_more = true;
+        }
+        if (need_more) return KRR_OK;
+    }
+    return KRR_OK;
+}
+
+template <class T>
+int compress(HssImpl *H) {
+    Ctx *c = H->c;
+    const double t0 = now_ms();
+    double ts = 0;
+    int c0 = 0;
+    H->rounds = 0;
+    // the QR needs at least one column beyond the held-out and oversampling columns
+    while (H->r - kHoldOut - H->opt.p < 1) {
+        if (H->r >= H->opt.r_max) return fail(KRR_ERR_INVALID_ARG, "hss_compress: r_max too small for p");
+        H->r = int(std::min<int64_t>(H->opt.r_max, 2 * int64_t(H->r)));
+    }
+    while (true) {
+        const double s0 = now_ms();
+        KRR_TRY(sample_columns<T>(H, c0, H->r));
+        KRR_CUDA(cudaStreamSynchronize(c->stream));
+        ts += now_ms() - s0;
+        ++H->rounds;
+        bool more = false;
+        KRR_TRY(id_sweep<T>(H, more));
+        if (!more) break;
+        if (H->r >= H->opt.r_max) return fail(KRR_ERR_RANK_BUDGET, "hss_compress: ranks not revealed within r_max");
+        c0 = H->r;
+        H->r = int(std::min<int64_t>(H->opt.r_max, 2 * int64_t(H->r)));
+    }
+    H->t_sample = ts;
+    H->t_compress = now_ms() - t0;
+    return KRR_OK;
+}
+
+template <class T>
+int factor(HssImpl *H) {
+    Ctx *c = H->c;
+    const double t0 = now_ms();
+    T *F = farena<T>(H);
+    const T inv2h2 = T(1.0 / (2.0 * H->opt.h * H->opt.h));
+    const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
+    KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), H->desc.size() * sizeof(NodeDesc),
+                             cudaMemcpyHostToDevice, c->stream));
+    for (int h = 0; h <= H->H; ++h) {
+        std::vector<int> &lv = H->by_height[h];
+        const int nn = int(lv.size());
+        if (!nn) continue;
+        std::vector<NodeDesc> ld(nn);
+        for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
+        DBuf<NodeDesc> dl(c, nn);
+        if (!dl.get()) return fail(KRR_ERR_OOM, "hss_factor: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(dl.get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
+        factor_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), X, H->d, inv2h2, T(H->lambda), F,
+                                                         H->IA.get(), h == H->H ? 1 : 0, c->status);
+        KRR_CUDA(cudaGetLastError());
+    }
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    H->factored = true;
+    H->t_factor = now_ms() - t0;
+    return KRR_OK;
+}
+
+// x_perm = H^{-1} y_perm (both n x nrhs in cluster order, precision T)
+template <class T>
+int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64_t ldx) {
+    Ctx *c = H->c;
+    T *F = farena<T>(H);
+    std::vector<DBuf<NodeDesc>> dls(H->H + 1);
+    for (int h = 0; h <= H->H; ++h) {
+        std::vector<int> &lv = H->by_height[h];
+        const int nn = int(lv.size());
+        if (!nn) continue;
+        std::vector<NodeDesc> ld(nn);
+        for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
+        if (!dls[h].reset(c, nn)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(dls[h].get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
+        solve_up_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), yperm, ldy, nrhs, F,
+                                                           H->IA.get(), h == H->H ? 1 : 0);
+        KRR_CUDA(cudaGetLastError());
+    }
+    for (int h = H->H; h >= 0; --h) {
+        const int nn = int(H->by_height[h].size());
+        if (!nn) continue;
+        if (h < H->H)
+            solve_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F, H->IA.get(),
+                                                                 xperm, ldx);
+        else if (H->desc[H->root].is_leaf)  // single-leaf tree: the root's solve is the answer
+            root_leaf_out_kernel<T><<<1, cta::kNT, 0, c->stream>>>(dls[h].get(), nrhs, F, xperm, ldx);
+        scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F);
+        KRR_CUDA(cudaGetLastError());
+    }
+    return KRR_OK;
+}
+
+}  // namespace
+
+// Fused product K(Xa, Xp) V for nrhs columns of V (double, n x nrhs, in
+// cluster order) in the path's precision; out = double m x nrhs.  With
+// lambda != 0 (Xa == Xp) adds lambda V.  Mixed: V is split into two FP16
+// parts so the product keeps FP32 precision in V.
+int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, const double *V, int64_t ldv, int nrhs,
+              double *out, int64_t ldo, double lambda, const double *y, int64_t ldy, double *res_norms) {
+    Ctx *c = H->c;
+    const int64_t n = H->n;
+    if (H->mixed()) {
+        const int cols = 2 * nrhs;
+        const int rpad = int(round_up(cols, 64));
+        DBuf<float> Rs(c, size_t(n) * cols), Sm(c, size_t(ma) * cols);
+        DBuf<__half> RTs(c, size_t(rpad) * H->ldrt);
+        if (!Rs.get() || !Sm.get() || !RTs.get()) return fail(KRR_ERR_OOM, "hss: out of memory");
+        split16_kernel<<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(V, n, nrhs, ldv, Rs.get(), cols);
+        KRR_TRY(transpose_half(c, Rs.get(), n, cols, cols, RTs.get(), rpad, H->ldrt));
+        KRR_TRY(sample_mixed_prepared(c, XAa, ma, H->XB.get(), n, H->d, RTs.get(), cols, H->ldrt, nullptr, nullptr,
+                                      Sm.get(), cols, true));
+        if (y)
+            residual_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
+                y, ldy, Sm.get(), cols, 1, V, ldv, ma, nrhs, lambda, out, ldo, res_norms);
+        else
+            combine_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm.get(), cols, 1, V, ldv,
+                                                                                        lambda, ma, nrhs, out, ldo);
+    } else {
+        DBuf<double> Sm(c, size_t(ma) * nrhs), Xa64;
+        if (!Sm.get()) return fail(KRR_ERR_OOM, "hss: out of memory");
+        const double *Xa = H->Xp64.get();
+        if (Xa32 != H->Xp32.get()) {
+            if (!Xa64.reset(c, size_t(ma) * H->d)) return fail(KRR_ERR_OOM, "hss: out of memory");
+            KRR_TRY(widen(c, Xa32, ma * H->d, Xa64.get()));
+            Xa = Xa64.get();
+        }
+        KRR_TRY(launch_sample_f64(c, Xa, ma, H->Xp64.get(), n, H->d, H->opt.h, V, nrhs, ldv, nullptr, nullptr,
+                                  Sm.get(), nrhs));
+        if (y)
+            residual_kernel<double><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
+                y, ldy, Sm.get(), nrhs, 0, V, ldv, ma, nrhs, lambda, out, ldo, res_norms);
+        else
+            combine_kernel<double><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm.get(), nrhs, 0, V, ldv,
+                                                                                         lambda, ma, nrhs, out, ldo);
+    }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
+int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, HssImpl *H) {
+    H->c = c;
+    H->opt = *o;
+    H->n = n;
+    H->d = d;
+    H->lambda = o->lambda;
+    const double t0 = now_ms();
+    if (!H->perm.reset(c, n) || !H->leaf_of.reset(c, n) || !H->Xp32.reset(c, size_t(n) * d))
+        return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+    KRR_TRY(cluster(c, X, n, d, o->leaf, o->seed, H->perm.get(), H->tb, H->te, H->tl, H->tr, H->tp, H->tv));
+    H->t_cluster = now_ms() - t0;
+    const int nn = int(H->tb.size());
+    H->root = nn - 1;
+    // heights
+    H->height.assign(nn, 0);
+    for (int v = 0; v < nn; ++v)
+        if (H->tl[v] >= 0) H->height[v] = 1 + std::max(H->height[H->tl[v]], H->height[H->tr[v]]);
+    H->H = H->height[H->root];
+    H->by_height.assign(H->H + 1, {});
+    for (int v = 0; v < nn; ++v) H->by_height[H->height[v]].push_back(v);
+    H->desc.assign(nn, NodeDesc{});
+    for (int v = 0; v < nn; ++v) {
+        NodeDesc &N = H->desc[v];
+        N.is_leaf = H->tl[v] < 0;
+        N.leaf_begin = H->tb[v];
+        N.m = N.is_leaf ? H->te[v] - H->tb[v] : 0;
+        N.k = 0;
+        N.child_a = H->tl[v];
+        N.child_b = H->tr[v];
+    }
+    // leaf id per row, permuted coordinates, augmented operands
+    {
+        std::vector<int32_t> isl(nn);
+        for (int v = 0; v < nn; ++v) isl[v] = H->tl[v] < 0;
+        DBuf<int32_t> db(c, nn), de(c, nn), dl(c, nn);
+        if (!db.get() || !de.get() || !dl.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(db.get(), H->tb.data(), nn * 4, cudaMemcpyHostToDevice, c->stream));
+        KRR_CUDA(cudaMemcpyAsync(de.get(), H->te.data(), nn * 4, cudaMemcpyHostToDevice, c->stream));
+        KRR_CUDA(cudaMemcpyAsync(dl.get(), isl.data(), nn * 4, cudaMemcpyHostToDevice, c->stream));
+        leaf_id_kernel<<<nn, 128, 0, c->stream>>>(n, db.get(), de.get(), dl.get(), nn, H->leaf_of.get());
+        KRR_CUDA(cudaGetLastError());
+        KRR_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    KRR_TRY((gather_rows<float, float>(c, X, d, H->perm.get(), n, d, H->Xp32.get(), d)));
+    H->r_cap = int(round_up(std::max(o->r0, o->r_max), 64));
+    H->r = int(round_up(o->r0, 64));
+    H->nrhs_cap = 64;
+    if (H->mixed()) {
+        H->kpad = aug_kpad(d);
+        H->ldrt = round_up(n, 8);
+        if (!H->XA.reset(c, size_t(n) * H->kpad) || !H->XB.reset(c, size_t(n) * H->kpad) ||
+            !H->R32.reset(c, size_t(n) * H->r_cap) || !H->S32.reset(c, size_t(n) * H->r_cap) ||
+            !H->RT.reset(c, size_t(round_up(H->r_cap, 64)) * H->ldrt))
+            return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        KRR_TRY(augment(c, H->Xp32.get(), n, d, o->h, 0, H->XA.get(), H->kpad));
+        KRR_TRY(augment(c, H->Xp32.get(), n, d, o->h, 1, H->XB.get(), H->kpad));
+        KRR_TRY(compress<float>(H));
+    } else {
+        if (!H->Xp64.reset(c, size_t(n) * d) || !H->R64.reset(c, size_t(n) * H->r_cap) ||
+            !H->S64.reset(c, size_t(n) * H->r_cap))
+            return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        KRR_TRY(widen(c, H->Xp32.get(), n * d, H->Xp64.get()));
+        KRR_TRY(compress<double>(H));
+    }
+    // the samples are no longer needed
+    H->R32.release();
+    H->S32.release();
+    H->RT.release();
+    H->R64.release();
+    H->S64.release();
+    return KRR_OK;
+}
+
+int hss_factor_impl(HssImpl *H) { return H->mixed() ? factor<float>(H) : factor<double>(H); }
+
+int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *alpha, int64_t lda, double tol,
+                   int max_refine, double *resid) {
+    Ctx *c = H->c;
+    if (!H->factored) KRR_TRY(hss_factor_impl(H));
+    const double t0 = now_ms();
+    const int64_t n = H->n;
+    if (nrhs > H->nrhs_cap) return fail(KRR_ERR_INVALID_ARG, "hss_solve: nrhs > 64");
+    DBuf<double> yp(c, size_t(n) * nrhs), ap(c, size_t(n) * nrhs), res(c, size_t(n) * nrhs), dx(c, size_t(n) * nrhs),
+        norms(c, 2 * nrhs);
+    if (!yp.get() || !ap.get() || !res.get() || !dx.get() || !norms.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+    KRR_TRY((gather_rows<double, double>(c, y, ldy, H->perm.get(), n, nrhs, yp.get(), nrhs)));
+    auto ulv = [&](const double *b, double *x) -> int {
+        if (H->mixed()) {
+            DBuf<float> bf(c, size_t(n) * nrhs), xf(c, size_t(n) * nrhs);
+            if (!bf.get() || !xf.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+            convert_kernel<double, float><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(b, n * nrhs, bf.get());
+            KRR_TRY(ulv_solve<float>(H, bf.get(), nrhs, nrhs, xf.get(), nrhs));
+            convert_kernel<float, double><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(xf.get(), n * nrhs, x);
+            KRR_CUDA(cudaGetLastError());
+            return KRR_OK;
+        }
+        return ulv_solve<double>(H, b, nrhs, nrhs, x, nrhs);
+    };
+    double rmax = -1.0;
+    H->refine_steps = 0;
+    if (tol <= 0) {
+        KRR_TRY(ulv(yp.get(), ap.get()));
+    } else {
+        // Right-preconditioned restarted GMRES, one Krylov space per column:
+        // A M^{-1} u = y, alpha = M^{-1} u, M^{-1} = the ULV solve.  Every
+        // column advances together (one fused product and one ULV solve per
+        // iteration); Gram-Schmidt runs twice (CGS2).  Restarts recompute
+        // the true residual with the precise (split-K) fused product.
+        const int mres = 30;
+        const int64_t nn = n * nrhs;
+        DBuf<double> V(c, size_t(mres + 1) * nn), Wv(c, nn), Zv(c, nn), dots(c, size_t(mres + 1) * nrhs),
+            coef(c, size_t(mres + 1) * nrhs), sc(c, nrhs), ynorm(c, 2 * nrhs);
+        if (!V.get() || !Wv.get() || !Zv.get() || !dots.get() || !coef.get() || !sc.get() || !ynorm.get())
+            return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+        KRR_CUDA(cudaMemsetAsync(ap.get(), 0, nn * sizeof(double), c->stream));
+        const unsigned g1 = unsigned(cdiv(nn, 256));
+        const unsigned gd = unsigned(std::min<int64_t>(256, cdiv(nn, 256)));
+        auto mdot = [&](const double *A, int nb, const double *B) -> int {
+            KRR_CUDA(cudaMemsetAsync(dots.get(), 0, size_t(nb) * nrhs * sizeof(double), c->stream));
+            multidot_kernel<<<dim3(gd, nb), 256, nrhs * sizeof(double), c->stream>>>(A, nn, nb, B, n, nrhs, dots.get());
+            KRR_CUDA(cudaGetLastError());
+            return KRR_OK;
+        };
+        std::vector<double> ynrm(nrhs), hd((mres + 1) * nrhs), hd2((mres + 1) * nrhs);
+        KRR_TRY(mdot(yp.get(), 1, yp.get()));
+        KRR_CUDA(cudaMemcpyAsync(ynrm.data(), dots.get(), nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
+        KRR_CUDA(cudaStreamSynchronize(c->stream));
+        for (auto &v : ynrm) v = std::sqrt(v) > 0 ? std::sqrt(v) : 1.0;
+        // per-column Hessenberg (column-major (mres+1) x mres), Givens, rhs
+        std::vector<double> Hm(size_t(nrhs) * (mres + 1) * mres), cs(size_t(nrhs) * mres), sn(size_t(nrhs) * mres),
+            g(size_t(nrhs) * (mres + 1)), beta(nrhs), yv(size_t(mres) * nrhs);
+        int total_it = 0;
+        for (int cycle = 0;; ++cycle) {
+            // r = y - A alpha (precise product); V0 = r / |r|
+            KRR_CUDA(cudaMemsetAsync(norms.get(), 0, 2 * nrhs * sizeof(double), c->stream));
+            KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, ap.get(), nrhs, nrhs, res.get(), nrhs, H->lambda,
+                              yp.get(), nrhs, norms.get()));
+            std::vector<double> hn(2 * nrhs);
+            KRR_CUDA(cudaMemcpyAsync(hn.data(), norms.get(), 2 * nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
+            KRR_CUDA(cudaStreamSynchronize(c->stream));
+            rmax = 0;
+            for (int q = 0; q < nrhs; ++q) {
+                beta[q] = std::sqrt(hn[2 * q]);
+                rmax = std::max(rmax, beta[q] / ynrm[q]);
+            }
+            if (rmax <= tol || total_it >= max_refine) break;
+            std::vector<double> inv(nrhs);
+            for (int q = 0; q < nrhs; ++q) inv[q] = beta[q] > 0 ? 1.0 / beta[q] : 0.0;
+            KRR_CUDA(cudaMemcpyAsync(sc.get(), inv.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
+            colscale_kernel<<<g1, 256, 0, c->stream>>>(V.get(), res.get(), sc.get(), n, nrhs);
+            std::fill(Hm.begin(), Hm.end(), 0.0);
+            std::fill(g.begin(), g.end(), 0.0);
+            for (int q = 0; q < nrhs; ++q) g[size_t(q) * (mres + 1)] = beta[q];
+            int jdone = 0;
+            double est = rmax;
+            for (int j = 0; j < mres && total_it < max_refine; ++j) {
+                ++total_it;
+                double *Vj = V.get() + int64_t(j) * nn;
+                KRR_TRY(ulv(Vj, Zv.get()));
+                KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, Zv.get(), nrhs, nrhs, Wv.get(), nrhs, H->lambda,
+                                  nullptr, 0, nullptr));
+                // two passes of classical Gram-Schmidt
+                std::fill(hd.begin(), hd.end(), 0.0);
+                for (int pass = 0; pass < 2; ++pass) {
+                    KRR_TRY(mdot(V.get(), j + 1, Wv.get()));
+                    KRR_CUDA(cudaMemcpyAsync(hd2.data(), dots.get(), size_t(j + 1) * nrhs * 8, cudaMemcpyDeviceToHost,
+                                             c->stream));
+                    KRR_CUDA(cudaStreamSynchronize(c->stream));
+                    std::vector<double> neg(size_t(j + 1) * nrhs);
+                    for (size_t e = 0; e < neg.size(); ++e) {
+                        hd[e] += hd2[e];
+                        neg[e] = -hd2[e];
+                    }
+                    KRR_CUDA(cudaMemcpyAsync(coef.get(), neg.data(), neg.size() * 8, cudaMemcpyHostToDevice, c->stream));
+                    combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, j + 1, coef.get(), n, nrhs);
+                }
+                KRR_TRY(mdot(Wv.get(), 1, Wv.get()));
+                std::vector<double> wn(nrhs);
+                KRR_CUDA(cudaMemcpyAsync(wn.data(), dots.get(), nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
+                KRR_CUDA(cudaStreamSynchronize(c->stream));
+                std::vector<double> inv2(nrhs);
+                est = 0;
+                for (int q = 0; q < nrhs; ++q) {
+                    double *Hq = Hm.data() + size_t(q) * (mres + 1) * mres;
+                    double *col = Hq + size_t(j) * (mres + 1);
+                    for (int i = 0; i <= j; ++i) col[i] = hd[size_t(i) * nrhs + q];
+                    const double hn1 = std::sqrt(std::max(wn[q], 0.0));
+                    col[j + 1] = hn1;
+                    inv2[q] = hn1 > 0 ? 1.0 / hn1 : 0.0;
+                    double *csq = cs.data() + size_t(q) * mres, *snq = sn.data() + size_t(q) * mres;
+                    double *gq = g.data() + size_t(q) * (mres + 1);
+                    for (int i = 0; i < j; ++i) {
+                        const double a = col[i], b = col[i + 1];
+                        col[i] = csq[i] * a + snq[i] * b;
+                        col[i + 1] = -snq[i] * a + csq[i] * b;
+                    }
+                    const double a = col[j], b = col[j + 1];
+                    const double rr = std::hypot(a, b);
+                    csq[j] = rr > 0 ? a / rr : 1.0;
+                    snq[j] = rr > 0 ? b / rr : 0.0;
+                    col[j] = rr;
+                    col[j + 1] = 0.0;
+                    gq[j + 1] = -snq[j] * gq[j];
+                    gq[j] = csq[j] * gq[j];
+                    est = std::max(est, std::fabs(gq[j + 1]) / ynrm[q]);
+                }
+                KRR_CUDA(cudaMemcpyAsync(sc.get(), inv2.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
+                colscale_kernel<<<g1, 256, 0, c->stream>>>(V.get() + int64_t(j + 1) * nn, Wv.get(), sc.get(), n, nrhs);
+                jdone = j + 1;
+                // stop a little below tol so the true residual also meets it
+                if (est <= 0.5 * tol) break;
+            }
+            // y = H^{-1} g per column; alpha += M^{-1} (V y)
+            for (int q = 0; q < nrhs; ++q) {
+                const double *Hq = Hm.data() + size_t(q) * (mres + 1) * mres;
+                const double *gq = g.data() + size_t(q) * (mres + 1);
+                for (int i = jdone - 1; i >= 0; --i) {
+                    double sacc = gq[i];
+                    for (int k2 = i + 1; k2 < jdone; ++k2) sacc -= Hq[size_t(k2) * (mres + 1) + i] * yv[size_t(k2) * nrhs + q];
+                    const double dgn = Hq[size_t(i) * (mres + 1) + i];
+                    yv[size_t(i) * nrhs + q] = dgn != 0 ? sacc / dgn : 0.0;
+                }
+            }
+            KRR_CUDA(cudaMemcpyAsync(coef.get(), yv.data(), size_t(jdone) * nrhs * 8, cudaMemcpyHostToDevice, c->stream));
+            KRR_CUDA(cudaMemsetAsync(Wv.get(), 0, nn * sizeof(double), c->stream));
+            combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, jdone, coef.get(), n, nrhs);
+            KRR_TRY(ulv(Wv.get(), Zv.get()));
+            axpy_kernel<<<g1, 256, 0, c->stream>>>(ap.get(), Zv.get(), nn);
+            KRR_CUDA(cudaGetLastError());
+        }
+        H->refine_steps = total_it;
+    }
+    KRR_TRY((scatter_rows<double, double>(c, ap.get(), nrhs, H->perm.get(), n, nrhs, alpha, lda)));
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    if (resid) *resid = rmax;
+    H->t_solve = now_ms() - t0;
+    if (tol > 0 && rmax > tol) return fail(KRR_ERR_NO_CONVERGENCE, "hss_solve: refinement did not reach tol");
+    return KRR_OK;
+}
+
+int hss_predict_impl(HssImpl *H, const float *Xt, int64_t m, const double *alpha, int nrhs, int64_t lda, double *out,
+                     int64_t ldo) {
+    Ctx *c = H->c;
+    const int64_t n = H->n;
+    DBuf<double> ap(c, size_t(n) * nrhs);
+    if (!ap.get()) return fail(KRR_ERR_OOM, "krr_predict: out of memory");
+    KRR_TRY((gather_rows<double, double>(c, alpha, lda, H->perm.get(), n, nrhs, ap.get(), nrhs)));
+    DBuf<__half> xa;
+    if (H->mixed()) {
+        if (!xa.reset(c, size_t(m) * H->kpad)) return fail(KRR_ERR_OOM, "krr_predict: out of memory");
+        KRR_TRY(augment(c, Xt, m, H->d, H->opt.h, 0, xa.get(), H->kpad));
+    }
+    return hss_apply(H, Xt, xa.get(), m, ap.get(), nrhs, nrhs, out, ldo, 0.0, nullptr, 0, nullptr);
+}
+
+int64_t hss_memory_bytes(const HssImpl *H) {
+    // D at leaves, U (T) at non-root nodes, B at parents: the generators
+    int64_t e = 0;
+    for (size_t v = 0; v < H->desc.size(); ++v) {
+        const NodeDesc &N = H->desc[v];
+        if (N.is_leaf) e += int64_t(N.m) * N.m;
+        if (int(v) != H->root) e += int64_t(N.k) * (N.m - N.k) + N.k;
+        if (!N.is_leaf) e += int64_t(H->desc[N.child_a].k) * H->desc[N.child_b].k;
+    }
+    return e * (H->mixed() ? 4 : 8);
+}
+
+}  // namespace krr
+
+struct krr_hss {
+    krr::HssImpl h;
+};
+
+using namespace krr;
+
+extern "C" {
+
+int hss_compress(krr_ctx *k, const float *X, int64_t n, int32_t d, const krr_options *o, krr_hss **out) {
+    if (out) *out = nullptr;
+    if (!k || !X || !o || !out || n <= 0 || d <= 0) return fail(KRR_ERR_INVALID_ARG, "hss_compress: bad arguments");
+    if (!(o->h > 0) || !(o->lambda > 0) || !(o->eps_c > 0) || o->eps_abs < 0 || o->leaf < 1 || o->r0 < 1 ||
+        o->p < 0 || o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64))
+        return fail(KRR_ERR_INVALID_ARG, "hss_compress: bad options");
+    if (o->precision == KRR_MIXED && d > kMaxMixedDim)
+        return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress: mixed path supports d <= 40");
+    if (n > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "hss_compress: n too large");
+    krr_hss *H = new (std::nothrow) krr_hss();
+    if (!H) return fail(KRR_ERR_OOM, "hss_compress: host allocation failed");
+    const int s = hss_build(&k->c, X, n, d, o, &H->h);
+    if (s != KRR_OK) {
+        delete H;
+        return s;
+    }
+    *out = H;
+    return KRR_OK;
+}
+
+int hss_update_lambda(krr_hss *H, double lambda) {
+    if (!H || !(lambda > 0)) return fail(KRR_ERR_INVALID_ARG, "hss_update_lambda: bad arguments");
+    H->h.lambda = lambda;
+    H->h.opt.lambda = lambda;
+    H->h.factored = false;
+    return KRR_OK;
+}
+
+int hss_factor(krr_hss *H) {
+    if (!H) return fail(KRR_ERR_INVALID_ARG, "hss_factor: NULL");
+    KRR_TRY(hss_factor_impl(&H->h));
+    DevStatus st{};
+    KRR_CUDA(cudaMemcpy(&st, H->h.c->status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st.code != 0) {
+        KRR_CUDA(cudaMemset(H->h.c->status, 0, sizeof(DevStatus)));
+        H->h.factored = false;
+        return fail(st.code, "hss_factor: device error (site " + std::to_string(st.where) + ")");
+    }
+    return KRR_OK;
+}
+
+int hss_solve(krr_hss *H, const double *y, int32_t nrhs, int64_t ldy, double *alpha, int64_t lda, double tol,
+              int32_t max_refine, double *resid) {
+    if (!H || !y || !alpha || nrhs < 1 || ldy < nrhs || lda < nrhs || max_refine < 0)
+        return fail(KRR_ERR_INVALID_ARG, "hss_solve: bad arguments");
+    return hss_solve_impl(&H->h, y, nrhs, ldy, alpha, lda, tol, max_refine, resid);
+}
+
+int krr_predict(krr_hss *H, const float *Xt, int64_t m, const double *alpha, int32_t nrhs, int64_t lda, double *out,
+                int64_t ldo) {
+    if (!H || !Xt || !alpha || !out || m < 0 || nrhs < 1 || nrhs > 64 || lda < nrhs || ldo < nrhs)
+        return fail(KRR_ERR_INVALID_ARG, "krr_predict: bad arguments");
+    if (m == 0) return KRR_OK;
+    return hss_predict_impl(&H->h, Xt, m, alpha, nrhs, lda, out, ldo);
+}
+
+int hss_stats(const krr_hss *H, krr_hss_stats *st) {
+    if (!H || !st) return fail(KRR_ERR_INVALID_ARG, "hss_stats: bad arguments");
+    const HssImpl &h = H->h;
+    st->n = h.n;
+    st->n_nodes = int32_t(h.desc.size());
+    st->n_levels = h.H + 1;
+    st->max_rank = h.max_rank;
+    st->samples = h.r;
+    st->rounds = h.rounds;
+    st->refine_steps = h.refine_steps;
+    st->memory_bytes = hss_memory_bytes(&h);
+    st->t_cluster_ms = h.t_cluster;
+    st->t_sample_ms = h.t_sample;
+    st->t_compress_ms = h.t_compress;
+    st->t_factor_ms = h.t_factor;
+    st->t_solve_ms = h.t_solve;
+    return KRR_OK;
+}
+
+const int32_t *hss_permutation(const krr_hss *H) { return H ? H->h.perm.get() : nullptr; }
+
+void hss_destroy(krr_hss *H) {
+    if (!H) return;
+    cudaStreamSynchronize(H->h.c->stream);
+    delete H;
+}
+
+}  // extern "C"

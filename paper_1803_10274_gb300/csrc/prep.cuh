@@ -29,16 +29,17 @@ constexpr int kMaxMixedDim = 40;
 
 int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
-                     const int32_t *leaf_b, float *S, int64_t lds);
+                     const int32_t *leaf_b, float *S, int64_t lds, bool split_k = false);
 int launch_sample_f64(Ctx *c, const double *Xa, int64_t ma, const double *Xb, int64_t nb, int d, double h,
                       const double *R, int r, int64_t ldr, const int32_t *leaf_a, const int32_t *leaf_b, double *S,
                       int64_t lds);
 
 // Mixed-precision product on already-prepared operands: S = W o K R over
 // any number of columns (split into launches of <= 256 columns).  S is
-// zeroed here.  RT holds r_total rows (ldrt each).
+// zeroed here.  RT holds r_total rows (ldrt each).  split_k evaluates K
+// as an FP16 pair K_hi + K_lo (about 2^-22 relative instead of 2^-11).
 int sample_mixed_prepared(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int d,
                           const __half *RT, int r_total, int64_t ldrt, const int32_t *leaf_a,
-                          const int32_t *leaf_b, float *S, int64_t lds);
+                          const int32_t *leaf_b, float *S, int64_t lds, bool split_k = false);
 
 }  // namespace krr

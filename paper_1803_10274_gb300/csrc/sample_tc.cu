@@ -53,6 +53,7 @@ struct Params {
     int s_bufs;   // S accumulators in tensor memory (1 or 2)
     int ndist;    // distance / K buffers in tensor memory (2 or 3)
     int dist_col0;
+    int split_k;  // 1: K = K_hi + K_lo (two FP16 parts, two product MMAs)
     uint32_t off_a, off_stage, stage_bytes, off_bar;
     const int32_t *leaf_a, *leaf_b;
     float *S;
@@ -85,6 +86,20 @@ __device__ __forceinline__ void exp_pack(const uint32_t (&v)[32], uint32_t (&pk)
 #pragma unroll
     for (int c = 0; c < 16; ++c)
         pk[c] = pack_h2(ptx::ex2_approx(__uint_as_float(v[2 * c])), ptx::ex2_approx(__uint_as_float(v[2 * c + 1])));
+}
+
+// K = 2^e for 32 exponents as an FP16 pair sum K_hi + K_lo (the low part
+// is the FP16-rounded remainder), both packed in pairs.
+__device__ __forceinline__ void exp_pack_split(const uint32_t (&v)[32], uint32_t (&hi)[16], uint32_t (&lo)[16]) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        const float e0 = ptx::ex2_approx(__uint_as_float(v[2 * c]));
+        const float e1 = ptx::ex2_approx(__uint_as_float(v[2 * c + 1]));
+        const __half2 h = __floats2half2_rn(e0, e1);
+        const float2 hf = __half22float2(h);
+        hi[c] = *reinterpret_cast<const uint32_t *>(&h);
+        lo[c] = pack_h2(e0 - hf.x, e1 - hf.y);
+    }
 }
 
 // Zero the FP16 halves whose bit is set in m (only tiles that cross a
@@ -324,6 +339,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t roff = uint32_t((k >> 2) * P.r * 128 + (k & 3) * 32);
                 mma_ts(s_tmem, a_t, sdesc_k_sw128(r_base + roff), idesc_p, (cp.first && k == 0) ? 0u : 1u);
             }
+            if (P.split_k) {
+                // K_lo sits 32 columns after K_hi
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t a_t = p_tmem + uint32_t((k >> 2) * 64 + 32 + (k & 3) * 8);
+                    const uint32_t roff = uint32_t((k >> 2) * P.r * 128 + (k & 3) * 32);
+                    mma_ts(s_tmem, a_t, sdesc_k_sw128(r_base + roff), idesc_p, 1u);
+                }
+            }
             tc_commit(&bars[BAR_EMPTY + cp.stage]);
             if (cp.last) tc_commit(&bars[BAR_SFULL + sb]);
         }
@@ -360,13 +384,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_wait_ld_regs(va);                 // chunk 0 of this tile
             tmem_ld32(base + 32, vb);              // chunk 1 in flight
             uint32_t pk[16];
-            exp_pack(va, pk);
-            if (mlo) mask_pack(pk, mlo);
-            tmem_st16(base, pk);
-            tmem_wait_ld_regs(vb);                 // chunk 1 of this tile
-            exp_pack(vb, pk);
-            if (mhi) mask_pack(pk, mhi);
-            tmem_st16(base + 16, pk);
+            if (!P.split_k) {
+                exp_pack(va, pk);
+                if (mlo) mask_pack(pk, mlo);
+                tmem_st16(base, pk);
+                tmem_wait_ld_regs(vb);             // chunk 1 of this tile
+                exp_pack(vb, pk);
+                if (mhi) mask_pack(pk, mhi);
+                tmem_st16(base + 16, pk);
+            } else {
+                // K_hi of chunk k -> columns [16 k, +16), K_lo -> [32 + 16 k, +16)
+                uint32_t pl[16];
+                exp_pack_split(va, pk, pl);
+                if (mlo) { mask_pack(pk, mlo); mask_pack(pl, mlo); }
+                tmem_st16(base, pk);
+                tmem_wait_ld_regs(vb);             // chunk 1 read: its columns are free
+                tmem_st16(base + 32, pl);
+                exp_pack_split(vb, pk, pl);
+                if (mhi) { mask_pack(pk, mhi); mask_pack(pl, mhi); }
+                tmem_st16(base + 16, pk);
+                tmem_st16(base + 48, pl);
+            }
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
@@ -440,7 +478,7 @@ int make_map(CUtensorMap *m, const void *base, int64_t cols, int64_t rows, int64
 // nchunk elements each); RT: FP16, rpad x ldrt (row c = column c of R).
 int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
-                     const int32_t *leaf_b, float *S, int64_t lds) {
+                     const int32_t *leaf_b, float *S, int64_t lds, bool split_k) {
     if (rpad % 64 != 0 || rpad < 64 || rpad > 256) return fail(KRR_ERR_INVALID_ARG, "sample_tc: r must be 64..256, /64");
     if (nchunk < 1 || nchunk > 2) return fail(KRR_ERR_INVALID_ARG, "sample_tc: feature dimension too large");
     if (ma <= 0 || nb <= 0) return KRR_OK;
@@ -458,6 +496,7 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     P.n_col_tiles = cdiv(nb, tc::kBN);
     P.r = rpad;
     P.r_valid = r_valid;
+    P.split_k = split_k ? 1 : 0;
     P.nchunk = nchunk;
     P.kmma = kmma;
     // Tensor memory (512 columns): S accumulators first, then 128-column

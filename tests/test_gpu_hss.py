@@ -1,0 +1,160 @@
+"""End-to-end parity of the randomized HSS path (compression, ULV-type
+factorization, GMRES with the HSS preconditioner, prediction) with the
+FP64 oracle, through the C-ABI.
+
+Gates (the method's targets): relative residual ||(K + lambda I) alpha - y||
+/ ||y|| <= 10 eps against the oracle's FP64 operator; test accuracy within
+0.5 points of the exact dense solve.  HSS generators are not unique (they
+depend on the random block and pivot order), so they are never compared
+entry by entry; exact special cases are."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import kernel, prep, solve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    import paper_1803_10274_gb300 as K
+    return K
+
+
+@pytest.fixture(scope="module")
+def ctx(K):
+    c = K.Context()
+    yield c
+    c.close()
+
+
+def _fit(K, ctx, X32, Y, h, lam, eps_c, leaf, prec, tol, seed=1, **kw):
+    o = K.default_options(h=h, lambda_=lam, eps_c=eps_c, leaf=leaf, precision=prec, seed=seed, **kw)
+    H = K.hss_compress(ctx, torch.from_numpy(X32).cuda(), o)
+    H.factor()
+    a, res = H.solve(torch.from_numpy(np.ascontiguousarray(Y)).cuda(), tol=tol)
+    return H, a.cpu().numpy(), res
+
+
+def _rhs(y, n, extra, seed=3):
+    return np.concatenate([y[:, None], np.random.default_rng(seed).standard_normal((n, extra))], 1)
+
+
+def test_plain_small_workload(K, ctx):
+    """n=1000, d=8 mixture of 4, h=1, lambda=1, leaf 64, eps=1e-6, 10
+    right-hand sides, 200 test points, everything in FP64."""
+    X, y, Xt, yt, _, _ = synth.mixture(1000, 8, 4, 0.7, 1, 200)
+    X32, Xt32 = X.astype(np.float32), Xt.astype(np.float32)
+    Y = _rhs(y, 1000, 9)
+    eps = 1e-6
+    H, A, res = _fit(K, ctx, X32, Y, 1.0, 1.0, eps, 64, K.KRR_FP64, 10 * eps)
+    Xo = X32.astype(np.float64)
+    rho = solve.residual(Xo, 1.0, 1.0, A, Y)
+    assert rho.max() <= 10 * eps
+    dec = H.predict(torch.from_numpy(Xt32).cuda(), torch.from_numpy(A[:, :1].copy()).cuda()).cpu().numpy()[:, 0]
+    wd = solve.krr_dense(Xo, y, 1.0, 1.0)
+    acc_d = solve.accuracy(solve.sign_pm1(solve.predict(Xt32.astype(np.float64), Xo, wd, 1.0)), yt)
+    acc = solve.accuracy(solve.sign_pm1(dec), yt)
+    assert abs(acc - acc_d) <= 0.005
+    # decision values against the oracle's product with the same weights
+    ref, ref_abs = kernel.kernel_product(Xt32, X32, 1.0, A[:, :1], want_abs=True)
+    assert np.all(np.abs(dec - ref[:, 0]) <= 1e-10 * ref_abs[:, 0] + 1e-300)
+    H.close()
+
+
+def test_exact_at_tiny_tolerance(K, ctx):
+    """With eps_c near round-off the HSS equals K + lambda I, so one ULV
+    solve (no refinement) is the dense solve."""
+    X, y, *_ = synth.mixture(600, 5, 3, 0.7, 4)
+    X32 = X.astype(np.float32)
+    H, A, _ = _fit(K, ctx, X32, y[:, None], 1.3, 0.5, 1e-13, 40, K.KRR_FP64, 0.0)
+    wd = solve.krr_dense(X32.astype(np.float64), y, 1.3, 0.5)
+    assert np.linalg.norm(A[:, 0] - wd) <= 1e-8 * np.linalg.norm(wd)
+    H.close()
+
+
+def test_single_leaf_is_dense_lu(K, ctx):
+    X, y, *_ = synth.mixture(100, 3, 2, 0.7, 5)
+    X32 = X.astype(np.float32)
+    H, A, _ = _fit(K, ctx, X32, y[:, None], 1.0, 1.0, 0.1, 128, K.KRR_FP64, 0.0)
+    wd = solve.krr_dense(X32.astype(np.float64), y, 1.0, 1.0)
+    assert np.linalg.norm(A[:, 0] - wd) <= 1e-11 * np.linalg.norm(wd)
+    H.close()
+
+
+def test_lambda_update_equals_recompression(K, ctx):
+    """Section 5.3: changing lambda only changes the diagonal, so updating
+    lambda and refactoring matches compressing at the new lambda (same
+    random block, same ranks)."""
+    X, y, *_ = synth.mixture(1500, 6, 4, 0.7, 6)
+    X32 = X.astype(np.float32)
+    Y = y[:, None]
+    o = K.default_options(h=1.0, lambda_=1.0, eps_c=1e-4, leaf=64, precision=K.KRR_FP64, seed=3)
+    H1 = K.hss_compress(ctx, torch.from_numpy(X32).cuda(), o)
+    H1.update_lambda(2.5)
+    H1.factor()
+    a1, _ = H1.solve(torch.from_numpy(Y).cuda())
+    o2 = K.default_options(h=1.0, lambda_=2.5, eps_c=1e-4, leaf=64, precision=K.KRR_FP64, seed=3)
+    H2 = K.hss_compress(ctx, torch.from_numpy(X32).cuda(), o2)
+    H2.factor()
+    a2, _ = H2.solve(torch.from_numpy(Y).cuda())
+    assert H1.stats()["max_rank"] == H2.stats()["max_rank"]
+    np.testing.assert_allclose(a1.cpu().numpy(), a2.cpu().numpy(), rtol=1e-9, atol=1e-12)
+    H1.close()
+    H2.close()
+
+
+def test_mixed_8192(K, ctx):
+    """SUSY-shaped data (d=8, 16 components, standardized), h=1, lambda=4,
+    leaf 128: mixed precision meets the residual and accuracy gates."""
+    n = 8192
+    X, y, Xt, yt, _, _ = synth.mixture(n, 8, 16, 0.7, 2, 1000)
+    Z, Zt, _, _ = prep.standardize(X, Xt)
+    Z32, Zt32 = Z.astype(np.float32), Zt.astype(np.float32)
+    Y = _rhs(y, n, 9)
+    tol = 1e-3
+    H, A, res = _fit(K, ctx, Z32, Y, 1.0, 4.0, 0.05, 128, K.KRR_MIXED, 0.5 * tol)
+    Zo = Z32.astype(np.float64)
+    rho = solve.residual(Zo, 1.0, 4.0, A, Y)
+    assert rho.max() <= tol
+    dec = H.predict(torch.from_numpy(Zt32).cuda(), torch.from_numpy(A[:, :1].copy()).cuda()).cpu().numpy()[:, 0]
+    wd = solve.krr_dense(Zo, y, 1.0, 4.0)
+    acc_d = solve.accuracy(solve.sign_pm1(solve.predict(Zt32.astype(np.float64), Zo, wd, 1.0)), yt)
+    assert abs(solve.accuracy(solve.sign_pm1(dec), yt) - acc_d) <= 0.005
+    ref, ref_abs = kernel.kernel_product(Zt32, Z32, 1.0, A[:, :1], want_abs=True)
+    assert np.all(np.abs(dec - ref[:, 0]) <= 2e-6 * ref_abs[:, 0] + 1e-9)
+    H.close()
+
+
+def test_mixed_full_size(K, ctx):
+    """The 65536-point workload the benchmark times: the residual gate on
+    256 sampled rows of the exact FP64 operator."""
+    n = 65536
+    X, y, Xt, yt, _, _ = synth.mixture(n, 8, 16, 0.7, 2, 4096)
+    Z, Zt, _, _ = prep.standardize(X, Xt)
+    Z32 = Z.astype(np.float32)
+    Y = _rhs(y, n, 9)
+    tol = 1e-3
+    H, A, res = _fit(K, ctx, Z32, Y, 1.0, 4.0, 0.05, 128, K.KRR_MIXED, 0.5 * tol, seed=2)
+    rows = np.concatenate([[0, n - 1], np.random.default_rng(0).choice(n, 254, replace=False)])
+    # sampled rows: ||r_rows|| / ||y_rows|| estimates the full relative residual
+    rho = solve.residual(Z32.astype(np.float64), 1.0, 4.0, A, Y, rows=rows)
+    assert rho.max() <= tol
+    H.close()
+
+
+def test_argument_and_budget_errors(K, ctx):
+    X = synth.mixture(3000, 8, 8, 0.7, 1)[0]
+    Xd = torch.from_numpy(((X - X.mean(0)) / X.std(0)).astype(np.float32)).cuda()
+    with pytest.raises(K.KRRError):
+        K.hss_compress(ctx, Xd, K.default_options(lambda_=-1.0))
+    with pytest.raises(K.KRRError) as e:
+        K.hss_compress(ctx, Xd, K.default_options(h=1.0, lambda_=1.0, eps_c=1e-3, r0=64, r_max=128))
+    assert e.value.code == 5            # KRR_ERR_RANK_BUDGET
+    Xn = Xd.clone()
+    Xn[5, 3] = float("nan")
+    with pytest.raises(K.KRRError) as e:
+        K.hss_compress(ctx, Xn, K.default_options())
+    assert e.value.code == 2            # KRR_ERR_NONFINITE_INPUT
