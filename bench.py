@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 kernel-ridge-regression hot path.
+
+One step is one pass of the whole path on the SUSY-shaped workload
+(n = 65536 training points, d = 8, 16-component Gaussian mixture,
+standardized; h = 1, lambda = 4, leaf 128): feature standardization,
+recursive two-means ordering, randomized HSS compression (adaptive
+sampling through the fused tcgen05 kernel-times-block product), ULV-type
+factorization, HSS-preconditioned GMRES to the relative residual 10 eps
+(eps = 1e-4) for 10 right-hand sides, and prediction of 4096 test points.
+
+Reported (one JSON line on rank 0): seconds per step (mixed precision),
+the FP64 "plain" GPU path on the same step, the fused sampling kernel's
+algorithmic TFLOP/s against the measured tensor peak, an end-to-end time
+through host buffers, and the CPU oracle's time on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kernel-sampling TFLOP/s and KRR compress+solve sec at n=65536: mixed vs FP64 plain"
+WL = dict(n=65536, d=8, comps=16, sigma=0.7, seed=2, h=1.0, lam=4.0, leaf=128, eps=1e-4, eps_c=0.05, r0=64,
+          nrhs=10, m_test=4096)
+WORKLOAD = ("SUSY-shaped synthetic Gaussian mixture (16 components, d=8, standardized), n=65536 train / 4096 test; "
+            "h=1, lambda=4, leaf 128, eps=1e-4 (GMRES to relative residual 5e-4 <= 10 eps), HSS eps_c=0.05, "
+            "r0=64 adaptive, 10 right-hand sides")
+CPU_SAMPLE_N = 8192
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _inputs():
+    import synth
+    X, y, Xt, yt, _, _ = synth.mixture(WL["n"], WL["d"], WL["comps"], WL["sigma"], WL["seed"], WL["m_test"])
+    Y = np.concatenate([y[:, None], np.random.default_rng(3).standard_normal((WL["n"], WL["nrhs"] - 1))], 1)
+    return X.astype(np.float32), Xt.astype(np.float32), np.ascontiguousarray(Y), yt
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+        self.f = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        try:
+            rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        except Exception:
+            return None
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args):
+    import torch
+    import paper_1803_10274_gb300 as K
+    from paper_1803_10274_gb300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    peaks, peak_src = _peaks()
+    ctx = K.Context()
+    stream = ctx.stream
+    X, Xt, Y, yt = _inputs()
+    Xd, Xtd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Xt).cuda(), torch.from_numpy(Y).cuda()
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    tol = 0.5 * 10 * WL["eps"]
+
+    def opts(prec):
+        return K.default_options(h=WL["h"], lambda_=WL["lam"], eps_c=WL["eps_c"], leaf=WL["leaf"], precision=prec,
+                                 seed=WL["seed"], r0=WL["r0"])
+
+    def step(prec, Xs, Xts, Ys):
+        K.krr_standardize(ctx, Xs, Xts)
+        H = K.hss_compress(ctx, Xs, opts(prec))
+        H.factor()
+        a, res = H.solve(Ys, tol=tol, max_refine=200)
+        dec = H.predict(Xts, a[:, :1].contiguous())
+        st = H.stats()
+        H.close()
+        return a, dec, res, st
+
+    def timed_step(prec):
+        Xs, Xts = Xd.clone(), Xtd.clone()
+        _flush_l2(l2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a, dec, res, st = step(prec, Xs, Xts, Yd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, a, dec, res, st
+
+    for _ in range(args.warmup):
+        timed_step(K.KRR_MIXED)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = _lib.lib().krr_launch_count()
+    times, last = [], None
+    with Clocks(dev) as clk:
+        for _ in range(args.steps):
+            t, a, dec, res, st = timed_step(K.KRR_MIXED)
+            times.append(t)
+            last = (a, dec, res, st)
+    launches = (_lib.lib().krr_launch_count() - l0) // max(args.steps, 1)
+    t_step = sum(times) / len(times)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    a, dec, res, st = last
+    acc = float(np.mean(np.where(dec.cpu().numpy()[:, 0] >= 0, 1.0, -1.0) == yt))
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- fused sampling kernel alone: algorithmic TFLOP/s (CUDA events on the library's stream)
+    Xs = Xd.clone()
+    K.krr_standardize(ctx, Xs)
+    samp = {}
+    n, d = WL["n"], WL["d"]
+    for r in (64, 256):
+        R = torch.from_numpy(np.random.default_rng(7).standard_normal((n, r)).astype(np.float16).astype(np.float32)).cuda()
+        S = torch.empty(n, r, device="cuda")
+        for _ in range(3):
+            K.krr_sample(ctx, Xs, Xs, WL["h"], 0.0, R, S=S)
+        ts = []
+        for _ in range(5):
+            _flush_l2(l2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            K.krr_sample(ctx, Xs, Xs, WL["h"], 0.0, R, S=S)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(ts)
+        samp[r] = (2.0 * n * n * (d + r) / t / 1e12, t)
+    ach, tk = samp[256]
+    peak = float(peaks["bf16_tflops"])
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("sample_tc_kernel_r256_bytes_per_launch")
+    except Exception:
+        pass
+
+    # ---- end to end through host buffers (H2D inputs, D2H weights + predictions inside the timed region)
+    Xh = torch.from_numpy(X).pin_memory()
+    Xth = torch.from_numpy(Xt).pin_memory()
+    Yh = torch.from_numpy(Y).pin_memory()
+    ah = torch.empty((n, WL["nrhs"]), dtype=torch.float64).pin_memory()
+    dh = torch.empty((WL["m_test"], 1), dtype=torch.float64).pin_memory()
+    e_times = []
+    for it in range(max(1, min(args.steps, 2)) + 1):
+        _flush_l2(l2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xs = Xh.to("cuda", non_blocking=True)
+        Xts = Xth.to("cuda", non_blocking=True)
+        Ys = Yh.to("cuda", non_blocking=True)
+        a, dec, res, st2 = step(K.KRR_MIXED, Xs, Xts, Ys)
+        ah.copy_(a, non_blocking=True)
+        dh.copy_(dec, non_blocking=True)
+        torch.cuda.synchronize()
+        if it > 0:
+            e_times.append(time.perf_counter() - t0)
+    e2e = sum(e_times) / len(e_times)
+    h2d = X.nbytes + Xt.nbytes + Y.nbytes
+    d2h = ah.numel() * 8 + dh.numel() * 8
+
+    # ---- FP64 plain path, same step (one run: it is slow)
+    plain = None
+    if not args.no_plain:
+        tp, ap, decp, resp, stp = timed_step(K.KRR_FP64)
+        plain = {"seconds": tp, "resid_gpu": resp, "max_rank": stp["max_rank"], "samples": stp["samples"],
+                 "gmres_iters": stp["refine_steps"]}
+
+    # ---- CPU oracle on a bounded sample
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline(X)
+
+    t_sample_frac = st["t_sample_ms"] / 1e3 / t_step if t_step > 0 else None
+    out = {
+        "metric": METRIC,
+        "value": t_step,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_step,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f16 tensor-core products with f32 accumulation; f32 ID/ULV/GMRES preconditioner; f64 residuals",
+        "data": "synthetic (seeded Gaussian mixture, SUSY-shaped)",
+        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "quality": {"resid_gpu": res, "test_accuracy": acc, "max_rank": st["max_rank"], "samples": st["samples"],
+                    "rounds": st["rounds"], "gmres_iters": st["refine_steps"],
+                    "hss_memory_MB": st["memory_bytes"] / 1e6},
+        "phases_ms": {k: st[k] for k in ("t_cluster_ms", "t_sample_ms", "t_compress_ms", "t_factor_ms",
+                                         "t_solve_ms")},
+        "fp64_plain": plain,
+        "sampling": {"tflops_r64": samp[64][0], "ms_r64": 1e3 * samp[64][1], "tflops_r256": samp[256][0],
+                     "ms_r256": 1e3 * samp[256][1], "algorithmic_flops": "2 n^2 (d + r)",
+                     "share_of_step": t_sample_frac},
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "traffic": traffic,
+                     "note": "fused sampling kernel, n=65536, d=8, r=256, one launch timed alone (burst peak, %s)"
+                             % ("of " + peak_src)},
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(X):
+    """The FP64 oracle's dense KRR (kernel matrix + Cholesky solve) on the
+    first CPU_SAMPLE_N standardized points, extrapolated to n = 65536 (the
+    kernel build scales as n^2, the factorization and solve as n^3)."""
+    from oracle import kernel, prep, solve
+    n0 = CPU_SAMPLE_N
+    Z = prep.standardize(X[:n0].astype(np.float64))[0]
+    y = np.random.default_rng(1).standard_normal((n0, WL["nrhs"]))
+    t0 = time.perf_counter()
+    Kd = kernel.kernel_matrix(Z, Z, WL["h"])
+    t1 = time.perf_counter()
+    Kd[np.diag_indices(n0)] += WL["lam"]
+    solve.spd_solve(Kd, y)
+    t2 = time.perf_counter()
+    s = WL["n"] / n0
+    est = (t1 - t0) * s * s + (t2 - t1) * s ** 3
+    return {"value": est, "unit": "s", "cores": int(kernel.num_threads()), "kind": "oracle",
+            "sample": "dense FP64 KRR (C kernel build + LAPACK Cholesky solve, 10 RHS) at n=%d, measured %.2f s, "
+                      "extrapolated to n=65536 (build x%.0f, factor/solve x%.0f)" % (n0, t2 - t0, s * s, s ** 3)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    X, Xt, Y, yt = _inputs()
+    for _ in range(args.warmup):
+        cpu_baseline(X)
+    vals = [cpu_baseline(X) for _ in range(args.steps)]
+    v = sum(c["value"] for c in vals) / len(vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (seeded Gaussian mixture, SUSY-shaped)", "impl": "reference",
+           "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -78,6 +78,10 @@ void krr_destroy(krr_ctx *ctx);
 /* Message for the last failing call on this thread ("" if none). */
 const char *krr_last_error(void);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (a diagnostic for profiling and benchmarks). */
+long long krr_launch_count(void);
+
 /* Wait for the context's stream and return (and clear) any latched device
  * error.  Synchronizes. */
 int krr_sync(krr_ctx *ctx);

@@ -49,6 +49,7 @@ SIGNATURES = {
     "krr_create": (i32, [ctypes.POINTER(P), ctypes.POINTER(krr_allocator), P]),
     "krr_destroy": (None, [P]),
     "krr_last_error": (ctypes.c_char_p, []),
+    "krr_launch_count": (ctypes.c_longlong, []),
     "krr_sync": (i32, [P]),
     "krr_standardize": (i32, [P, P, i64, i32, P, i64, P, P]),
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),

@@ -5,6 +5,7 @@ passed to the C library, errors become KRRError.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 
 import torch
@@ -16,6 +17,17 @@ __all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "krr_standardize", "k
            "krr_sample_f64", "krr_random_block", "HSS", "hss_compress", "default_options", "lib"]
 
 
+_shutting_down = [False]
+
+
+@atexit.register
+def _mark_shutdown():
+    # Handles still open at interpreter exit are not destroyed: their
+    # device memory goes back through callbacks into torch, which may
+    # already be finalized.  The process is ending; the driver reclaims it.
+    _shutting_down[0] = True
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -25,7 +37,7 @@ def _need(t, dtype, name, dims=2):
         return
     if not (t.is_cuda and t.dtype == dtype and t.dim() == dims):
         raise ValueError("%s must be a %d-D CUDA %s tensor" % (name, dims, dtype))
-    if dims == 2 and t.stride(1) != 1:
+    if dims == 2 and t.shape[1] > 1 and t.stride(1) != 1:
         raise ValueError("%s must be row-major (unit column stride)" % name)
 
 
@@ -62,7 +74,8 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().krr_destroy(self.h)
+            if not _shutting_down[0]:
+                lib().krr_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -152,9 +165,10 @@ class HSS:
     def solve(self, y, tol=0.0, max_refine=100):
         """alpha (n x nrhs float64, original order) and the final residual."""
         _need(y, torch.float64, "y")
-        alpha = torch.empty_like(y)
+        y = y.contiguous()
+        alpha = torch.empty(y.shape, dtype=torch.float64, device=y.device)
         res = ctypes.c_double(-1.0)
-        check(lib().hss_solve(self.h, _ptr(y), y.shape[1], y.stride(0), _ptr(alpha), alpha.stride(0), tol,
+        check(lib().hss_solve(self.h, _ptr(y), y.shape[1], y.shape[1], _ptr(alpha), alpha.shape[1], tol,
                               max_refine, ctypes.byref(res)))
         return alpha, res.value
 
@@ -177,7 +191,8 @@ class HSS:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().hss_destroy(self.h)
+            if not _shutting_down[0]:
+                lib().hss_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,5 +1,6 @@
 // C-ABI entry points: context, errors, standardization, the fused
 // products and the random block.  The HSS entry points live in hss_api.cu.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -9,6 +10,9 @@
 namespace krr {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 int fail(int code, const std::string &msg) {
@@ -63,6 +67,8 @@ using namespace krr;
 extern "C" {
 
 const char *krr_last_error(void) { return g_last_error.c_str(); }
+
+long long krr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int krr_create(krr_ctx **out, const krr_allocator *alloc, void *stream) {
     if (!out) return fail(KRR_ERR_INVALID_ARG, "krr_create: out is NULL");

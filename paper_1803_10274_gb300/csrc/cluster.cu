@@ -364,7 +364,7 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
     if (!mx.get() || !bad.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
     KRR_CUDA(cudaMemsetAsync(mx.get(), 0, 4, st));
     KRR_CUDA(cudaMemsetAsync(bad.get(), 0, 4, st));
-    absmax_kernel<<<std::min<int64_t>(1024, cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, mx.get(), bad.get());
+    { absmax_kernel<<<std::min<int64_t>(1024, cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, mx.get(), bad.get()); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     unsigned int hmx = 0;
     int hbad = 0;
@@ -393,7 +393,7 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
     if (!q.get() || !q2.get() || !pa.get() || !pb.get() || !node_of.get() || !zflag.get() || !label.get() ||
         !zscan.get() || !bsum.get())
         return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
-    quantize_kernel<<<unsigned(cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, std::ldexp(1.0, kexp), q.get());
+    { quantize_kernel<<<unsigned(cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, std::ldexp(1.0, kexp), q.get()); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     {
         std::vector<int32_t> idp(n);
@@ -425,27 +425,27 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         KRR_CUDA(cudaMemcpyAsync(db.get(), hb.data(), nn * 8, cudaMemcpyHostToDevice, st));
         KRR_CUDA(cudaMemcpyAsync(ds.get(), hs.data(), nn * 8, cudaMemcpyHostToDevice, st));
         KRR_CUDA(cudaMemsetAsync(node_of.get(), 0xFF, n * 4, st));
-        mark_nodes_kernel<<<nn, kTB, 0, st>>>(nn, db.get(), ds.get(), node_of.get());
-        seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dns.get(), seed);
+        { mark_nodes_kernel<<<nn, kTB, 0, st>>>(nn, db.get(), ds.get(), node_of.get()); ::krr::count_launch(); }
+        { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dns.get(), seed); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         for (int iter = 0; iter <= kMaxIter; ++iter) {
             KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
-            assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(qc, d, n, node_of.get(), dns.get(), label.get());
-            update_kernel<<<unsigned(cdiv(nn, 128)), 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get());
+            { assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(qc, d, n, node_of.get(), dns.get(), label.get()); ::krr::count_launch(); }
+            { update_kernel<<<unsigned(cdiv(nn, 128)), 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             int hrun = 0;
             KRR_CUDA(cudaMemcpyAsync(&hrun, running.get(), 4, cudaMemcpyDeviceToHost, st));
             KRR_CUDA(cudaStreamSynchronize(st));
             if (hrun == 0) break;
         }
-        finalize_labels_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(n, node_of.get(), db.get(), ds.get(),
-                                                                        dns.get(), label.get(), zflag.get());
+        { finalize_labels_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(n, node_of.get(), db.get(), ds.get(),
+                                                                        dns.get(), label.get(), zflag.get()); ::krr::count_launch(); }
         const int64_t nblk = cdiv(n, kTB);
-        scan_blocks_kernel<<<unsigned(nblk), kTB, 0, st>>>(zflag.get(), n, zscan.get(), bsum.get());
-        scan_sums_kernel<<<1, kTB, 0, st>>>(bsum.get(), nblk);
-        scan_add_kernel<<<unsigned(nblk), kTB, 0, st>>>(zscan.get(), n, bsum.get(), nullptr);
-        partition_kernel<<<unsigned(nblk), kTB, 0, st>>>(n, d, node_of.get(), db.get(), ds.get(), label.get(),
-                                                          zscan.get(), zflag.get(), qc, pc, qn, pn, dcnt0.get());
+        { scan_blocks_kernel<<<unsigned(nblk), kTB, 0, st>>>(zflag.get(), n, zscan.get(), bsum.get()); ::krr::count_launch(); }
+        { scan_sums_kernel<<<1, kTB, 0, st>>>(bsum.get(), nblk); ::krr::count_launch(); }
+        { scan_add_kernel<<<unsigned(nblk), kTB, 0, st>>>(zscan.get(), n, bsum.get(), nullptr); ::krr::count_launch(); }
+        { partition_kernel<<<unsigned(nblk), kTB, 0, st>>>(n, d, node_of.get(), db.get(), ds.get(), label.get(),
+                                                          zscan.get(), zflag.get(), qc, pc, qn, pn, dcnt0.get()); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         std::vector<int64_t> hc0(nn);
         KRR_CUDA(cudaMemcpyAsync(hc0.data(), dcnt0.get(), nn * 8, cudaMemcpyDeviceToHost, st));

@@ -86,6 +86,9 @@ __device__ __forceinline__ void dev_fail(DevStatus *st, int code, int where) {
 }
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Count of kernel launches made by this library (all threads).
+void count_launch();
 inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 
 // --------------------------------------------------- Philox4x64-10 (device)

@@ -211,7 +211,7 @@ __device__ void lu_solve(int n, const T *A, int64_t lda, const int *ipiv, int nr
 // R12 (k x (m-k), row-major, ldt = m - k) is written to Tout.
 template <class T>
 __device__ int row_id(int m, int r, int rfull, T *W, int64_t ldw, T eps, T eps_abs, int *piv, T *norm2, T *Tout,
-                       int kmax) {
+                       int kmax, T *in_err) {
     __shared__ int s_k;
     extern __shared__ unsigned char dyn_smem_raw[];
     T *v = reinterpret_cast<T *>(dyn_smem_raw);  // Householder vector, length r
@@ -229,6 +229,9 @@ __device__ int row_id(int m, int r, int rfull, T *W, int64_t ldw, T eps, T eps_a
     }
     if (threadIdx.x == 0) s_k = 0;
     __syncthreads();
+    T tot0 = T(0);
+    for (int i = threadIdx.x; i < m; i += kNT) tot0 += norm2[i];
+    tot0 = sum_block(tot0);
     T r11 = T(0);
     const int jmax = min(min(m, r), kmax);
     for (int j = 0; j < jmax; ++j) {
@@ -287,6 +290,12 @@ __device__ int row_id(int m, int r, int rfull, T *W, int64_t ldw, T eps, T eps_a
     }
     __syncthreads();
     const int k = s_k;
+    // in-sample relative residual ||R22||_F / ||W||_F (trailing norms of the
+    // rows not taken)
+    T rest = T(0);
+    for (int i = k + threadIdx.x; i < m; i += kNT) rest += norm2[i];
+    rest = sum_block(rest);
+    if (in_err) *in_err = tot0 > T(0) ? sqrt(rest / tot0) : T(0);
     // T = R11^{-1} R12: one thread per redundant row c (column of R12)
     const int nr = m - k;
     for (int c = threadIdx.x; c < nr; c += kNT) {

@@ -47,7 +47,7 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
 namespace {
 
 constexpr int kHoldOut = 16;  // sample columns held out of each ID for its error test
-constexpr double kTestFactor = 3.0;  // held-out error allowed, relative to eps_c
+constexpr double kTestFactor = 2.0;  // held-out error allowed, relative to the in-sample error
 
 // Per-node descriptor of one level (offsets are element offsets into the
 // HSS arenas; -1 when unused).
@@ -145,12 +145,15 @@ __global__ void __launch_bounds__(cta::kNT) id_kernel(NodeDesc *nd, const NodeDe
     // the last kHoldOut sample columns are held out of the QR and measure
     // the decomposition's error on fresh random directions
     const int rid = r - kHoldOut;
-    const int k = cta::row_id<T>(m, rid, r, W, r, eps, eps_abs, piv, F + N.norm, F + N.tmat, kmax);
+    __shared__ T s_in_err;
+    const int k = cta::row_id<T>(m, rid, r, W, r, eps, eps_abs, piv, F + N.norm, F + N.tmat, kmax, &s_in_err);
     const T terr = cta::id_test_error<T>(m, k, W, r, F + N.tmat, rid, r);
+    __syncthreads();
     if (threadIdx.x == 0) {
         N.k = k;
         ranks[blockIdx.x] = k;
-        test_err[blockIdx.x] = float(terr);
+        test_err[2 * blockIdx.x] = float(terr);
+        test_err[2 * blockIdx.x + 1] = float(s_in_err);
     }
     // skeleton ids and skeleton samples (from the unmodified S_loc)
     const T *Sorig = N.is_leaf ? nullptr : F + N.sloc;
@@ -593,7 +596,7 @@ int id_sweep(HssImpl *H, bool &need_more) {
     if (H->IA.n < isize && !H->IA.reset(c, isize)) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
     if (!H->ddesc.get() && !H->ddesc.reset(c, H->desc.size())) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
     DBuf<int> dranks(c, H->desc.size());
-    DBuf<float> derr(c, H->desc.size());
+    DBuf<float> derr(c, 2 * H->desc.size());
     if (!dranks.get() || !derr.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
     H->max_test_err = 0;
     std::vector<NodeDesc> lvdesc;
@@ -620,8 +623,8 @@ int id_sweep(HssImpl *H, bool &need_more) {
         KRR_CUDA(cudaMemcpyAsync(dl.get(), lvdesc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
         const bool is_root_level = (h == H->H);
         if (h > 0)
-            extract_b_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), X, H->d, inv2h2, F, H->IA.get(),
-                                                                H->ddesc.get());
+            { extract_b_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), X, H->d, inv2h2, F, H->IA.get(),
+                                                                H->ddesc.get()); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         if (is_root_level) break;  // the root needs B only
         const size_t smem = size_t(H->r) * sizeof(T);
@@ -630,21 +633,24 @@ int id_sweep(HssImpl *H, bool &need_more) {
             KRR_CUDA(cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
             attr = true;
         }
-        id_kernel<T><<<nn, cta::kNT, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, H->r, F,
+        { id_kernel<T><<<nn, cta::kNT, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, H->r, F,
                                                         H->IA.get(), T(H->opt.eps_c), T(H->opt.eps_abs), kmax,
-                                                        dranks.get(), derr.get(), c->status);
+                                                        dranks.get(), derr.get(), c->status); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         std::vector<int> hr(nn);
-        std::vector<float> he(nn);
+        std::vector<float> he(2 * nn);
         KRR_CUDA(cudaMemcpyAsync(hr.data(), dranks.get(), nn * 4, cudaMemcpyDeviceToHost, c->stream));
-        KRR_CUDA(cudaMemcpyAsync(he.data(), derr.get(), nn * 4, cudaMemcpyDeviceToHost, c->stream));
+        KRR_CUDA(cudaMemcpyAsync(he.data(), derr.get(), 2 * nn * 4, cudaMemcpyDeviceToHost, c->stream));
         KRR_CUDA(cudaStreamSynchronize(c->stream));
         for (int a = 0; a < nn; ++a) {
             H->desc[lv[a]].k = hr[a];
             H->max_rank = std::max(H->max_rank, hr[a]);
-            H->max_test_err = std::max(H->max_test_err, double(he[a]));
+            const double e_test = he[2 * a], e_in = he[2 * a + 1];
+            H->max_test_err = std::max(H->max_test_err, e_test);
             if (hr[a] > H->r - kHoldOut - H->opt.p) need_more = true;
-            if (double(he[a]) > kTestFactor * H->opt.eps_c) need_more = true;
+            // under-sampled: the decomposition fits the sampled directions
+            // markedly better than fresh ones
+            if (e_test > kTestFactor * std::max(e_in, H->opt.eps_c)) need_more = true;
         }
         if (need_more) return KRR_OK;
     }
@@ -699,8 +705,8 @@ int factor(HssImpl *H) {
         DBuf<NodeDesc> dl(c, nn);
         if (!dl.get()) return fail(KRR_ERR_OOM, "hss_factor: out of memory");
         KRR_CUDA(cudaMemcpyAsync(dl.get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
-        factor_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), X, H->d, inv2h2, T(H->lambda), F,
-                                                         H->IA.get(), h == H->H ? 1 : 0, c->status);
+        { factor_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), X, H->d, inv2h2, T(H->lambda), F,
+                                                         H->IA.get(), h == H->H ? 1 : 0, c->status); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
     KRR_CUDA(cudaStreamSynchronize(c->stream));
@@ -723,19 +729,19 @@ int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64
         for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
         if (!dls[h].reset(c, nn)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
         KRR_CUDA(cudaMemcpyAsync(dls[h].get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
-        solve_up_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), yperm, ldy, nrhs, F,
-                                                           H->IA.get(), h == H->H ? 1 : 0);
+        { solve_up_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), yperm, ldy, nrhs, F,
+                                                           H->IA.get(), h == H->H ? 1 : 0); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
     for (int h = H->H; h >= 0; --h) {
         const int nn = int(H->by_height[h].size());
         if (!nn) continue;
         if (h < H->H)
-            solve_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F, H->IA.get(),
-                                                                 xperm, ldx);
+            { solve_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F, H->IA.get(),
+                                                                 xperm, ldx); ::krr::count_launch(); }
         else if (H->desc[H->root].is_leaf)  // single-leaf tree: the root's solve is the answer
-            root_leaf_out_kernel<T><<<1, cta::kNT, 0, c->stream>>>(dls[h].get(), nrhs, F, xperm, ldx);
-        scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F);
+            { root_leaf_out_kernel<T><<<1, cta::kNT, 0, c->stream>>>(dls[h].get(), nrhs, F, xperm, ldx); ::krr::count_launch(); }
+        { scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
     return KRR_OK;
@@ -757,16 +763,16 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
         DBuf<float> Rs(c, size_t(n) * cols), Sm(c, size_t(ma) * cols);
         DBuf<__half> RTs(c, size_t(rpad) * H->ldrt);
         if (!Rs.get() || !Sm.get() || !RTs.get()) return fail(KRR_ERR_OOM, "hss: out of memory");
-        split16_kernel<<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(V, n, nrhs, ldv, Rs.get(), cols);
+        { split16_kernel<<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(V, n, nrhs, ldv, Rs.get(), cols); ::krr::count_launch(); }
         KRR_TRY(transpose_half(c, Rs.get(), n, cols, cols, RTs.get(), rpad, H->ldrt));
         KRR_TRY(sample_mixed_prepared(c, XAa, ma, H->XB.get(), n, H->d, RTs.get(), cols, H->ldrt, nullptr, nullptr,
                                       Sm.get(), cols, true));
         if (y)
-            residual_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
-                y, ldy, Sm.get(), cols, 1, V, ldv, ma, nrhs, lambda, out, ldo, res_norms);
+            { residual_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
+                y, ldy, Sm.get(), cols, 1, V, ldv, ma, nrhs, lambda, out, ldo, res_norms); ::krr::count_launch(); }
         else
-            combine_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm.get(), cols, 1, V, ldv,
-                                                                                        lambda, ma, nrhs, out, ldo);
+            { combine_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm.get(), cols, 1, V, ldv,
+                                                                                        lambda, ma, nrhs, out, ldo); ::krr::count_launch(); }
     } else {
         DBuf<double> Sm(c, size_t(ma) * nrhs), Xa64;
         if (!Sm.get()) return fail(KRR_ERR_OOM, "hss: out of memory");
@@ -779,11 +785,11 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
         KRR_TRY(launch_sample_f64(c, Xa, ma, H->Xp64.get(), n, H->d, H->opt.h, V, nrhs, ldv, nullptr, nullptr,
                                   Sm.get(), nrhs));
         if (y)
-            residual_kernel<double><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
-                y, ldy, Sm.get(), nrhs, 0, V, ldv, ma, nrhs, lambda, out, ldo, res_norms);
+            { residual_kernel<double><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
+                y, ldy, Sm.get(), nrhs, 0, V, ldv, ma, nrhs, lambda, out, ldo, res_norms); ::krr::count_launch(); }
         else
-            combine_kernel<double><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm.get(), nrhs, 0, V, ldv,
-                                                                                         lambda, ma, nrhs, out, ldo);
+            { combine_kernel<double><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm.get(), nrhs, 0, V, ldv,
+                                                                                         lambda, ma, nrhs, out, ldo); ::krr::count_launch(); }
     }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
@@ -828,7 +834,7 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
         KRR_CUDA(cudaMemcpyAsync(db.get(), H->tb.data(), nn * 4, cudaMemcpyHostToDevice, c->stream));
         KRR_CUDA(cudaMemcpyAsync(de.get(), H->te.data(), nn * 4, cudaMemcpyHostToDevice, c->stream));
         KRR_CUDA(cudaMemcpyAsync(dl.get(), isl.data(), nn * 4, cudaMemcpyHostToDevice, c->stream));
-        leaf_id_kernel<<<nn, 128, 0, c->stream>>>(n, db.get(), de.get(), dl.get(), nn, H->leaf_of.get());
+        { leaf_id_kernel<<<nn, 128, 0, c->stream>>>(n, db.get(), de.get(), dl.get(), nn, H->leaf_of.get()); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         KRR_CUDA(cudaStreamSynchronize(c->stream));
     }
@@ -879,9 +885,9 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
         if (H->mixed()) {
             DBuf<float> bf(c, size_t(n) * nrhs), xf(c, size_t(n) * nrhs);
             if (!bf.get() || !xf.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
-            convert_kernel<double, float><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(b, n * nrhs, bf.get());
+            { convert_kernel<double, float><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(b, n * nrhs, bf.get()); ::krr::count_launch(); }
             KRR_TRY(ulv_solve<float>(H, bf.get(), nrhs, nrhs, xf.get(), nrhs));
-            convert_kernel<float, double><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(xf.get(), n * nrhs, x);
+            { convert_kernel<float, double><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(xf.get(), n * nrhs, x); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             return KRR_OK;
         }
@@ -908,7 +914,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
         const unsigned gd = unsigned(std::min<int64_t>(256, cdiv(nn, 256)));
         auto mdot = [&](const double *A, int nb, const double *B) -> int {
             KRR_CUDA(cudaMemsetAsync(dots.get(), 0, size_t(nb) * nrhs * sizeof(double), c->stream));
-            multidot_kernel<<<dim3(gd, nb), 256, nrhs * sizeof(double), c->stream>>>(A, nn, nb, B, n, nrhs, dots.get());
+            { multidot_kernel<<<dim3(gd, nb), 256, nrhs * sizeof(double), c->stream>>>(A, nn, nb, B, n, nrhs, dots.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             return KRR_OK;
         };
@@ -938,7 +944,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
             std::vector<double> inv(nrhs);
             for (int q = 0; q < nrhs; ++q) inv[q] = beta[q] > 0 ? 1.0 / beta[q] : 0.0;
             KRR_CUDA(cudaMemcpyAsync(sc.get(), inv.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
-            colscale_kernel<<<g1, 256, 0, c->stream>>>(V.get(), res.get(), sc.get(), n, nrhs);
+            { colscale_kernel<<<g1, 256, 0, c->stream>>>(V.get(), res.get(), sc.get(), n, nrhs); ::krr::count_launch(); }
             std::fill(Hm.begin(), Hm.end(), 0.0);
             std::fill(g.begin(), g.end(), 0.0);
             for (int q = 0; q < nrhs; ++q) g[size_t(q) * (mres + 1)] = beta[q];
@@ -963,7 +969,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
                         neg[e] = -hd2[e];
                     }
                     KRR_CUDA(cudaMemcpyAsync(coef.get(), neg.data(), neg.size() * 8, cudaMemcpyHostToDevice, c->stream));
-                    combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, j + 1, coef.get(), n, nrhs);
+                    { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, j + 1, coef.get(), n, nrhs); ::krr::count_launch(); }
                 }
                 KRR_TRY(mdot(Wv.get(), 1, Wv.get()));
                 std::vector<double> wn(nrhs);
@@ -996,7 +1002,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
                     est = std::max(est, std::fabs(gq[j + 1]) / ynrm[q]);
                 }
                 KRR_CUDA(cudaMemcpyAsync(sc.get(), inv2.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
-                colscale_kernel<<<g1, 256, 0, c->stream>>>(V.get() + int64_t(j + 1) * nn, Wv.get(), sc.get(), n, nrhs);
+                { colscale_kernel<<<g1, 256, 0, c->stream>>>(V.get() + int64_t(j + 1) * nn, Wv.get(), sc.get(), n, nrhs); ::krr::count_launch(); }
                 jdone = j + 1;
                 // stop a little below tol so the true residual also meets it
                 if (est <= 0.5 * tol) break;
@@ -1014,9 +1020,9 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
             }
             KRR_CUDA(cudaMemcpyAsync(coef.get(), yv.data(), size_t(jdone) * nrhs * 8, cudaMemcpyHostToDevice, c->stream));
             KRR_CUDA(cudaMemsetAsync(Wv.get(), 0, nn * sizeof(double), c->stream));
-            combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, jdone, coef.get(), n, nrhs);
+            { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, jdone, coef.get(), n, nrhs); ::krr::count_launch(); }
             KRR_TRY(ulv(Wv.get(), Zv.get()));
-            axpy_kernel<<<g1, 256, 0, c->stream>>>(ap.get(), Zv.get(), nn);
+            { axpy_kernel<<<g1, 256, 0, c->stream>>>(ap.get(), Zv.get(), nn); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
         }
         H->refine_steps = total_it;

@@ -59,13 +59,13 @@ int standardize(Ctx *c, float *X, int64_t n, int d, float *Xt, int64_t m, double
         if (!sb.reset(c, d)) return fail(KRR_ERR_OOM, "standardize: out of memory");
         sd = sb.get();
     }
-    col_stats_kernel<<<d, 256, 0, c->stream>>>(X, n, d, mu, sd);
+    { col_stats_kernel<<<d, 256, 0, c->stream>>>(X, n, d, mu, sd); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     if (Xt && m > 0) {
-        apply_standardize_kernel<<<unsigned(cdiv(m * d, 256)), 256, 0, c->stream>>>(Xt, m, d, mu, sd);
+        { apply_standardize_kernel<<<unsigned(cdiv(m * d, 256)), 256, 0, c->stream>>>(Xt, m, d, mu, sd); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
-    apply_standardize_kernel<<<unsigned(cdiv(n * d, 256)), 256, 0, c->stream>>>(X, n, d, mu, sd);
+    { apply_standardize_kernel<<<unsigned(cdiv(n * d, 256)), 256, 0, c->stream>>>(X, n, d, mu, sd); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
@@ -95,8 +95,8 @@ template <class Tin, class Tout>
 int gather_rows(Ctx *c, const Tin *src, int64_t lds, const int32_t *perm, int64_t n, int cols, Tout *dst,
                 int64_t ldd) {
     if (n * cols == 0) return KRR_OK;
-    gather_rows_kernel<Tin, Tout><<<unsigned(cdiv(n * cols, 256)), 256, 0, c->stream>>>(src, lds, perm, n, cols,
-                                                                                          dst, ldd);
+    { gather_rows_kernel<Tin, Tout><<<unsigned(cdiv(n * cols, 256)), 256, 0, c->stream>>>(src, lds, perm, n, cols,
+                                                                                          dst, ldd); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
@@ -104,8 +104,8 @@ template <class Tin, class Tout>
 int scatter_rows(Ctx *c, const Tin *src, int64_t lds, const int32_t *perm, int64_t n, int cols, Tout *dst,
                  int64_t ldd) {
     if (n * cols == 0) return KRR_OK;
-    scatter_rows_kernel<Tin, Tout><<<unsigned(cdiv(n * cols, 256)), 256, 0, c->stream>>>(src, lds, perm, n, cols,
-                                                                                           dst, ldd);
+    { scatter_rows_kernel<Tin, Tout><<<unsigned(cdiv(n * cols, 256)), 256, 0, c->stream>>>(src, lds, perm, n, cols,
+                                                                                           dst, ldd); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
@@ -123,7 +123,7 @@ __global__ void widen_kernel(const float *src, int64_t n, double *dst) {
 }
 int widen(Ctx *c, const float *src, int64_t n, double *dst) {
     if (n == 0) return KRR_OK;
-    widen_kernel<<<unsigned(cdiv(n, 256)), 256, 0, c->stream>>>(src, n, dst);
+    { widen_kernel<<<unsigned(cdiv(n, 256)), 256, 0, c->stream>>>(src, n, dst); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
@@ -189,7 +189,7 @@ __global__ void augment_kernel(const float *X, int64_t rows, int d, double c, in
 int augment(Ctx *c, const float *X, int64_t rows, int d, double h, int role, __half *out, int kpad) {
     if (rows == 0) return KRR_OK;
     const double cc = 1.4426950408889634 / (2.0 * h * h);  // log2(e) / (2 h^2)
-    augment_kernel<<<unsigned(cdiv(rows, 128)), 128, 0, c->stream>>>(X, rows, d, cc, role, out, kpad, c->status);
+    { augment_kernel<<<unsigned(cdiv(rows, 128)), 128, 0, c->stream>>>(X, rows, d, cc, role, out, kpad, c->status); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
@@ -215,7 +215,7 @@ __global__ void transpose_half_kernel(const float *R, int64_t n, int r, int64_t 
 
 int transpose_half(Ctx *c, const float *R, int64_t n, int r, int64_t ldr, __half *RT, int rpad, int64_t ldrt) {
     dim3 grid(unsigned(cdiv(ldrt, 32)), unsigned(cdiv(rpad, 32)));
-    transpose_half_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(R, n, r, ldr, RT, rpad, ldrt);
+    { transpose_half_kernel<<<grid, dim3(32, 8), 0, c->stream>>>(R, n, r, ldr, RT, rpad, ldrt); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
@@ -235,8 +235,8 @@ __global__ void add_lambda_kernel(T *S, int64_t lds, const T *R, int64_t ldr, in
 template <class T>
 int add_lambda(Ctx *c, T *S, int64_t lds, const T *R, int64_t ldr, int64_t n, int r, double lambda, bool round16) {
     if (lambda == 0.0 || n * r == 0) return KRR_OK;
-    add_lambda_kernel<T><<<unsigned(cdiv(n * r, 256)), 256, 0, c->stream>>>(S, lds, R, ldr, n, r, lambda,
-                                                                            round16 ? 1 : 0);
+    { add_lambda_kernel<T><<<unsigned(cdiv(n * r, 256)), 256, 0, c->stream>>>(S, lds, R, ldr, n, r, lambda,
+                                                                            round16 ? 1 : 0); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
@@ -281,9 +281,9 @@ int random_block(Ctx *c, int64_t n, int r, int col0, uint64_t seed, int precisio
     const int ng = (r + 3) / 4;
     const unsigned grid = unsigned(cdiv(n * ng, 256));
     if (precision == KRR_FP64)
-        random_block_kernel<double><<<grid, 256, 0, c->stream>>>(n, r, col0, seed, 0, static_cast<double *>(out), ld);
+        { random_block_kernel<double><<<grid, 256, 0, c->stream>>>(n, r, col0, seed, 0, static_cast<double *>(out), ld); ::krr::count_launch(); }
     else
-        random_block_kernel<float><<<grid, 256, 0, c->stream>>>(n, r, col0, seed, 1, static_cast<float *>(out), ld);
+        { random_block_kernel<float><<<grid, 256, 0, c->stream>>>(n, r, col0, seed, 1, static_cast<float *>(out), ld); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }

@@ -79,8 +79,8 @@ int launch_sample_f64(Ctx *c, const double *Xa, int64_t ma, const double *Xb, in
     if (d > F_MAXD) return fail(KRR_ERR_NOT_IMPLEMENTED, "sample_f64: d > 64");
     if (ma == 0 || r == 0) return KRR_OK;
     dim3 grid(unsigned(cdiv(ma, F_BM)), unsigned(cdiv(r, F_BC)));
-    sample_f64_kernel<<<grid, 256, 0, c->stream>>>(Xa, ma, Xb, nb, d, 1.0 / (2.0 * h * h), R, r, ldr, leaf_a, leaf_b,
-                                                   S, lds);
+    { sample_f64_kernel<<<grid, 256, 0, c->stream>>>(Xa, ma, Xb, nb, d, 1.0 / (2.0 * h * h), R, r, ldr, leaf_a, leaf_b,
+                                                   S, lds); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }

@@ -535,7 +535,7 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     }
     const int64_t T = P.n_row_tiles * P.n_col_tiles;
     const int grid = int(T < c->num_sms ? T : c->num_sms);
-    tc::sample_tc_kernel<<<grid, tc::kThreads, smem, c->stream>>>(mA, mB, mR, P);
+    { tc::sample_tc_kernel<<<grid, tc::kThreads, smem, c->stream>>>(mA, mB, mR, P); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
