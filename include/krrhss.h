@@ -145,6 +145,24 @@ int krr_sample(krr_ctx *ctx, const float *Xa, int64_t ma, const float *Xb,
                int32_t r, int64_t ldr, const int32_t *leaf_a,
                const int32_t *leaf_b, float *S, int64_t lds);
 
+/* krr_sample without device-memory allocation, for callers that cannot
+ * allocate at the point of the call (for example while a CUDA graph is
+ * being captured, or under a fixed memory budget with no allocator at
+ * hand).  The paper has no counterpart: this is an interface convenience.
+ * Same arguments, result and precision as krr_sample (KRR_MIXED).  Its
+ * scratch lives in one fixed device array inside the library (about
+ * 12.6 MB, reserved on every GPU that loads the library until the process
+ * exits), so sizes are limited to max(ma, nb) <= 16384, r <= 256 and
+ * d <= 19; larger sizes return KRR_ERR_INVALID_ARG.  The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  Every call reuses the same array: calls that may
+ * overlap on the GPU (other streams or unordered threads) race on it. */
+int krr_sample_noalloc(krr_ctx *ctx, const float *Xa, int64_t ma,
+                       const float *Xb, int64_t nb, int32_t d, double h,
+                       double lambda, const float *R, int32_t r, int64_t ldr,
+                       const int32_t *leaf_a, const int32_t *leaf_b, float *S,
+                       int64_t lds);
+
 /* Same product in FP64 on the CUDA cores (the "plain" comparator):
  * Xa, Xb device double; R, S device double.  No size limit on d. */
 int krr_sample_f64(krr_ctx *ctx, const double *Xa, int64_t ma,

@@ -55,6 +55,7 @@ SIGNATURES = {
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),
     "krr_sample": (i32, [P, P, i64, P, i64, i32, f64, f64, P, i32, i64, P, P, P, i64]),
     "krr_sample_f64": (i32, [P, P, i64, P, i64, i32, f64, f64, P, i32, i64, P, P, P, i64]),
+    "krr_sample_noalloc": (i32, [P, P, i64, P, i64, i32, f64, f64, P, i32, i64, P, P, P, i64]),
     "krr_random_block": (i32, [P, i64, i32, i32, u64, ctypes.c_int, P, i64]),
     "krr_default_options": (None, [ctypes.POINTER(krr_options)]),
     "hss_compress": (i32, [P, P, i64, i32, ctypes.POINTER(krr_options), ctypes.POINTER(P)]),

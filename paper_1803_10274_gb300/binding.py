@@ -14,7 +14,7 @@ from . import _lib
 from ._lib import KRR_FP64, KRR_MIXED, KRRError, check, lib
 
 __all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "krr_standardize", "krr_cluster", "krr_sample",
-           "krr_sample_f64", "krr_random_block", "HSS", "hss_compress", "default_options", "lib"]
+           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "HSS", "hss_compress", "default_options", "lib"]
 
 
 _shutting_down = [False]
@@ -118,6 +118,20 @@ def krr_sample(ctx, Xa, Xb, h, lam, R, leaf_a=None, leaf_b=None, S=None):
     _need(S, torch.float32, "S")
     check(lib().krr_sample(ctx.h, _ptr(Xa), ma, _ptr(Xb), nb, d, h, lam, _ptr(R), r, R.stride(0),
                            _ptr(leaf_a), _ptr(leaf_b), _ptr(S), S.stride(0)))
+    return S
+
+
+def krr_sample_noalloc(ctx, Xa, Xb, h, lam, R, S, leaf_a=None, leaf_b=None):
+    """krr_sample into a caller-provided S, with no device allocation in
+    the library (fixed internal scratch; see include/krrhss.h for limits)."""
+    _need(Xa, torch.float32, "Xa")
+    _need(Xb, torch.float32, "Xb")
+    _need(R, torch.float32, "R")
+    _need(S, torch.float32, "S")
+    ma, d = Xa.shape
+    nb, r = R.shape
+    check(lib().krr_sample_noalloc(ctx.h, _ptr(Xa), ma, _ptr(Xb), nb, d, h, lam, _ptr(R), r, R.stride(0),
+                                   _ptr(leaf_a), _ptr(leaf_b), _ptr(S), S.stride(0)))
     return S
 
 
