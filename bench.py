@@ -215,8 +215,12 @@ def run_ours(args):
     peak = float(peaks["bf16_tflops"])
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("sample_tc_kernel_r256_bytes_per_launch")
+        # DRAM bytes per launch from the ncu capture summarized in profiles/
+        with open(os.path.join(ROOT, "profiles", "sample_tc_traffic.txt")) as f:
+            for line in f:
+                k, v = line.split()
+                if k == "bytes_per_launch_n65536_r256":
+                    traffic = int(v)
     except Exception:
         pass
 
@@ -297,6 +301,29 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def sample_only(n, r):
+    """Five launches of the fused sampling product on the benchmark's data
+    distribution (d=8, standardized), for kernel profiling."""
+    import torch
+    import paper_1803_10274_gb300 as K
+    import synth
+    torch.cuda.set_device(0)
+    ctx = K.Context()
+    X = synth.mixture(n, WL["d"], WL["comps"], WL["sigma"], WL["seed"])[0]
+    X = ((X - X.mean(0)) / X.std(0)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    R = torch.from_numpy(np.random.default_rng(7).standard_normal((n, r)).astype(np.float16).astype(np.float32)).cuda()
+    S = torch.empty(n, r, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(5):
+        K.krr_sample(ctx, Xd, Xd, WL["h"], 0.0, R, S=S)
+    e1.record(ctx.stream)
+    ctx.sync()
+    ms = e0.elapsed_time(e1) / 5
+    print(json.dumps({"n": n, "r": r, "ms": ms, "tflops": 2.0 * n * n * (WL["d"] + r) / ms / 1e9}), flush=True)
+
+
 def cpu_baseline(X):
     """The FP64 oracle's dense KRR (kernel matrix + Cholesky solve) on the
     first CPU_SAMPLE_N standardized points, extrapolated to n = 65536 (the
@@ -347,8 +374,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sample-only", nargs=2, type=int, metavar=("N", "R"),
+                    help="only run the fused sampling product at n=N, r=R (5 launches; for profilers)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.sample_only:
+        sample_only(*args.sample_only)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
