@@ -198,6 +198,21 @@ __device__ void lu_solve(int n, const T *A, int64_t lda, const int *ipiv, int nr
     }
 }
 
+// T = R11^{-1} R12 (k x (m-k), row-major, ld m-k) from a pivoted QR stored
+// transposed in the first k rows of W (row b, coordinate a = R[a][b]):
+// one thread per redundant row (column of R12), back substitution.
+template <class T>
+__device__ void id_T(int m, int k, const T *W, int64_t ldw, T *Tout) {
+    const int nr = m - k;
+    for (int c = threadIdx.x; c < nr; c += kNT) {
+        for (int a = k - 1; a >= 0; --a) {
+            T s = W[int64_t(k + c) * ldw + a];  // R12[a][c]
+            for (int b = a + 1; b < k; ++b) s -= W[int64_t(b) * ldw + a] * Tout[int64_t(b) * nr + c];
+            Tout[int64_t(a) * nr + c] = s / W[int64_t(a) * ldw + a];
+        }
+    }
+}
+
 // Row interpolative decomposition of the m x r matrix W (row-major,
 // overwritten): Householder QR with column pivoting of W^T, pivoting over
 // the rows of W.  Only the first r columns enter the QR; rows are swapped
@@ -296,15 +311,7 @@ __device__ int row_id(int m, int r, int rfull, T *W, int64_t ldw, T eps, T eps_a
     for (int i = k + threadIdx.x; i < m; i += kNT) rest += norm2[i];
     rest = sum_block(rest);
     if (in_err) *in_err = tot0 > T(0) ? sqrt(rest / tot0) : T(0);
-    // T = R11^{-1} R12: one thread per redundant row c (column of R12)
-    const int nr = m - k;
-    for (int c = threadIdx.x; c < nr; c += kNT) {
-        for (int a = k - 1; a >= 0; --a) {
-            T s = W[int64_t(k + c) * ldw + a];  // R12[a][c]
-            for (int b = a + 1; b < k; ++b) s -= W[int64_t(b) * ldw + a] * Tout[int64_t(b) * nr + c];
-            Tout[int64_t(a) * nr + c] = s / W[int64_t(a) * ldw + a];
-        }
-    }
+    id_T<T>(m, k, W, ldw, Tout);
     __syncthreads();
     return k;
 }
@@ -334,6 +341,78 @@ __device__ T id_test_error(int m, int k, const T *W, int64_t ldw, const T *Tm, i
     err = sum_block(err);
     tot = sum_block(tot);
     return tot > T(0) ? sqrt(err / tot) : T(0);
+}
+}  // namespace cta
+}  // namespace krr
+
+namespace krr {
+namespace cta {
+// In-place inverse of the n x n matrix A (row-major) by Gauss-Jordan
+// elimination with partial pivoting; ipiv is scratch (n ints).  Returns
+// false on an exactly zero pivot.
+template <class T>
+__device__ bool gj_inverse(int n, T *A, int64_t lda, int *ipiv) {
+    bool ok = true;
+    __shared__ T s_piv;
+    for (int j = 0; j < n; ++j) {
+        T best = T(-1);
+        int bi = 0x7fffffff;
+        for (int i = j + threadIdx.x; i < n; i += kNT) {
+            const T v = tabs(A[int64_t(i) * lda + j]);
+            if (v > best) { best = v; bi = i; }
+        }
+        argmax_block(best, bi);
+        const int p = bi;
+        if (p != j)
+            for (int c = threadIdx.x; c < n; c += kNT) {
+                const T t = A[int64_t(j) * lda + c];
+                A[int64_t(j) * lda + c] = A[int64_t(p) * lda + c];
+                A[int64_t(p) * lda + c] = t;
+            }
+        if (threadIdx.x == 0) {
+            ipiv[j] = p;
+            s_piv = A[int64_t(j) * lda + j];
+        }
+        __syncthreads();
+        const T piv = s_piv;
+        if (piv == T(0)) {
+            ok = false;
+            break;
+        }
+        // row j /= pivot, with A[j][j] replaced by 1 first
+        const T inv = T(1) / piv;
+        for (int c = threadIdx.x; c < n; c += kNT) {
+            const T v = c == j ? T(1) : A[int64_t(j) * lda + c];
+            A[int64_t(j) * lda + c] = v * inv;
+        }
+        __syncthreads();
+        // eliminate column j from every other row (one warp per row)
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        for (int i = w; i < n; i += kNT / 32) {
+            if (i == j) continue;
+            T *ri = A + int64_t(i) * lda;
+            const T f = ri[j];
+            if (f == T(0)) continue;
+            __syncwarp();
+            const T *rj = A + int64_t(j) * lda;
+            for (int c = l; c < n; c += 32) ri[c] = (c == j ? T(0) : ri[c]) - f * rj[c];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (!ok) return false;
+    // undo the row interchanges as column interchanges, last first
+    for (int j = n - 1; j >= 0; --j) {
+        const int p = ipiv[j];
+        if (p != j)
+            for (int r = threadIdx.x; r < n; r += kNT) {
+                const T t = A[int64_t(r) * lda + j];
+                A[int64_t(r) * lda + j] = A[int64_t(r) * lda + p];
+                A[int64_t(r) * lda + p] = t;
+            }
+        __syncthreads();
+    }
+    return true;
 }
 }  // namespace cta
 }  // namespace krr

@@ -31,11 +31,15 @@
 // down.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "bigsteps.cuh"
+#include "grouped.cuh"
 #include "prep.cuh"
 
 namespace krr {
@@ -47,7 +51,8 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
 namespace {
 
 constexpr int kHoldOut = 16;  // sample columns held out of each ID for its error test
-constexpr double kTestFactor = 2.0;  // held-out error allowed, relative to the in-sample error
+constexpr double kTestFactor = 2.0;
+constexpr int kBigNode = 384;  // levels whose largest node has at least this many rows use batched pivot steps  // held-out error allowed, relative to the in-sample error
 
 // Per-node descriptor of one level (offsets are element offsets into the
 // HSS arenas; -1 when unused).
@@ -104,8 +109,26 @@ __global__ void extract_b_kernel(const NodeDesc *nd, const T *X, int d, T inv2h2
     }
 }
 
-// Build S_loc, R_loc (into rg) and global row ids of every node; then the
-// row ID, skeleton samples and Rhat.
+// Parents: the children's skeleton samples stacked into S_loc, and the
+// global ids of the local rows.  The subtraction of B R-hat follows as a
+// grouped GEMM over the whole level.
+template <class T>
+__global__ void parent_sloc_kernel(const NodeDesc *nd, const NodeDesc *all, int r, T *F, int32_t *I) {
+    const NodeDesc &N = nd[blockIdx.x];
+    if (N.is_leaf) return;
+    const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
+    const int ka = A.k, kb = B.k;
+    T *Sl = F + N.sloc;
+    for (int64_t e = threadIdx.x; e < int64_t(ka) * r; e += blockDim.x) Sl[e] = F[A.skel + e];
+    for (int64_t e = threadIdx.x; e < int64_t(kb) * r; e += blockDim.x) Sl[int64_t(ka) * r + e] = F[B.skel + e];
+    for (int a = threadIdx.x; a < ka; a += blockDim.x) I[N.rows + a] = I[A.jsk + a];
+    for (int a = threadIdx.x; a < kb; a += blockDim.x) I[N.rows + ka + a] = I[B.jsk + a];
+}
+
+// Row ID of every node's S_loc (Householder QR with column pivoting of
+// S_loc^T on a copy), its held-out test, the skeleton ids and samples, and
+// R_loc gathered in pivot order (rg) with R-hat initialized to its first k
+// rows; R-hat += T R_loc(redundant) follows as a grouped GEMM.
 template <class T>
 __global__ void __launch_bounds__(cta::kNT) id_kernel(NodeDesc *nd, const NodeDesc *all, const T *S, const T *R,
                                                       int64_t ldsr, int r, T *F, int32_t *I, T eps, T eps_abs,
@@ -115,31 +138,14 @@ __global__ void __launch_bounds__(cta::kNT) id_kernel(NodeDesc *nd, const NodeDe
     T *W = F + N.w;
     T *Rg = F + N.rg;
     int32_t *rows = I + N.rows;
-    // local S_loc -> W, local R -> Rg (local order), row ids
-    if (N.is_leaf) {
-        for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) {
-            const int a = int(e / r), t = int(e % r);
-            const int64_t gi = N.leaf_begin + a;
-            W[e] = S[gi * ldsr + t];
-            Rg[e] = R[gi * ldsr + t];
-        }
-        for (int a = threadIdx.x; a < m; a += blockDim.x) rows[a] = N.leaf_begin + a;
-    } else {
-        const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
-        const int ka = A.k, kb = B.k;
-        T *Sl = F + N.sloc;
-        for (int64_t e = threadIdx.x; e < int64_t(ka) * r; e += blockDim.x) Sl[e] = F[A.skel + e];
-        for (int64_t e = threadIdx.x; e < int64_t(kb) * r; e += blockDim.x) Sl[int64_t(ka) * r + e] = F[B.skel + e];
-        __syncthreads();
-        // S_a(J_a) - B_ab Rhat_b ;  S_b(J_b) - B_ab^T Rhat_a
-        cta::gemm<T, false, false>(ka, r, kb, T(-1), F + N.bmat, kb, F + B.rhat, r, T(1), Sl, r);
-        cta::gemm<T, true, false>(kb, r, ka, T(-1), F + N.bmat, kb, F + A.rhat, r, T(1), Sl + int64_t(ka) * r, r);
-        for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) W[e] = Sl[e];
-        for (int64_t e = threadIdx.x; e < int64_t(ka) * r; e += blockDim.x) Rg[e] = F[A.rhat + e];
-        for (int64_t e = threadIdx.x; e < int64_t(kb) * r; e += blockDim.x) Rg[int64_t(ka) * r + e] = F[B.rhat + e];
-        for (int a = threadIdx.x; a < ka; a += blockDim.x) rows[a] = I[A.jsk + a];
-        for (int a = threadIdx.x; a < kb; a += blockDim.x) rows[ka + a] = I[B.jsk + a];
+    const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
+    const int64_t lds = N.is_leaf ? ldsr : r;
+    for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) {
+        const int a = int(e / r), t = int(e % r);
+        W[e] = Sorig[int64_t(a) * lds + t];
     }
+    if (N.is_leaf)
+        for (int a = threadIdx.x; a < m; a += blockDim.x) rows[a] = N.leaf_begin + a;
     __syncthreads();
     int32_t *piv = I + N.piv;
     // the last kHoldOut sample columns are held out of the QR and measure
@@ -155,180 +161,186 @@ __global__ void __launch_bounds__(cta::kNT) id_kernel(NodeDesc *nd, const NodeDe
         test_err[2 * blockIdx.x] = float(terr);
         test_err[2 * blockIdx.x + 1] = float(s_in_err);
     }
-    // skeleton ids and skeleton samples (from the unmodified S_loc)
-    const T *Sorig = N.is_leaf ? nullptr : F + N.sloc;
     for (int a = threadIdx.x; a < k; a += blockDim.x) I[N.jsk + a] = rows[piv[a]];
     for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += blockDim.x) {
         const int a = int(e / r), t = int(e % r);
-        const int src = piv[a];
-        F[N.skel + e] = N.is_leaf ? S[(N.leaf_begin + int64_t(src)) * ldsr + t] : Sorig[int64_t(src) * r + t];
+        F[N.skel + e] = Sorig[int64_t(piv[a]) * lds + t];
     }
-    // R rows in pivot order into W (free now), then Rhat = R_s + T R_r
-    __syncthreads();
+    // R_loc rows in pivot order: R(I) at a leaf, [Rhat_a; Rhat_b] at a parent
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
+    T *Rh = F + N.rhat;
     for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) {
         const int a = int(e / r), t = int(e % r);
-        W[e] = Rg[int64_t(piv[a]) * r + t];
+        const int src = piv[a];
+        T v;
+        if (N.is_leaf) v = R[(int64_t(N.leaf_begin) + src) * ldsr + t];
+        else if (src < A->k) v = F[A->rhat + int64_t(src) * r + t];
+        else v = F[B->rhat + int64_t(src - A->k) * r + t];
+        Rg[e] = v;
+        if (a < k) Rh[e] = v;
     }
+}
+
+// Large-node path of the row ID, step 1: S_loc copied into W (ld r), row
+// ids of leaves.  The QR then runs as batched pivot-step launches.
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) id_prep_kernel(const NodeDesc *nd, const T *S, int64_t ldsr, int r, T *F,
+                                                           int32_t *I) {
+    const NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
+    const int64_t lds = N.is_leaf ? ldsr : r;
+    T *W = F + N.w;
+    for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) W[e] = Sorig[(e / r) * lds + e % r];
+    if (N.is_leaf)
+        for (int a = threadIdx.x; a < m; a += blockDim.x) I[N.rows + a] = N.leaf_begin + a;
+}
+
+// Large-node path, last step: T from the QR, in-sample and held-out errors,
+// skeleton ids and samples, R_loc in pivot order and R-hat's first rows.
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) id_post_kernel(NodeDesc *nd, const NodeDesc *all, const big::QrState *qs,
+                                                           const T *S, const T *R, int64_t ldsr, int r, T *F,
+                                                           int32_t *I, int *ranks, float *test_err) {
+    NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    const int k = qs[blockIdx.x].k;
+    T *W = F + N.w;
+    const int rid = r - kHoldOut;
+    cta::id_T<T>(m, k, W, r, F + N.tmat);
     __syncthreads();
+    T rest = T(0);
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) rest += F[N.norm + i];
+    rest = cta::sum_block(rest);
+    const double tot0 = qs[blockIdx.x].tot0;
+    const T in_err = tot0 > 0 ? T(sqrt(double(rest) / tot0)) : T(0);
+    const T terr = cta::id_test_error<T>(m, k, W, r, F + N.tmat, rid, r);
+    if (threadIdx.x == 0) {
+        N.k = k;
+        ranks[blockIdx.x] = k;
+        test_err[2 * blockIdx.x] = float(terr);
+        test_err[2 * blockIdx.x + 1] = float(in_err);
+    }
+    const int32_t *piv = I + N.piv;
+    const int32_t *rows = I + N.rows;
+    const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
+    const int64_t lds = N.is_leaf ? ldsr : r;
+    for (int a = threadIdx.x; a < k; a += blockDim.x) I[N.jsk + a] = rows[piv[a]];
+    for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += blockDim.x)
+        F[N.skel + e] = Sorig[int64_t(piv[e / r]) * lds + e % r];
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
+    T *Rg = F + N.rg;
     T *Rh = F + N.rhat;
-    for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += blockDim.x) Rh[e] = W[e];
-    __syncthreads();
-    if (k > 0 && m > k)
-        cta::gemm<T, false, false>(k, r, m - k, T(1), F + N.tmat, m - k, W + int64_t(k) * r, r, T(1), Rh, r);
+    __syncthreads();  // the Householder vector lived in rg
+    for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) {
+        const int a = int(e / r), t = int(e % r);
+        const int src = piv[a];
+        T v;
+        if (N.is_leaf) v = R[(int64_t(N.leaf_begin) + src) * ldsr + t];
+        else if (src < A->k) v = F[A->rhat + int64_t(src) * r + t];
+        else v = F[B->rhat + int64_t(src - A->k) * r + t];
+        Rg[e] = v;
+        if (a < k) Rh[e] = v;
+    }
 }
 
-// Diagonal block of every node: K(I,I) + lambda I at leaves, the merged
-// [Dt_a, B; B^T, Dt_b] at parents; then (non-root) the elimination.
+// Diagonal block of a node in skeleton-first order: K(I,I) + lambda I at a
+// leaf, [Dt_a, B; B^T, Dt_b] at a parent.  Writes D_ss -> dtil, D_rs ->
+// dmat (kept) and drs (to be updated), D_rr -> drr; the root's whole
+// block (local order) -> drr.
 template <class T>
-__global__ void __launch_bounds__(cta::kNT) factor_kernel(NodeDesc *nd, const NodeDesc *all, const T *X, int d,
-                                                          T inv2h2, T lambda, T *F, int32_t *I, int is_root,
-                                                          DevStatus *st) {
-    NodeDesc &N = nd[blockIdx.x];
+__global__ void __launch_bounds__(cta::kNT) factor_build_kernel(const NodeDesc *nd, const NodeDesc *all, const T *X,
+                                                                int d, T inv2h2, T lambda, T *F, const int32_t *I,
+                                                                int is_root) {
+    const NodeDesc &N = nd[blockIdx.x];
     const int m = N.m;
-    T *D = F + N.dmat;
-    if (N.is_leaf) {
-        for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) {
-            const int a = int(e / m), b = int(e % m);
-            T v = a == b ? T(1) : kern(X + (N.leaf_begin + int64_t(a)) * d, X + (N.leaf_begin + int64_t(b)) * d, d, inv2h2);
-            if (a == b) v += lambda;
-            D[e] = v;
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
+    auto dval = [&](int a, int b) -> T {
+        if (N.is_leaf) {
+            if (a == b) return T(1) + lambda;
+            return kern(X + (N.leaf_begin + int64_t(a)) * d, X + (N.leaf_begin + int64_t(b)) * d, d, inv2h2);
         }
-    } else {
-        const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
-        const int ka = A.k, kb = B.k;
-        for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) {
-            const int a = int(e / m), b = int(e % m);
-            T v;
-            if (a < ka && b < ka) v = F[A.dtil + int64_t(a) * ka + b];
-            else if (a >= ka && b >= ka) v = F[B.dtil + int64_t(a - ka) * kb + (b - ka)];
-            else if (a < ka) v = F[N.bmat + int64_t(a) * kb + (b - ka)];
-            else v = F[N.bmat + int64_t(b) * kb + (a - ka)];
-            D[e] = v;
-        }
-    }
-    __syncthreads();
+        const int ka = A->k, kb = B->k;
+        if (a < ka && b < ka) return F[A->dtil + int64_t(a) * ka + b];
+        if (a >= ka && b >= ka) return F[B->dtil + int64_t(a - ka) * kb + (b - ka)];
+        if (a < ka) return F[N.bmat + int64_t(a) * kb + (b - ka)];
+        return F[N.bmat + int64_t(b) * kb + (a - ka)];
+    };
     if (is_root) {
-        if (!cta::lu<T>(m, D, m, I + N.ipiv) && threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 200);
+        for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) F[N.drr + e] = dval(int(e / m), int(e % m));
         return;
     }
     const int k = N.k, nr = m - k;
     const int32_t *piv = I + N.piv;
-    // permute to (skeleton, redundant) order into drr's slot as scratch
-    T *Dp = F + N.drr;
-    for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) {
-        const int a = int(e / m), b = int(e % m);
-        Dp[e] = D[int64_t(piv[a]) * m + piv[b]];
-    }
-    __syncthreads();
-    // copy Dp back into D so D holds the permuted block; Dss = D[0:k,0:k],
-    // Dsr = D[0:k,k:], Drs = D[k:,0:k], Drr = D[k:,k:]
-    for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) D[e] = Dp[e];
-    __syncthreads();
-    const T *Tm = F + N.tmat;
-    T *Drs = F + N.drs;    // nr x k
-    T *Drr = F + N.drr;    // nr x nr
-    T *Y = F + N.ymat;     // nr x k
-    T *Dt = F + N.dtil;    // k x k
+    for (int64_t e = threadIdx.x; e < int64_t(k) * k; e += blockDim.x)
+        F[N.dtil + e] = dval(piv[e / k], piv[e % k]);
     for (int64_t e = threadIdx.x; e < int64_t(nr) * k; e += blockDim.x) {
-        const int a = int(e / k), b = int(e % k);
-        Drs[e] = D[int64_t(k + a) * m + b];
+        const T v = dval(piv[k + e / k], piv[e % k]);
+        F[N.dmat + e] = v;
+        F[N.drs + e] = v;
     }
-    for (int64_t e = threadIdx.x; e < int64_t(nr) * nr; e += blockDim.x) {
-        const int a = int(e / nr), b = int(e % nr);
-        Drr[e] = D[int64_t(k + a) * m + k + b];
-    }
-    __syncthreads();
-    if (k > 0 && nr > 0) {
-        // D'_rs = D_rs - T^T D_ss
-        cta::gemm<T, true, false>(nr, k, k, T(-1), Tm, nr, D, m, T(1), Drs, k);
-        // D'_rr = D_rr - T^T D_sr - D'_rs T
-        cta::gemm<T, true, false>(nr, nr, k, T(-1), Tm, nr, D + k, m, T(1), Drr, nr);
-        cta::gemm<T, false, false>(nr, nr, k, T(-1), Drs, k, Tm, nr, T(1), Drr, nr);
-    }
-    if (nr > 0 && !cta::lu<T>(nr, Drr, nr, I + N.ipiv)) {
-        if (threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 201);
-        return;
-    }
-    // Y = D'_rr^{-1} D'_rs ; Dt = D_ss - D'_rs^T Y
-    for (int64_t e = threadIdx.x; e < int64_t(nr) * k; e += blockDim.x) Y[e] = Drs[e];
-    for (int64_t e = threadIdx.x; e < int64_t(k) * k; e += blockDim.x) {
-        const int a = int(e / k), b = int(e % k);
-        Dt[e] = D[int64_t(a) * m + b];
-    }
-    __syncthreads();
-    if (nr > 0 && k > 0) {
-        cta::lu_solve<T>(nr, Drr, nr, I + N.ipiv, k, Y, k);
-        cta::gemm<T, true, false>(k, k, nr, T(-1), Drs, k, Y, k, T(1), Dt, k);
+    for (int64_t e = threadIdx.x; e < int64_t(nr) * nr; e += blockDim.x)
+        F[N.drr + e] = dval(piv[k + e / nr], piv[k + e % nr]);
+}
+
+// drr <- drr^{-1} (redundant block, or the root's whole block).
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) invert_kernel(const NodeDesc *nd, T *F, int32_t *I, int is_root,
+                                                          DevStatus *st) {
+    const NodeDesc &N = nd[blockIdx.x];
+    const int n = is_root ? N.m : N.m - N.k;
+    if (n <= 0) return;
+    if (!cta::gj_inverse<T>(n, F + N.drr, n, I + N.ipiv) && threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 201);
+}
+
+// Up-sweep, step 1 (one CTA per node): the node's local right-hand side
+// (rows of y at a leaf, [btil_a; btil_b] at a parent) split in pivot order:
+// skeleton rows -> btil (k x nrhs), redundant rows -> xloc (nr x nrhs).
+// The root's whole block goes to zvec.  The eliminations follow as
+// grouped GEMMs over the level:
+//   xloc -= T^T btil ; zvec = D'_rr^{-1} xloc ; btil -= D'_rs^T zvec
+// and at the root xloc = D^{-1} zvec.
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) solve_gather_kernel(const NodeDesc *nd, const NodeDesc *all,
+                                                                const T *yperm, int64_t ldy, int nrhs, T *F,
+                                                                const int32_t *I, int is_root) {
+    const NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m, k = is_root ? 0 : N.k;
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
+    const int32_t *piv = I + N.piv;
+    for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
+        const int a = int(e / nrhs), c = int(e % nrhs);
+        const int src = is_root ? a : piv[a];
+        T v;
+        if (N.is_leaf) v = yperm[(N.leaf_begin + int64_t(src)) * ldy + c];
+        else if (src < A->k) v = F[A->btil + int64_t(src) * nrhs + c];
+        else v = F[B->btil + int64_t(src - A->k) * nrhs + c];
+        if (is_root) F[N.zvec + e] = v;
+        else if (a < k) F[N.btil + int64_t(a) * nrhs + c] = v;
+        else F[N.xloc + int64_t(a - k) * nrhs + c] = v;
     }
 }
 
-// Up-sweep of the solve: local b -> (z, btil).
+// Down-sweep, last step (one CTA per node): after
+//   zvec -= Y btil  (x'_r) ;  btil -= T zvec  (x_s)
+// the local x in the node's original row order -> xloc; leaves write
+// their rows of the solution.
 template <class T>
-__global__ void __launch_bounds__(cta::kNT) solve_up_kernel(NodeDesc *nd, const NodeDesc *all, const T *yperm,
-                                                            int64_t ldy, int nrhs, T *F, const int32_t *I, int is_root) {
-    NodeDesc &N = nd[blockIdx.x];
-    const int m = N.m;
-    T *b = F + N.xloc;  // local b (m x nrhs), reused for x in the down-sweep
-    if (N.is_leaf) {
-        for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
-            const int a = int(e / nrhs), c = int(e % nrhs);
-            b[e] = yperm[(N.leaf_begin + int64_t(a)) * ldy + c];
-        }
-    } else {
-        const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
-        for (int64_t e = threadIdx.x; e < int64_t(A.k) * nrhs; e += blockDim.x) b[e] = F[A.btil + e];
-        for (int64_t e = threadIdx.x; e < int64_t(B.k) * nrhs; e += blockDim.x) b[int64_t(A.k) * nrhs + e] = F[B.btil + e];
-    }
-    __syncthreads();
-    if (is_root) {
-        cta::lu_solve<T>(m, F + N.dmat, m, I + N.ipiv, nrhs, b, nrhs);
-        return;
-    }
-    const int k = N.k, nr = m - k;
+__global__ void __launch_bounds__(cta::kNT) solve_place_kernel(const NodeDesc *nd, int nrhs, T *F, const int32_t *I,
+                                                               T *xperm, int64_t ldx) {
+    const NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m, k = N.k;
     const int32_t *piv = I + N.piv;
-    T *z = F + N.zvec;   // nr x nrhs
-    T *bt = F + N.btil;  // k x nrhs
     for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
         const int a = int(e / nrhs), c = int(e % nrhs);
-        const T v = b[int64_t(piv[a]) * nrhs + c];
-        if (a < k) bt[int64_t(a) * nrhs + c] = v;
-        else z[int64_t(a - k) * nrhs + c] = v;
-    }
-    __syncthreads();
-    if (nr > 0) {
-        if (k > 0) cta::gemm<T, true, false>(nr, nrhs, k, T(-1), F + N.tmat, nr, bt, nrhs, T(1), z, nrhs);
-        cta::lu_solve<T>(nr, F + N.drr, nr, I + N.ipiv, nrhs, z, nrhs);
-        if (k > 0) cta::gemm<T, true, false>(k, nrhs, nr, T(-1), F + N.drs, k, z, nrhs, T(1), bt, nrhs);
-    }
-}
-
-// Down-sweep: receive x's (k x nrhs), produce the local x.
-template <class T>
-__global__ void __launch_bounds__(cta::kNT) solve_down_kernel(NodeDesc *nd, const NodeDesc *all, int nrhs, T *F,
-                                                              const int32_t *I, T *xperm, int64_t ldx) {
-    NodeDesc &N = nd[blockIdx.x];
-    const int m = N.m, k = N.k, nr = m - k;
-    // x's arrives in btil (written by the parent's down step)
-    T *xs = F + N.btil;
-    T *z = F + N.zvec;
-    const int32_t *piv = I + N.piv;
-    if (nr > 0 && k > 0) {
-        // x'_r = z - Y x'_s ; then x_s = x'_s - T x'_r
-        cta::gemm<T, false, false>(nr, nrhs, k, T(-1), F + N.ymat, k, xs, nrhs, T(1), z, nrhs);
-        cta::gemm<T, false, false>(k, nrhs, nr, T(-1), F + N.tmat, nr, z, nrhs, T(1), xs, nrhs);
-    }
-    T *x = F + N.xloc;
-    for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
-        const int a = int(e / nrhs), c = int(e % nrhs);
-        const T v = a < k ? xs[int64_t(a) * nrhs + c] : z[int64_t(a - k) * nrhs + c];
-        x[int64_t(piv[a]) * nrhs + c] = v;
-    }
-    __syncthreads();
-    if (N.is_leaf) {
-        for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
-            const int a = int(e / nrhs), c = int(e % nrhs);
-            xperm[(N.leaf_begin + int64_t(a)) * ldx + c] = x[e];
-        }
+        const T v = a < k ? F[N.btil + int64_t(a) * nrhs + c] : F[N.zvec + int64_t(a - k) * nrhs + c];
+        const int dst = piv[a];
+        if (N.is_leaf) xperm[(N.leaf_begin + int64_t(dst)) * ldx + c] = v;
+        else F[N.xloc + int64_t(dst) * nrhs + c] = v;
     }
 }
 
@@ -495,6 +507,27 @@ double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// KRR_TRACE=1 in the environment: synchronize and print the time of every
+// phase of every level (a diagnostic; it serializes the stream).
+struct Tracer {
+    bool on;
+    double t;
+    Ctx *c;
+    explicit Tracer(Ctx *ctx) : on(std::getenv("KRR_TRACE") != nullptr), t(0), c(ctx) {
+        if (on) {
+            cudaStreamSynchronize(c->stream);
+            t = now_ms();
+        }
+    }
+    void mark(const char *what, int h, int nn, int mmax) {
+        if (!on) return;
+        cudaStreamSynchronize(c->stream);
+        const double t1 = now_ms();
+        std::fprintf(stderr, "[krr] %-14s h=%2d nodes=%4d mmax=%5d %9.3f ms\n", what, h, nn, mmax, t1 - t);
+        t = t1;
+    }
+};
+
 template <class T>
 T *farena(HssImpl *H);
 template <>
@@ -601,6 +634,7 @@ int id_sweep(HssImpl *H, bool &need_more) {
     H->max_test_err = 0;
     std::vector<NodeDesc> lvdesc;
     H->max_rank = 0;
+    Tracer tr(c);
     for (int h = 0; h <= H->H; ++h) {
         std::vector<int> &lv = H->by_height[h];
         // exact m for parents now that children are done
@@ -622,21 +656,80 @@ int id_sweep(HssImpl *H, bool &need_more) {
         if (!dl.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
         KRR_CUDA(cudaMemcpyAsync(dl.get(), lvdesc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
         const bool is_root_level = (h == H->H);
-        if (h > 0)
+        if (h > 0) {
             { extract_b_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), X, H->d, inv2h2, F, H->IA.get(),
-                                                                H->ddesc.get()); ::krr::count_launch(); }
-        KRR_CUDA(cudaGetLastError());
-        if (is_root_level) break;  // the root needs B only
-        const size_t smem = size_t(H->r) * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            KRR_CUDA(cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-            attr = true;
+                                                                  H->ddesc.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
         }
-        { id_kernel<T><<<nn, cta::kNT, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, H->r, F,
-                                                        H->IA.get(), T(H->opt.eps_c), T(H->opt.eps_abs), kmax,
-                                                        dranks.get(), derr.get(), c->status); ::krr::count_launch(); }
-        KRR_CUDA(cudaGetLastError());
+        int mmax = 0;
+        for (int v : lv) mmax = std::max(mmax, H->desc[v].m);
+        tr.mark("extract_b", h, nn, mmax);
+        if (is_root_level) break;  // the root needs B only
+        const int r = H->r;
+        if (h > 0) {
+            { parent_sloc_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), r, F, H->IA.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+            // S_a(J_a) - B_ab Rhat_b ;  S_b(J_b) - B_ab^T Rhat_a
+            GemmBatch<T> gb;
+            for (int v : lv) {
+                const NodeDesc &N = H->desc[v];
+                const NodeDesc &A = H->desc[N.child_a], &B = H->desc[N.child_b];
+                T *Sl = F + N.sloc;
+                gb.add(A.k, r, B.k, T(-1), F + N.bmat, B.k, false, F + B.rhat, r, false, T(1), Sl, r);
+                gb.add(B.k, r, A.k, T(-1), F + N.bmat, B.k, true, F + A.rhat, r, false, T(1), Sl + int64_t(A.k) * r, r);
+            }
+            KRR_TRY(gb.launch(c));
+            tr.mark("parent_sloc", h, nn, mmax);
+        }
+        if (mmax < kBigNode && nn >= c->num_sms) {
+            const size_t smem = size_t(r) * sizeof(T);
+            static bool attr = false;
+            if (!attr) {
+                KRR_CUDA(cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+                attr = true;
+            }
+            { id_kernel<T><<<nn, cta::kNT, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, r, F,
+                                                              H->IA.get(), T(H->opt.eps_c), T(H->opt.eps_abs), kmax,
+                                                              dranks.get(), derr.get(), c->status); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+        } else {
+            // large nodes: the pivoted QR as batched pivot-step launches
+            { id_prep_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), S, H->r_cap, r, F, H->IA.get()); ::krr::count_launch(); }
+            std::vector<big::QrItem> qi(nn);
+            for (int a = 0; a < nn; ++a) {
+                const NodeDesc &N = lvdesc[a];
+                qi[a] = big::QrItem{N.w, N.norm, N.rg, N.piv, N.m, r - kHoldOut, r, kmax};
+            }
+            DBuf<big::QrItem> dqi(c, nn);
+            DBuf<big::QrState> dqs(c, nn);
+            if (!dqi.get() || !dqs.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+            KRR_CUDA(cudaMemcpyAsync(dqi.get(), qi.data(), nn * sizeof(big::QrItem), cudaMemcpyHostToDevice, c->stream));
+            KRR_CUDA(cudaMemsetAsync(dqs.get(), 0, nn * sizeof(big::QrState), c->stream));
+            const dim3 g(unsigned(cdiv(mmax, big::kRowsPerBlock)), unsigned(nn));
+            { big::qr_init_kernel<T><<<g, 256, 0, c->stream>>>(dqi.get(), dqs.get(), F, H->IA.get()); ::krr::count_launch(); }
+            const int jmax = std::min(std::min(mmax, r - kHoldOut), kmax);
+            std::vector<big::QrState> hs(nn);
+            for (int j = 0; j < jmax; ++j) {
+                { big::qr_pivot_kernel<T><<<nn, 256, 0, c->stream>>>(dqi.get(), dqs.get(), F, H->IA.get(), j,
+                                                                     H->opt.eps_c, H->opt.eps_abs); ::krr::count_launch(); }
+                { big::qr_apply_kernel<T><<<g, 256, 0, c->stream>>>(dqi.get(), dqs.get(), F, j); ::krr::count_launch(); }
+                if ((j & 15) == 15) {  // stop early once every node has found its rank
+                    KRR_CUDA(cudaMemcpyAsync(hs.data(), dqs.get(), nn * sizeof(big::QrState), cudaMemcpyDeviceToHost,
+                                             c->stream));
+                    KRR_CUDA(cudaStreamSynchronize(c->stream));
+                    bool all = true;
+                    for (const big::QrState &q : hs) all = all && q.done;
+                    if (all) break;
+                }
+            }
+            // nodes still running at jmax stop there
+            { big::qr_pivot_kernel<T><<<nn, 256, 0, c->stream>>>(dqi.get(), dqs.get(), F, H->IA.get(), jmax,
+                                                                 H->opt.eps_c, H->opt.eps_abs); ::krr::count_launch(); }
+            { id_post_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), dqs.get(), S, R, H->r_cap,
+                                                                r, F, H->IA.get(), dranks.get(), derr.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+        }
+        tr.mark("id", h, nn, mmax);
         std::vector<int> hr(nn);
         std::vector<float> he(2 * nn);
         KRR_CUDA(cudaMemcpyAsync(hr.data(), dranks.get(), nn * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -653,6 +746,18 @@ int id_sweep(HssImpl *H, bool &need_more) {
             if (e_test > kTestFactor * std::max(e_in, H->opt.eps_c)) need_more = true;
         }
         if (need_more) return KRR_OK;
+        {
+            // R-hat += T R_loc(redundant)
+            GemmBatch<T> gb;
+            for (int v : lv) {
+                const NodeDesc &N = H->desc[v];
+                const int k = N.k, nr = N.m - N.k;
+                gb.add(k, H->r, nr, T(1), F + N.tmat, nr, false, F + N.rg + int64_t(k) * H->r, H->r, false, T(1),
+                       F + N.rhat, H->r);
+            }
+            KRR_TRY(gb.launch(c));
+            tr.mark("rhat", h, nn, 0);
+        }
     }
     return KRR_OK;
 }
@@ -696,18 +801,60 @@ int factor(HssImpl *H) {
     const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
     KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), H->desc.size() * sizeof(NodeDesc),
                              cudaMemcpyHostToDevice, c->stream));
+    Tracer tr(c);
     for (int h = 0; h <= H->H; ++h) {
         std::vector<int> &lv = H->by_height[h];
         const int nn = int(lv.size());
         if (!nn) continue;
+        const int is_root = h == H->H ? 1 : 0;
+        int mmax = 0;
+        for (int v : lv) mmax = std::max(mmax, H->desc[v].m);
         std::vector<NodeDesc> ld(nn);
         for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
         DBuf<NodeDesc> dl(c, nn);
         if (!dl.get()) return fail(KRR_ERR_OOM, "hss_factor: out of memory");
         KRR_CUDA(cudaMemcpyAsync(dl.get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
-        { factor_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), X, H->d, inv2h2, T(H->lambda), F,
-                                                         H->IA.get(), h == H->H ? 1 : 0, c->status); ::krr::count_launch(); }
+        { factor_build_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), X, H->d, inv2h2,
+                                                                 T(H->lambda), F, H->IA.get(), is_root); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
+        if (!is_root) {
+            // D'_rs = D_rs - T^T D_ss ; D'_rr = D_rr - T^T D_sr - D'_rs T
+            GemmBatch<T> g1, g2, g3;
+            for (const NodeDesc &N : ld) {
+                const int k = N.k, nr = N.m - N.k;
+                g1.add(nr, k, k, T(-1), F + N.tmat, nr, true, F + N.dtil, k, false, T(1), F + N.drs, k);
+                g2.add(nr, nr, k, T(-1), F + N.tmat, nr, true, F + N.dmat, k, true, T(1), F + N.drr, nr);
+                g3.add(nr, nr, k, T(-1), F + N.drs, k, false, F + N.tmat, nr, false, T(1), F + N.drr, nr);
+            }
+            tr.mark("f_build", h, nn, mmax);
+            KRR_TRY(g1.launch(c));
+            KRR_TRY(g2.launch(c));
+            KRR_TRY(g3.launch(c));
+            tr.mark("f_gemm123", h, nn, mmax);
+        }
+        int nmax_inv = 0;
+        for (const NodeDesc &N : ld) nmax_inv = std::max(nmax_inv, is_root ? N.m : N.m - N.k);
+        if (nmax_inv < 96 || (nmax_inv < kBigNode && nn >= c->num_sms)) {
+            { invert_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), F, H->IA.get(), is_root, c->status); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+        } else {
+            std::vector<big::InvItem> items;
+            for (const NodeDesc &N : ld) items.push_back(big::InvItem{N.drr, N.ipiv, is_root ? N.m : N.m - N.k});
+            KRR_TRY(big::gj_inverse_batched<T>(c, items, F, H->IA.get()));
+        }
+        tr.mark("f_invert", h, nn, mmax);
+        if (!is_root) {
+            // Y = D'_rr^{-1} D'_rs ; Dt = D_ss - D'_rs^T Y
+            GemmBatch<T> g4, g5;
+            for (const NodeDesc &N : ld) {
+                const int k = N.k, nr = N.m - N.k;
+                g4.add(nr, k, nr, T(1), F + N.drr, nr, false, F + N.drs, k, false, T(0), F + N.ymat, k);
+                g5.add(k, k, nr, T(-1), F + N.drs, k, true, F + N.ymat, k, false, T(1), F + N.dtil, k);
+            }
+            KRR_TRY(g4.launch(c));
+            KRR_TRY(g5.launch(c));
+            tr.mark("f_gemm45", h, nn, mmax);
+        }
     }
     KRR_CUDA(cudaStreamSynchronize(c->stream));
     H->factored = true;
@@ -725,22 +872,49 @@ int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64
         std::vector<int> &lv = H->by_height[h];
         const int nn = int(lv.size());
         if (!nn) continue;
+        const int is_root = h == H->H ? 1 : 0;
         std::vector<NodeDesc> ld(nn);
         for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
         if (!dls[h].reset(c, nn)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
         KRR_CUDA(cudaMemcpyAsync(dls[h].get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
-        { solve_up_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), yperm, ldy, nrhs, F,
-                                                           H->IA.get(), h == H->H ? 1 : 0); ::krr::count_launch(); }
+        { solve_gather_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), yperm, ldy, nrhs, F,
+                                                                 H->IA.get(), is_root); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
+        if (is_root) {
+            GemmBatch<T, 16> g;
+            for (const NodeDesc &N : ld)
+                g.add(N.m, nrhs, N.m, T(1), F + N.drr, N.m, false, F + N.zvec, nrhs, false, T(0), F + N.xloc, nrhs);
+            KRR_TRY(g.launch(c));
+            break;
+        }
+        GemmBatch<T, 16> g2, g3, g4;
+        for (const NodeDesc &N : ld) {
+            const int k = N.k, nr = N.m - N.k;
+            g2.add(nr, nrhs, k, T(-1), F + N.tmat, nr, true, F + N.btil, nrhs, false, T(1), F + N.xloc, nrhs);
+            g3.add(nr, nrhs, nr, T(1), F + N.drr, nr, false, F + N.xloc, nrhs, false, T(0), F + N.zvec, nrhs);
+            g4.add(k, nrhs, nr, T(-1), F + N.drs, k, true, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
+        }
+        KRR_TRY(g2.launch(c));
+        KRR_TRY(g3.launch(c));
+        KRR_TRY(g4.launch(c));
     }
     for (int h = H->H; h >= 0; --h) {
         const int nn = int(H->by_height[h].size());
         if (!nn) continue;
-        if (h < H->H)
-            { solve_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F, H->IA.get(),
-                                                                 xperm, ldx); ::krr::count_launch(); }
-        else if (H->desc[H->root].is_leaf)  // single-leaf tree: the root's solve is the answer
+        if (h < H->H) {
+            GemmBatch<T, 16> d1, d2;
+            for (int v : H->by_height[h]) {
+                const NodeDesc &N = H->desc[v];
+                const int k = N.k, nr = N.m - N.k;
+                d1.add(nr, nrhs, k, T(-1), F + N.ymat, k, false, F + N.btil, nrhs, false, T(1), F + N.zvec, nrhs);
+                d2.add(k, nrhs, nr, T(-1), F + N.tmat, nr, false, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
+            }
+            KRR_TRY(d1.launch(c));
+            KRR_TRY(d2.launch(c));
+            { solve_place_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), nrhs, F, H->IA.get(), xperm, ldx); ::krr::count_launch(); }
+        } else if (H->desc[H->root].is_leaf) {  // single-leaf tree: the root's solve is the answer
             { root_leaf_out_kernel<T><<<1, cta::kNT, 0, c->stream>>>(dls[h].get(), nrhs, F, xperm, ldx); ::krr::count_launch(); }
+        }
         { scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
@@ -919,6 +1093,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
             return KRR_OK;
         };
         std::vector<double> ynrm(nrhs), hd((mres + 1) * nrhs), hd2((mres + 1) * nrhs);
+        Tracer tr(c);
         KRR_TRY(mdot(yp.get(), 1, yp.get()));
         KRR_CUDA(cudaMemcpyAsync(ynrm.data(), dots.get(), nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
         KRR_CUDA(cudaStreamSynchronize(c->stream));
@@ -954,8 +1129,10 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
                 ++total_it;
                 double *Vj = V.get() + int64_t(j) * nn;
                 KRR_TRY(ulv(Vj, Zv.get()));
+                tr.mark("g_ulv", j, 0, 0);
                 KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, Zv.get(), nrhs, nrhs, Wv.get(), nrhs, H->lambda,
                                   nullptr, 0, nullptr));
+                tr.mark("g_apply", j, 0, 0);
                 // two passes of classical Gram-Schmidt
                 std::fill(hd.begin(), hd.end(), 0.0);
                 for (int pass = 0; pass < 2; ++pass) {
@@ -971,6 +1148,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
                     KRR_CUDA(cudaMemcpyAsync(coef.get(), neg.data(), neg.size() * 8, cudaMemcpyHostToDevice, c->stream));
                     { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, j + 1, coef.get(), n, nrhs); ::krr::count_launch(); }
                 }
+                tr.mark("g_ortho", j, 0, 0);
                 KRR_TRY(mdot(Wv.get(), 1, Wv.get()));
                 std::vector<double> wn(nrhs);
                 KRR_CUDA(cudaMemcpyAsync(wn.data(), dots.get(), nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
