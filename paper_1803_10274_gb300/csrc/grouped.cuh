@@ -93,6 +93,20 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(const GemmProb<T> *pr
     }
 }
 
+// A problem list uploaded once and launched many times.
+template <class T, int TN>
+struct GemmPlan {
+    DBuf<GemmProb<T>> d;
+    int np = 0, tiles = 0;
+    int run(Ctx *c) const {
+        if (np == 0) return KRR_OK;
+        const int grid = tiles < 4 * c->num_sms ? tiles : 4 * c->num_sms;
+        { grouped_gemm_kernel<T, TN><<<grid, 256, 0, c->stream>>>(d.get(), np, tiles); ::krr::count_launch(); }
+        KRR_CUDA(cudaGetLastError());
+        return KRR_OK;
+    }
+};
+
 template <class T, int TN = 64>
 struct GemmBatch {
     std::vector<GemmProb<T>> v;
@@ -119,6 +133,20 @@ struct GemmBatch {
         p.tn = int(cdiv(N, TN));
         tiles += int(cdiv(M, 64)) * p.tn;
         v.push_back(p);
+    }
+    // upload into a reusable plan (the batch is left empty)
+    int freeze(Ctx *c, GemmPlan<T, TN> &plan) {
+        plan.np = int(v.size());
+        plan.tiles = tiles;
+        if (!v.empty()) {
+            if (!plan.d.reset(c, v.size())) return fail(KRR_ERR_OOM, "grouped gemm: out of memory");
+            KRR_CUDA(cudaMemcpyAsync(plan.d.get(), v.data(), v.size() * sizeof(GemmProb<T>), cudaMemcpyHostToDevice,
+                                     c->stream));
+            KRR_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        v.clear();
+        tiles = 0;
+        return KRR_OK;
     }
     int launch(Ctx *c) {
         if (v.empty()) return KRR_OK;

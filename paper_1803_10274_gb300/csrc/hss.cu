@@ -494,6 +494,17 @@ struct HssImpl {
     DBuf<int32_t> IA;
     int nrhs_cap = 0;
     bool factored = false;
+    // cached solve plan (rebuilt when the factorization or nrhs changes)
+    struct LevelPlan {
+        DBuf<NodeDesc> dl;
+        GemmPlan<float, 16> f2, f3, f4, f1, fd1, fd2;
+        GemmPlan<double, 16> e2, e3, e4, e1, ed1, ed2;
+    };
+    std::vector<LevelPlan> plan;
+    int plan_nrhs = -1;
+    DBuf<float> ws_bf, ws_xf, ws_rs, ws_sm;
+    DBuf<__half> ws_rt;
+    int ws_nrhs = -1;
     double lambda = 0;
     int max_rank = 0, refine_steps = 0;
     double max_test_err = 0;
@@ -862,60 +873,95 @@ int factor(HssImpl *H) {
     return KRR_OK;
 }
 
+template <class T>
+GemmPlan<T, 16> &pick(HssImpl::LevelPlan &P, int which);
+template <>
+GemmPlan<float, 16> &pick<float>(HssImpl::LevelPlan &P, int which) {
+    GemmPlan<float, 16> *a[6] = {&P.f1, &P.f2, &P.f3, &P.f4, &P.fd1, &P.fd2};
+    return *a[which];
+}
+template <>
+GemmPlan<double, 16> &pick<double>(HssImpl::LevelPlan &P, int which) {
+    GemmPlan<double, 16> *a[6] = {&P.e1, &P.e2, &P.e3, &P.e4, &P.ed1, &P.ed2};
+    return *a[which];
+}
+
+// Per-level descriptors and GEMM problem lists of the ULV sweeps for nrhs
+// right-hand sides, uploaded once per factorization.
+template <class T>
+int build_solve_plan(HssImpl *H, int nrhs) {
+    Ctx *c = H->c;
+    T *F = farena<T>(H);
+    H->plan.clear();
+    H->plan.resize(H->H + 1);
+    for (int h = 0; h <= H->H; ++h) {
+        std::vector<int> &lv = H->by_height[h];
+        const int nn = int(lv.size());
+        if (!nn) continue;
+        HssImpl::LevelPlan &P = H->plan[h];
+        std::vector<NodeDesc> ld(nn);
+        for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
+        if (!P.dl.reset(c, nn)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(P.dl.get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
+        GemmBatch<T, 16> g1, g2, g3, g4, d1, d2;
+        if (h == H->H) {
+            for (const NodeDesc &N : ld)
+                g1.add(N.m, nrhs, N.m, T(1), F + N.drr, N.m, false, F + N.zvec, nrhs, false, T(0), F + N.xloc, nrhs);
+        } else {
+            for (const NodeDesc &N : ld) {
+                const int k = N.k, nr = N.m - N.k;
+                g2.add(nr, nrhs, k, T(-1), F + N.tmat, nr, true, F + N.btil, nrhs, false, T(1), F + N.xloc, nrhs);
+                g3.add(nr, nrhs, nr, T(1), F + N.drr, nr, false, F + N.xloc, nrhs, false, T(0), F + N.zvec, nrhs);
+                g4.add(k, nrhs, nr, T(-1), F + N.drs, k, true, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
+                d1.add(nr, nrhs, k, T(-1), F + N.ymat, k, false, F + N.btil, nrhs, false, T(1), F + N.zvec, nrhs);
+                d2.add(k, nrhs, nr, T(-1), F + N.tmat, nr, false, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
+            }
+        }
+        KRR_TRY(g1.freeze(c, pick<T>(P, 0)));
+        KRR_TRY(g2.freeze(c, pick<T>(P, 1)));
+        KRR_TRY(g3.freeze(c, pick<T>(P, 2)));
+        KRR_TRY(g4.freeze(c, pick<T>(P, 3)));
+        KRR_TRY(d1.freeze(c, pick<T>(P, 4)));
+        KRR_TRY(d2.freeze(c, pick<T>(P, 5)));
+    }
+    H->plan_nrhs = nrhs;
+    return KRR_OK;
+}
+
 // x_perm = H^{-1} y_perm (both n x nrhs in cluster order, precision T)
 template <class T>
 int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64_t ldx) {
     Ctx *c = H->c;
     T *F = farena<T>(H);
-    std::vector<DBuf<NodeDesc>> dls(H->H + 1);
+    if (H->plan_nrhs != nrhs) KRR_TRY(build_solve_plan<T>(H, nrhs));
     for (int h = 0; h <= H->H; ++h) {
-        std::vector<int> &lv = H->by_height[h];
-        const int nn = int(lv.size());
+        const int nn = int(H->by_height[h].size());
         if (!nn) continue;
+        HssImpl::LevelPlan &P = H->plan[h];
         const int is_root = h == H->H ? 1 : 0;
-        std::vector<NodeDesc> ld(nn);
-        for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
-        if (!dls[h].reset(c, nn)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
-        KRR_CUDA(cudaMemcpyAsync(dls[h].get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
-        { solve_gather_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), yperm, ldy, nrhs, F,
+        { solve_gather_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(P.dl.get(), H->ddesc.get(), yperm, ldy, nrhs, F,
                                                                  H->IA.get(), is_root); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         if (is_root) {
-            GemmBatch<T, 16> g;
-            for (const NodeDesc &N : ld)
-                g.add(N.m, nrhs, N.m, T(1), F + N.drr, N.m, false, F + N.zvec, nrhs, false, T(0), F + N.xloc, nrhs);
-            KRR_TRY(g.launch(c));
+            KRR_TRY(pick<T>(P, 0).run(c));
             break;
         }
-        GemmBatch<T, 16> g2, g3, g4;
-        for (const NodeDesc &N : ld) {
-            const int k = N.k, nr = N.m - N.k;
-            g2.add(nr, nrhs, k, T(-1), F + N.tmat, nr, true, F + N.btil, nrhs, false, T(1), F + N.xloc, nrhs);
-            g3.add(nr, nrhs, nr, T(1), F + N.drr, nr, false, F + N.xloc, nrhs, false, T(0), F + N.zvec, nrhs);
-            g4.add(k, nrhs, nr, T(-1), F + N.drs, k, true, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
-        }
-        KRR_TRY(g2.launch(c));
-        KRR_TRY(g3.launch(c));
-        KRR_TRY(g4.launch(c));
+        KRR_TRY(pick<T>(P, 1).run(c));
+        KRR_TRY(pick<T>(P, 2).run(c));
+        KRR_TRY(pick<T>(P, 3).run(c));
     }
     for (int h = H->H; h >= 0; --h) {
         const int nn = int(H->by_height[h].size());
         if (!nn) continue;
+        HssImpl::LevelPlan &P = H->plan[h];
         if (h < H->H) {
-            GemmBatch<T, 16> d1, d2;
-            for (int v : H->by_height[h]) {
-                const NodeDesc &N = H->desc[v];
-                const int k = N.k, nr = N.m - N.k;
-                d1.add(nr, nrhs, k, T(-1), F + N.ymat, k, false, F + N.btil, nrhs, false, T(1), F + N.zvec, nrhs);
-                d2.add(k, nrhs, nr, T(-1), F + N.tmat, nr, false, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
-            }
-            KRR_TRY(d1.launch(c));
-            KRR_TRY(d2.launch(c));
-            { solve_place_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), nrhs, F, H->IA.get(), xperm, ldx); ::krr::count_launch(); }
+            KRR_TRY(pick<T>(P, 4).run(c));
+            KRR_TRY(pick<T>(P, 5).run(c));
+            { solve_place_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(P.dl.get(), nrhs, F, H->IA.get(), xperm, ldx); ::krr::count_launch(); }
         } else if (H->desc[H->root].is_leaf) {  // single-leaf tree: the root's solve is the answer
-            { root_leaf_out_kernel<T><<<1, cta::kNT, 0, c->stream>>>(dls[h].get(), nrhs, F, xperm, ldx); ::krr::count_launch(); }
+            { root_leaf_out_kernel<T><<<1, cta::kNT, 0, c->stream>>>(P.dl.get(), nrhs, F, xperm, ldx); ::krr::count_launch(); }
         }
-        { scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dls[h].get(), H->ddesc.get(), nrhs, F); ::krr::count_launch(); }
+        { scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(P.dl.get(), H->ddesc.get(), nrhs, F); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
     return KRR_OK;
@@ -934,18 +980,37 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
     if (H->mixed()) {
         const int cols = 2 * nrhs;
         const int rpad = int(round_up(cols, 64));
-        DBuf<float> Rs(c, size_t(n) * cols), Sm(c, size_t(ma) * cols);
-        DBuf<__half> RTs(c, size_t(rpad) * H->ldrt);
-        if (!Rs.get() || !Sm.get() || !RTs.get()) return fail(KRR_ERR_OOM, "hss: out of memory");
-        { split16_kernel<<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(V, n, nrhs, ldv, Rs.get(), cols); ::krr::count_launch(); }
-        KRR_TRY(transpose_half(c, Rs.get(), n, cols, cols, RTs.get(), rpad, H->ldrt));
-        KRR_TRY(sample_mixed_prepared(c, XAa, ma, H->XB.get(), n, H->d, RTs.get(), cols, H->ldrt, nullptr, nullptr,
-                                      Sm.get(), cols, true));
+        DBuf<float> Rs_own, Sm_own;
+        DBuf<__half> RT_own;
+        float *Rs, *Sm;
+        __half *RTs;
+        if (ma == n) {  // the residual / GMRES path: workspaces kept across calls
+            if (H->ws_nrhs != nrhs) {
+                if (!H->ws_rs.reset(c, size_t(n) * cols) || !H->ws_sm.reset(c, size_t(n) * cols) ||
+                    !H->ws_rt.reset(c, size_t(rpad) * H->ldrt))
+                    return fail(KRR_ERR_OOM, "hss: out of memory");
+                H->ws_nrhs = nrhs;
+            }
+            Rs = H->ws_rs.get();
+            Sm = H->ws_sm.get();
+            RTs = H->ws_rt.get();
+        } else {
+            if (!Rs_own.reset(c, size_t(n) * cols) || !Sm_own.reset(c, size_t(ma) * cols) ||
+                !RT_own.reset(c, size_t(rpad) * H->ldrt))
+                return fail(KRR_ERR_OOM, "hss: out of memory");
+            Rs = Rs_own.get();
+            Sm = Sm_own.get();
+            RTs = RT_own.get();
+        }
+        { split16_kernel<<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(V, n, nrhs, ldv, Rs, cols); ::krr::count_launch(); }
+        KRR_TRY(transpose_half(c, Rs, n, cols, cols, RTs, rpad, H->ldrt));
+        KRR_TRY(sample_mixed_prepared(c, XAa, ma, H->XB.get(), n, H->d, RTs, cols, H->ldrt, nullptr, nullptr,
+                                      Sm, cols, true));
         if (y)
             { residual_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
-                y, ldy, Sm.get(), cols, 1, V, ldv, ma, nrhs, lambda, out, ldo, res_norms); ::krr::count_launch(); }
+                y, ldy, Sm, cols, 1, V, ldv, ma, nrhs, lambda, out, ldo, res_norms); ::krr::count_launch(); }
         else
-            { combine_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm.get(), cols, 1, V, ldv,
+            { combine_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(Sm, cols, 1, V, ldv,
                                                                                         lambda, ma, nrhs, out, ldo); ::krr::count_launch(); }
     } else {
         DBuf<double> Sm(c, size_t(ma) * nrhs), Xa64;
@@ -1042,7 +1107,10 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
     return KRR_OK;
 }
 
-int hss_factor_impl(HssImpl *H) { return H->mixed() ? factor<float>(H) : factor<double>(H); }
+int hss_factor_impl(HssImpl *H) {
+    H->plan_nrhs = -1;  // the cached solve plan refers to the old factors
+    return H->mixed() ? factor<float>(H) : factor<double>(H);
+}
 
 int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *alpha, int64_t lda, double tol,
                    int max_refine, double *resid) {
@@ -1057,11 +1125,13 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
     KRR_TRY((gather_rows<double, double>(c, y, ldy, H->perm.get(), n, nrhs, yp.get(), nrhs)));
     auto ulv = [&](const double *b, double *x) -> int {
         if (H->mixed()) {
-            DBuf<float> bf(c, size_t(n) * nrhs), xf(c, size_t(n) * nrhs);
-            if (!bf.get() || !xf.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
-            { convert_kernel<double, float><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(b, n * nrhs, bf.get()); ::krr::count_launch(); }
-            KRR_TRY(ulv_solve<float>(H, bf.get(), nrhs, nrhs, xf.get(), nrhs));
-            { convert_kernel<float, double><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(xf.get(), n * nrhs, x); ::krr::count_launch(); }
+            if (H->ws_bf.n < size_t(n) * nrhs &&
+                (!H->ws_bf.reset(c, size_t(n) * nrhs) || !H->ws_xf.reset(c, size_t(n) * nrhs)))
+                return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+            float *bf = H->ws_bf.get(), *xf = H->ws_xf.get();
+            { convert_kernel<double, float><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(b, n * nrhs, bf); ::krr::count_launch(); }
+            KRR_TRY(ulv_solve<float>(H, bf, nrhs, nrhs, xf, nrhs));
+            { convert_kernel<float, double><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(xf, n * nrhs, x); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             return KRR_OK;
         }
