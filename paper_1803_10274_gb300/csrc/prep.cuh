@@ -25,7 +25,7 @@ inline int aug_used(int d) { return 3 * d + 6; }
 inline int aug_kmma(int d) { return int(cdiv(aug_used(d), 16)); }
 inline int aug_chunks(int d) { return int(cdiv(aug_used(d), 64)); }
 inline int aug_kpad(int d) { return 64 * aug_chunks(d); }
-constexpr int kMaxMixedDim = 40;
+constexpr int kMaxMixedDim = 82;  // 3d + 6 <= 256: at most four 64-element chunks
 
 int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,

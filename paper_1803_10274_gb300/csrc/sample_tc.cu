@@ -54,6 +54,7 @@ struct Params {
     int ndist;    // distance / K buffers in tensor memory (2 or 3)
     int dist_col0;
     int split_k;  // 1: K = K_hi + K_lo (two FP16 parts, two product MMAs)
+    int a_bufs;   // row-tile (A) buffers in shared memory: 2, or 1 for wide feature rows
     uint32_t off_a, off_stage, stage_bytes, off_bar;
     const int32_t *leaf_a, *leaf_b;
     float *S;
@@ -254,8 +255,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             c.flags(nloc, nct);
             if (c.first) {
                 const int seg = c.seg++;
-                const int ab = seg & 1;
-                if (!mbar_wait(&bars[BAR_AEMPTY + ab], uint32_t((seg >> 1) & 1) ^ 1u, abort_flag, kWaitBudget,
+                const int ab = P.a_bufs == 2 ? (seg & 1) : 0;
+                const int au = P.a_bufs == 2 ? (seg >> 1) : seg;  // use count of that buffer
+                if (!mbar_wait(&bars[BAR_AEMPTY + ab], uint32_t(au & 1) ^ 1u, abort_flag, kWaitBudget,
                                P.status, 1))
                     break;
                 mbar_expect_tx(&bars[BAR_AFULL + ab], a_bytes);
@@ -279,7 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int u = issued - 1 - k;
             mbar_wait_bounded(&bars[BAR_FULL + (u % NS)], uint32_t((u / NS) & 1), kWaitBudget);
         }
-        if (a_issued >= 0) mbar_wait_bounded(&bars[BAR_AFULL + (a_issued & 1)], uint32_t((a_issued >> 1) & 1), kWaitBudget);
+        if (a_issued >= 0)
+            mbar_wait_bounded(&bars[BAR_AFULL + (P.a_bufs == 2 ? (a_issued & 1) : 0)],
+                              uint32_t((P.a_bufs == 2 ? (a_issued >> 1) : a_issued) & 1), kWaitBudget);
     } else if (warp == 1 && lane == 0 && nloc > 0) {
         // ------------------------------------------------ MMA issuer
         // The distance GEMM of tile loc + ND - 1 is issued before waiting for
@@ -297,13 +301,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             cd.flags(nloc, nct);
             if (cd.first) {
                 ++cd.seg;
-                if (!mbar_wait(&bars[BAR_AFULL + ((cd.seg - 1) & 1)], uint32_t(((cd.seg - 1) >> 1) & 1), abort_flag,
+                const int sg = cd.seg - 1;
+                if (!mbar_wait(&bars[BAR_AFULL + (P.a_bufs == 2 ? (sg & 1) : 0)],
+                               uint32_t((P.a_bufs == 2 ? (sg >> 1) : sg) & 1), abort_flag,
                                kWaitBudget, P.status, 3))
                     return false;
             }
             if (!mbar_wait(&bars[BAR_FULL + cd.stage], cd.sphase, abort_flag, kWaitBudget, P.status, 4)) return false;
             tc_fence_after();
-            const uint32_t a_base = smem_u32(smem + P.off_a + ((cd.seg - 1) & 1) * a_bytes);
+            const int abuf = P.a_bufs == 2 ? ((cd.seg - 1) & 1) : 0;
+            const uint32_t a_base = smem_u32(smem + P.off_a + abuf * a_bytes);
             const uint32_t b_base = smem_u32(smem + P.off_stage + cd.stage * P.stage_bytes);
             const uint32_t d_tmem = tmem + uint32_t(P.dist_col0 + cd.db * kBN);
             for (int k = 0; k < P.kmma; ++k) {
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma_ss(d_tmem, sdesc_k_sw128(a_base + off), sdesc_k_sw128(b_base + off), idesc_d, k > 0);
             }
             tc_commit(&bars[BAR_DFULL + cd.db]);
-            if (cd.last) tc_commit(&bars[BAR_AEMPTY + ((cd.seg - 1) & 1)]);
+            if (cd.last) tc_commit(&bars[BAR_AEMPTY + abuf]);
             cd.next(nct, NS, ND);
             return true;
         };
@@ -480,7 +487,7 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
                      const int32_t *leaf_b, float *S, int64_t lds, bool split_k) {
     if (rpad % 64 != 0 || rpad < 64 || rpad > 256) return fail(KRR_ERR_INVALID_ARG, "sample_tc: r must be 64..256, /64");
-    if (nchunk < 1 || nchunk > 2) return fail(KRR_ERR_INVALID_ARG, "sample_tc: feature dimension too large");
+    if (nchunk < 1 || nchunk > 4) return fail(KRR_ERR_INVALID_ARG, "sample_tc: feature dimension too large");
     if (ma <= 0 || nb <= 0) return KRR_OK;
     if (ldrt % 8 != 0) return fail(KRR_ERR_INVALID_ARG, "sample_tc: ldrt must be a multiple of 8");
     CUtensorMap mA, mB, mR;
@@ -507,10 +514,12 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     P.ndist = (512 - P.dist_col0) / 128;
     if (P.ndist > 3) P.ndist = 3;
     const uint32_t a_bytes = nchunk * tc::kChunkBytes;
-    P.off_a = 0;
-    P.off_stage = 2 * a_bytes;
     P.stage_bytes = a_bytes + 2 * rpad * 128;
     const int budget = 227 * 1024 - 1024 - 256;  // alignment slack + barriers
+    // two row-tile buffers when they fit beside two stages, else one
+    P.a_bufs = (2 * a_bytes + 2 * P.stage_bytes <= uint32_t(budget)) ? 2 : 1;
+    P.off_a = 0;
+    P.off_stage = P.a_bufs * a_bytes;
     int ns = int((budget - int(P.off_stage)) / int(P.stage_bytes));
     if (ns > tc::kMaxStages) ns = tc::kMaxStages;
     if (ns < 2) return fail(KRR_ERR_INVALID_ARG, "sample_tc: tile does not fit in shared memory");

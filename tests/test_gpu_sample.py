@@ -44,7 +44,9 @@ def _cuda(a):
                                          (777, 1313, 8, 40, 1.3),       # ragged tiles, padded columns
                                          (300, 129, 3, 256, 0.7),       # one column past a tile
                                          (1500, 2000, 19, 100, 2.0),    # one 64-wide feature chunk, full
-                                         (700, 900, 33, 300, 1.5)])     # two chunks, 2 launches of columns
+                                         (700, 900, 33, 300, 1.5),      # two chunks, 2 launches of columns
+                                         (640, 1000, 54, 100, 2.0),     # three chunks, one row-tile buffer
+                                         (300, 513, 80, 64, 3.0)])      # four chunks
 def test_mixed_matches_oracle(K, ctx, ma, nb, d, r, h):
     Xa = synth.mixture(ma, d, 4, 0.7, 10 + d)[0].astype(np.float32)
     Xb = synth.mixture(nb, d, 4, 0.7, 20 + d)[0].astype(np.float32)
