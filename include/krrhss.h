@@ -238,6 +238,47 @@ int hss_solve(krr_hss *H, const double *y, int32_t nrhs, int64_t ldy,
 int krr_predict(krr_hss *H, const float *Xt, int64_t m, const double *alpha,
                 int32_t nrhs, int64_t lda, double *out, int64_t ldo);
 
+/* ---------------------------------------------------------------------
+ * Held-out squared-error loss and its gradient in h, lambda and the
+ * training points: the quantities Section 5.3 tunes (h and lambda of
+ * Eq. (1) and Algorithm 1, chosen on held-out data) made differentiable.
+ * With alpha = (K + lambda I)^{-1} y (solved through H as hss_solve with
+ * tol) and g = K(Xt, X) alpha - yt:
+ *     L = 1/2 sum_k g_k^2.
+ * With a = K(Xt, X)^T g and z = (K + lambda I)^{-1} a (a second solve; K
+ * is symmetric), the adjoint gives
+ *     dL/dlambda = -z . alpha
+ *     dL/dh      = h^-3 [ g^T (Kt o Dt) alpha - z^T (K o D) alpha ]
+ *     dL/dx_p    = h^-2 [ alpha_p sum_k g_k Kt_kp (xt_k - x_p)
+ *                  - sum_j (z_p alpha_j + z_j alpha_p) K_pj (x_j - x_p) ]
+ * where D and Dt hold squared distances.  Each sum over kernel entries is
+ * one fused product (the kernel recomputed, never stored) against the
+ * augmented columns [v, v |x|^2, v x] of the expansion
+ * |u - v|^2 = |u|^2 - 2 u.v + |v|^2, on coordinates centred on the training
+ * mean.  The arithmetic follows H's precision (KRR_MIXED: tensor-core
+ * products with FP16 hi/lo splits of the kernel and of the columns, FP64
+ * accumulation of the sums; KRR_FP64: FP64 throughout).
+ *   H        compressed at X, h, lambda (hss_compress; lambda as last set by
+ *            hss_update_lambda); factored here if needed
+ *   Xt       device float m x d held-out points (scaled like X), m >= 1
+ *   y        device double[n] training targets, original row order
+ *   yt       device double[m] held-out targets
+ *   tol, max_refine  as hss_solve, for each of the two solves
+ *   loss     host double[1] out
+ *   dh, dlambda  host double[1] outs, or NULL
+ *   dX       device double n x d out (row stride lddx >= d), original row
+ *            order, or NULL
+ *   alpha    device double[n] out (original order), or NULL
+ *   resid    host double[1] out (may be NULL): the larger final residual
+ *            of the two solves
+ * With dh, dlambda and dX all NULL only the first solve and the held-out
+ * product run.  Returns KRR_ERR_NO_CONVERGENCE (outputs still written)
+ * when a solve stops above tol.  Synchronizes. */
+int krr_heldout_grad(krr_hss *H, const float *Xt, int64_t m, const double *y,
+                     const double *yt, double tol, int32_t max_refine,
+                     double *loss, double *dh, double *dlambda, double *dX,
+                     int64_t lddx, double *alpha, double *resid);
+
 typedef struct {
     int64_t n;
     int32_t n_nodes, n_levels, max_rank, samples, rounds, refine_steps;

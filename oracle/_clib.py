@@ -39,6 +39,8 @@ def lib():
             i64 = ctypes.c_int64
             L.okrr_kernel_matrix.argtypes = [P, i64, P, i64, ctypes.c_int, ctypes.c_double, P]
             L.okrr_kernel_matrix.restype = None
+            L.okrr_sqdist_matrix.argtypes = [P, i64, P, i64, ctypes.c_int, P]
+            L.okrr_sqdist_matrix.restype = None
             L.okrr_kernel_product.argtypes = [P, i64, P, i64, ctypes.c_int, ctypes.c_double,
                                               P, ctypes.c_int, P, P, P, i64, P, P]
             L.okrr_kernel_product.restype = None

@@ -34,6 +34,23 @@ void okrr_kernel_matrix(const double *Xa, int64_t ma, const double *Xb,
             K[i * nb + j] = kval(Xa + i * d, Xb + j * d, d, inv2h2);
 }
 
+/* Squared distances D(i, j) = sum_k (Xa_ik - Xb_jk)^2 (the exponent of
+ * Eq. (1) times -2 h^2), ma x nb row-major, difference form. */
+void okrr_sqdist_matrix(const double *Xa, int64_t ma, const double *Xb,
+                        int64_t nb, int d, double *D) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < ma; ++i)
+        for (int64_t j = 0; j < nb; ++j) {
+            const double *a = Xa + i * d, *b = Xb + j * d;
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) {
+                double t = a[k] - b[k];
+                s += t * t;
+            }
+            D[i * nb + j] = s;
+        }
+}
+
 /*
  * S(i, :) = sum_j w_ij K(Xa_i, Xb_j) R(j, :) for the rows listed in rows[]
  * (rows == NULL means all ma rows, in order).  w_ij = 0 when both leaf

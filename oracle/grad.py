@@ -26,10 +26,16 @@ import numpy as np
 from . import kernel, solve
 
 
-def _sqdist(A, B):
-    A = np.asarray(A, dtype=np.float64)
-    B = np.asarray(B, dtype=np.float64)
-    return ((A[:, None, :] - B[None, :, :]) ** 2).sum(-1)
+def _spd_factor_solver(A):
+    """Solver for A x = b reusing one factorization of the SPD matrix A
+    (LAPACK Cholesky above the size where the oracle's own loops get
+    slow, as in ``solve.spd_solve``)."""
+    if A.shape[0] > solve.LAPACK_ABOVE:
+        import scipy.linalg as sl
+        c = sl.cho_factor(A, lower=True)
+        return lambda b: sl.cho_solve(c, b)
+    L = solve.cholesky(A)
+    return lambda b: solve.backward_sub_t(L, solve.forward_sub(L, b))
 
 
 def loss(X, Xt, y, yt, h, lam):
@@ -48,15 +54,17 @@ def loss_and_grad(X, Xt, y, yt, h, lam):
     n = X.shape[0]
     K = kernel.kernel_matrix(X, X, h)
     A = K + lam * np.eye(n)
-    alpha = solve.spd_solve(A, y)
+    sol = _spd_factor_solver(A)
+    del A
+    alpha = sol(y)
     Kt = kernel.kernel_matrix(Xt, X, h)
     g = Kt @ alpha - yt
     L = 0.5 * float(g @ g)
     a = Kt.T @ g
-    z = solve.spd_solve(A, a)
+    z = sol(a)
     dlam = -float(z @ alpha)
-    D = _sqdist(X, X)
-    Dt = _sqdist(Xt, X)
+    D = kernel.sqdist_matrix(X, X)
+    Dt = kernel.sqdist_matrix(Xt, X)
     dh = (float(g @ ((Kt * Dt) @ alpha)) - float(z @ ((K * D) @ alpha))) / h ** 3
     # dL/dX
     t1 = alpha[:, None] * (Kt.T @ (g[:, None] * Xt) - X * (Kt.T @ g)[:, None])

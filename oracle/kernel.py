@@ -26,6 +26,16 @@ def kernel_matrix(Xa, Xb, h: float) -> np.ndarray:
     return K
 
 
+def sqdist_matrix(Xa, Xb) -> np.ndarray:
+    """Squared distances ||xa_i - xb_j||^2 (ma x nb), difference form."""
+    Xa, Xb = _f64(Xa), _f64(Xb)
+    ma, d = Xa.shape
+    nb = Xb.shape[0]
+    D = np.empty((ma, nb))
+    _clib.lib().okrr_sqdist_matrix(_clib.ptr(Xa), ma, _clib.ptr(Xb), nb, d, _clib.ptr(D))
+    return D
+
+
 def kernel_product(Xa, Xb, h: float, R, leaf_a=None, leaf_b=None, rows=None,
                    want_abs: bool = False):
     """S = W o K(Xa, Xb) @ R without storing K.

@@ -63,6 +63,8 @@ SIGNATURES = {
     "hss_factor": (i32, [P]),
     "hss_solve": (i32, [P, P, i32, i64, P, i64, f64, i32, ctypes.POINTER(f64)]),
     "krr_predict": (i32, [P, P, i64, P, i32, i64, P, i64]),
+    "krr_heldout_grad": (i32, [P, P, i64, P, P, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(f64),
+                               ctypes.POINTER(f64), P, i64, P, ctypes.POINTER(f64)]),
     "hss_stats": (i32, [P, ctypes.POINTER(krr_hss_stats)]),
     "hss_permutation": (P, [P]),
     "hss_destroy": (None, [P]),

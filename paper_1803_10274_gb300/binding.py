@@ -14,7 +14,8 @@ from . import _lib
 from ._lib import KRR_FP64, KRR_MIXED, KRRError, check, lib
 
 __all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "krr_standardize", "krr_cluster", "krr_sample",
-           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "HSS", "hss_compress", "default_options", "lib"]
+           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "HSS", "hss_compress", "default_options",
+           "HeldOutLoss", "krr_heldout_loss", "lib"]
 
 
 _shutting_down = [False]
@@ -194,6 +195,27 @@ class HSS:
                                 _ptr(out), out.stride(0)))
         return out
 
+    def heldout_grad(self, Xt, y, yt, tol=1e-6, max_refine=200, grad=True, want_alpha=False):
+        """krr_heldout_grad: {"loss", "dh", "dlambda", "dX" (n x d float64,
+        original order), "alpha", "resid"}; without grad only the loss."""
+        _need(Xt, torch.float32, "Xt")
+        y = y.reshape(-1).contiguous()
+        yt = yt.reshape(-1).contiguous()
+        _need(y, torch.float64, "y", dims=1)
+        _need(yt, torch.float64, "yt", dims=1)
+        d = Xt.shape[1]
+        loss, dh, dl, res = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double(-1.0)
+        dX = torch.empty(self.n, d, dtype=torch.float64, device=Xt.device) if grad else None
+        alpha = torch.empty(self.n, dtype=torch.float64, device=Xt.device) if want_alpha else None
+        check(lib().krr_heldout_grad(self.h, _ptr(Xt.contiguous()), Xt.shape[0], _ptr(y), _ptr(yt), tol, max_refine,
+                                     ctypes.byref(loss), ctypes.byref(dh) if grad else None,
+                                     ctypes.byref(dl) if grad else None, _ptr(dX), d, _ptr(alpha),
+                                     ctypes.byref(res)))
+        out = {"loss": loss.value, "resid": res.value, "alpha": alpha}
+        if grad:
+            out.update(dh=dh.value, dlambda=dl.value, dX=dX)
+        return out
+
     def stats(self):
         st = _lib.krr_hss_stats()
         check(lib().hss_stats(self.h, ctypes.byref(st)))
@@ -222,3 +244,50 @@ def hss_compress(ctx, X, opts):
     h = ctypes.c_void_p()
     check(lib().hss_compress(ctx.h, _ptr(X), n, d, ctypes.byref(opts), ctypes.byref(h)))
     return HSS(ctx, h, n)
+
+
+class HeldOutLoss(torch.autograd.Function):
+    """L(X, h, lambda) = 1/2 ||K(Xt, X) alpha - yt||^2 with
+    alpha = (K + lambda I)^{-1} y, through an HSS solve.
+
+    forward compresses K + lambda I at (X, h, lambda) and calls
+    krr_heldout_grad, which also evaluates the adjoint gradient when any of
+    X, h, lambda requires it; backward scales that gradient by the incoming
+    one.  h and lambda are 0-dim tensors (or floats, then not
+    differentiated)."""
+
+    @staticmethod
+    def forward(fctx, X, h, lam, Xt, y, yt, kctx, opts, tol, max_refine):
+        import copy
+        o = copy.copy(opts)
+        o.h = float(h)
+        o.lam = float(lam)
+        want = any(fctx.needs_input_grad[:3])
+        H = hss_compress(kctx, X.detach().contiguous(), o)
+        try:
+            r = H.heldout_grad(Xt.detach(), y.detach().to(torch.float64), yt.detach().to(torch.float64), tol,
+                               max_refine, grad=want)
+        finally:
+            H.close()
+        dev = X.device
+        if want:
+            fctx.save_for_backward(r["dX"], torch.tensor(r["dh"], dtype=torch.float64, device=dev),
+                                   torch.tensor(r["dlambda"], dtype=torch.float64, device=dev))
+        fctx.h_is_tensor = torch.is_tensor(h)
+        fctx.lam_is_tensor = torch.is_tensor(lam)
+        return torch.tensor(r["loss"], dtype=torch.float64, device=dev)
+
+    @staticmethod
+    def backward(fctx, gout):
+        dX, dh, dl = fctx.saved_tensors
+        gX = (gout * dX).to(torch.float32) if fctx.needs_input_grad[0] else None
+        gh = (gout * dh) if fctx.h_is_tensor and fctx.needs_input_grad[1] else None
+        gl = (gout * dl) if fctx.lam_is_tensor and fctx.needs_input_grad[2] else None
+        return gX, gh, gl, None, None, None, None, None, None, None
+
+
+def krr_heldout_loss(ctx, X, h, lam, Xt, y, yt, opts=None, tol=1e-6, max_refine=200):
+    """Differentiable held-out loss (see HeldOutLoss)."""
+    if opts is None:
+        opts = default_options()
+    return HeldOutLoss.apply(X, h, lam, Xt, y, yt, ctx, opts, tol, max_refine)

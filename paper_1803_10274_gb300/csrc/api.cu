@@ -19,8 +19,13 @@ int fail(int code, const std::string &msg) {
     set_error(msg);
     return code;
 }
-int cuda_fail(cudaError_t e, const char *what) {
-    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    std::string where;
+    if (file) {
+        const char *b = std::strrchr(file, '/');
+        where = " (" + std::string(b ? b + 1 : file) + ":" + std::to_string(line) + ")";
+    }
+    set_error(std::string(what) + ": " + cudaGetErrorString(e) + where);
     return e == cudaErrorMemoryAllocation ? KRR_ERR_OOM : KRR_ERR_CUDA;
 }
 

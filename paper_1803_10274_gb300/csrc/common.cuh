@@ -15,12 +15,12 @@ namespace krr {
 // ---------------------------------------------------------------- errors
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
-int cuda_fail(cudaError_t e, const char *what);
+int cuda_fail(cudaError_t e, const char *what, const char *file = nullptr, int line = 0);
 
-#define KRR_CUDA(call)                                             \
-    do {                                                           \
-        cudaError_t e_ = (call);                                   \
-        if (e_ != cudaSuccess) return ::krr::cuda_fail(e_, #call); \
+#define KRR_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) return ::krr::cuda_fail(e_, #call, __FILE__, __LINE__); \
     } while (0)
 
 #define KRR_TRY(call)                 \

@@ -518,6 +518,20 @@ double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Read (and clear) the context's device status word; an error latched by a
+// kernel (a wait past its limit, a zero pivot, an input out of range)
+// fails the call.  Synchronizes.
+int take_status(Ctx *c, const char *what) {
+    DevStatus st{};
+    KRR_CUDA(cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    if (st.code != 0) {
+        KRR_CUDA(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->stream));
+        return fail(st.code, std::string(what) + ": device error (site " + std::to_string(st.where) + ")");
+    }
+    return KRR_OK;
+}
+
 // KRR_TRACE=1 in the environment: synchronize and print the time of every
 // phase of every level (a diagnostic; it serializes the stream).
 struct Tracer {
@@ -692,7 +706,11 @@ int id_sweep(HssImpl *H, bool &need_more) {
             KRR_TRY(gb.launch(c));
             tr.mark("parent_sloc", h, nn, mmax);
         }
-        if (mmax < kBigNode && nn >= c->num_sms) {
+        if (mmax == 0) {
+            // every node of the level is empty (its children have rank 0)
+            KRR_CUDA(cudaMemsetAsync(dranks.get(), 0, nn * sizeof(int), c->stream));
+            KRR_CUDA(cudaMemsetAsync(derr.get(), 0, 2 * nn * sizeof(float), c->stream));
+        } else if (mmax < kBigNode && nn >= c->num_sms) {
             const size_t smem = size_t(r) * sizeof(T);
             static bool attr = false;
             if (!attr) {
@@ -788,6 +806,7 @@ int compress(HssImpl *H) {
     while (true) {
         const double s0 = now_ms();
         KRR_TRY(sample_columns<T>(H, c0, H->r));
+        KRR_TRY(take_status(c, "hss_compress"));
         KRR_CUDA(cudaStreamSynchronize(c->stream));
         ts += now_ms() - s0;
         ++H->rounds;
@@ -1112,17 +1131,15 @@ int hss_factor_impl(HssImpl *H) {
     return H->mixed() ? factor<float>(H) : factor<double>(H);
 }
 
-int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *alpha, int64_t lda, double tol,
-                   int max_refine, double *resid) {
+// Solve (K + lambda I) a = y in cluster order: yp, ap device double
+// n x nrhs (row stride nrhs).  tol <= 0: one ULV solve; else restarted
+// GMRES preconditioned by the ULV solve.  rmax: final relative residual
+// (max over columns) or -1.
+int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, int max_refine, double &rmax) {
     Ctx *c = H->c;
-    if (!H->factored) KRR_TRY(hss_factor_impl(H));
-    const double t0 = now_ms();
     const int64_t n = H->n;
-    if (nrhs > H->nrhs_cap) return fail(KRR_ERR_INVALID_ARG, "hss_solve: nrhs > 64");
-    DBuf<double> yp(c, size_t(n) * nrhs), ap(c, size_t(n) * nrhs), res(c, size_t(n) * nrhs), dx(c, size_t(n) * nrhs),
-        norms(c, 2 * nrhs);
-    if (!yp.get() || !ap.get() || !res.get() || !dx.get() || !norms.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
-    KRR_TRY((gather_rows<double, double>(c, y, ldy, H->perm.get(), n, nrhs, yp.get(), nrhs)));
+    DBuf<double> res(c, size_t(n) * nrhs), norms(c, 2 * nrhs);
+    if (!res.get() || !norms.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
     auto ulv = [&](const double *b, double *x) -> int {
         if (H->mixed()) {
             if (H->ws_bf.n < size_t(n) * nrhs &&
@@ -1137,10 +1154,10 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
         }
         return ulv_solve<double>(H, b, nrhs, nrhs, x, nrhs);
     };
-    double rmax = -1.0;
+    rmax = -1.0;
     H->refine_steps = 0;
     if (tol <= 0) {
-        KRR_TRY(ulv(yp.get(), ap.get()));
+        KRR_TRY(ulv(yp, ap));
     } else {
         // Right-preconditioned restarted GMRES, one Krylov space per column:
         // A M^{-1} u = y, alpha = M^{-1} u, M^{-1} = the ULV solve.  Every
@@ -1153,7 +1170,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
             coef(c, size_t(mres + 1) * nrhs), sc(c, nrhs), ynorm(c, 2 * nrhs);
         if (!V.get() || !Wv.get() || !Zv.get() || !dots.get() || !coef.get() || !sc.get() || !ynorm.get())
             return fail(KRR_ERR_OOM, "hss_solve: out of memory");
-        KRR_CUDA(cudaMemsetAsync(ap.get(), 0, nn * sizeof(double), c->stream));
+        KRR_CUDA(cudaMemsetAsync(ap, 0, nn * sizeof(double), c->stream));
         const unsigned g1 = unsigned(cdiv(nn, 256));
         const unsigned gd = unsigned(std::min<int64_t>(256, cdiv(nn, 256)));
         auto mdot = [&](const double *A, int nb, const double *B) -> int {
@@ -1164,7 +1181,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
         };
         std::vector<double> ynrm(nrhs), hd((mres + 1) * nrhs), hd2((mres + 1) * nrhs);
         Tracer tr(c);
-        KRR_TRY(mdot(yp.get(), 1, yp.get()));
+        KRR_TRY(mdot(yp, 1, yp));
         KRR_CUDA(cudaMemcpyAsync(ynrm.data(), dots.get(), nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
         KRR_CUDA(cudaStreamSynchronize(c->stream));
         for (auto &v : ynrm) v = std::sqrt(v) > 0 ? std::sqrt(v) : 1.0;
@@ -1175,8 +1192,8 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
         for (int cycle = 0;; ++cycle) {
             // r = y - A alpha (precise product); V0 = r / |r|
             KRR_CUDA(cudaMemsetAsync(norms.get(), 0, 2 * nrhs * sizeof(double), c->stream));
-            KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, ap.get(), nrhs, nrhs, res.get(), nrhs, H->lambda,
-                              yp.get(), nrhs, norms.get()));
+            KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, ap, nrhs, nrhs, res.get(), nrhs, H->lambda,
+                              yp, nrhs, norms.get()));
             std::vector<double> hn(2 * nrhs);
             KRR_CUDA(cudaMemcpyAsync(hn.data(), norms.get(), 2 * nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
             KRR_CUDA(cudaStreamSynchronize(c->stream));
@@ -1270,13 +1287,28 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
             KRR_CUDA(cudaMemsetAsync(Wv.get(), 0, nn * sizeof(double), c->stream));
             { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, jdone, coef.get(), n, nrhs); ::krr::count_launch(); }
             KRR_TRY(ulv(Wv.get(), Zv.get()));
-            { axpy_kernel<<<g1, 256, 0, c->stream>>>(ap.get(), Zv.get(), nn); ::krr::count_launch(); }
+            { axpy_kernel<<<g1, 256, 0, c->stream>>>(ap, Zv.get(), nn); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
         }
         H->refine_steps = total_it;
     }
+    return KRR_OK;
+}
+
+int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *alpha, int64_t lda, double tol,
+                   int max_refine, double *resid) {
+    Ctx *c = H->c;
+    if (!H->factored) KRR_TRY(hss_factor_impl(H));
+    const double t0 = now_ms();
+    const int64_t n = H->n;
+    if (nrhs > H->nrhs_cap) return fail(KRR_ERR_INVALID_ARG, "hss_solve: nrhs > 64");
+    DBuf<double> yp(c, size_t(n) * nrhs), ap(c, size_t(n) * nrhs);
+    if (!yp.get() || !ap.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+    KRR_TRY((gather_rows<double, double>(c, y, ldy, H->perm.get(), n, nrhs, yp.get(), nrhs)));
+    double rmax = -1.0;
+    KRR_TRY(solve_perm(H, yp.get(), nrhs, ap.get(), tol, max_refine, rmax));
     KRR_TRY((scatter_rows<double, double>(c, ap.get(), nrhs, H->perm.get(), n, nrhs, alpha, lda)));
-    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    KRR_TRY(take_status(c, "hss_solve"));
     if (resid) *resid = rmax;
     H->t_solve = now_ms() - t0;
     if (tol > 0 && rmax > tol) return fail(KRR_ERR_NO_CONVERGENCE, "hss_solve: refinement did not reach tol");
@@ -1296,6 +1328,238 @@ int hss_predict_impl(HssImpl *H, const float *Xt, int64_t m, const double *alpha
         KRR_TRY(augment(c, Xt, m, H->d, H->opt.h, 0, xa.get(), H->kpad));
     }
     return hss_apply(H, Xt, xa.get(), m, ap.get(), nrhs, nrhs, out, ldo, 0.0, nullptr, 0, nullptr);
+}
+
+// ------------------------------------------------------------ gradient
+// Held-out loss L = 1/2 ||K(Xt, X) alpha - yt||^2 with alpha =
+// (K + lambda I)^{-1} y and its adjoint gradient in h, lambda and X (the
+// parameters of Eq. (1) and Algorithm 1 that Section 5.3 tunes on held-out
+// data).  Every kernel sum is a fused product against augmented columns,
+// using  |u - v|^2 = |u|^2 - 2 u.v + |v|^2  on coordinates centred on the
+// training mean (the kernel depends only on differences).
+namespace {
+
+// sum[q] += sum_i X(i, q)  (FP64; blockDim.x threads over a grid-stride)
+__global__ void colsum_kernel(const float *X, int64_t n, int d, double *sum) {
+    extern __shared__ double sh[];
+    for (int q = threadIdx.x; q < d; q += blockDim.x) sh[q] = 0.0;
+    __syncthreads();
+    const int64_t tot = n * d;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < tot; e += int64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&sh[e % d], double(X[e]));
+    __syncthreads();
+    for (int q = threadIdx.x; q < d; q += blockDim.x) atomicAdd(&sum[q], sh[q]);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per training row i (cluster order), xc = x_i - mean:
+//   which 0: V(i, 0 .. d+1) = [v_i, v_i |xc|^2, v_i xc]
+//   which 1: V(i, d+2 .. 2d+2) = [v_i, v_i xc]
+__global__ void grad_cols_kernel(const float *X, int64_t n, int d, const double *sum, double inv_n, const double *v,
+                                 int which, double *V, int64_t ldv) {
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int l = threadIdx.x & 31;
+    if (i >= n) return;
+    const double vi = v[i];
+    double nrm = 0.0;
+    double *row = V + i * ldv;
+    for (int q = l; q < d; q += 32) {
+        const double xc = double(X[i * d + q]) - sum[q] * inv_n;
+        nrm += xc * xc;
+        if (which == 0) row[2 + q] = vi * xc;
+        else row[d + 3 + q] = vi * xc;
+    }
+    nrm = warp_sum(nrm);
+    if (l == 0) {
+        if (which == 0) {
+            row[0] = vi;
+            row[1] = vi * nrm;
+        } else {
+            row[d + 2] = vi;
+        }
+    }
+}
+
+// One warp per held-out row k.  P(k, :) = K(xt_k, X) [alpha, alpha |xc|^2,
+// alpha xc] (only column 0 when full == 0).  g_k = P(k, 0) - yt_k;
+// W(k, :) = [g_k, g_k xtc_k];  acc[0] += g_k^2 / 2;
+// acc[1] += g_k (|xtc_k|^2 P(k,0) - 2 xtc_k . P(k, 2..) + P(k, 1))
+//        = g_k sum_i K(xt_k, x_i) |xt_k - x_i|^2 alpha_i.
+__global__ void grad_test_kernel(const float *Xt, int64_t m, int d, const double *sum, double inv_n,
+                                 const double *P, int64_t ldp, const double *yt, int full, double *W, int64_t ldw,
+                                 double *acc) {
+    const int64_t k = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int l = threadIdx.x & 31;
+    if (k >= m) return;
+    const double *pk = P + k * ldp;
+    const double g = pk[0] - yt[k];
+    double nrm = 0.0, dot = 0.0;
+    if (full) {
+        for (int q = l; q < d; q += 32) {
+            const double xc = double(Xt[k * d + q]) - sum[q] * inv_n;
+            nrm += xc * xc;
+            dot += xc * pk[2 + q];
+            W[k * ldw + 1 + q] = g * xc;
+        }
+        nrm = warp_sum(nrm);
+        dot = warp_sum(dot);
+    }
+    if (l == 0) {
+        atomicAdd(&acc[0], 0.5 * g * g);
+        if (full) {
+            W[k * ldw] = g;
+            atomicAdd(&acc[1], g * (nrm * pk[0] - 2.0 * dot + pk[1]));
+        }
+    }
+}
+
+// One warp per training row p (cluster order).  Q(p, :) = K(x_p, Xt) [g, g xtc]
+// (so Q(p, 0) = a_p), Pn(p, :) = K(x_p, X) [alpha, alpha |xc|^2, alpha xc,
+// z, z xc].  acc[2] += z_p sum_j K_pj |x_p - x_j|^2 alpha_j;
+// acc[3] += z_p alpha_p;  dX(perm[p], :) = h^-2 [alpha_p (Q(p,1..) - xc_p Q(p,0))
+//   - z_p (Pn(p,2..) - xc_p Pn(p,0)) - alpha_p (Pn(p,d+3..) - xc_p Pn(p,d+2))].
+__global__ void grad_train_kernel(const float *X, int64_t n, int d, const double *sum, double inv_n,
+                                  const double *alpha, const double *z, const double *Q, int64_t ldq,
+                                  const double *Pn, int64_t ldpn, double inv_h2, const int32_t *perm, double *dX,
+                                  int64_t lddx, double *acc) {
+    const int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int l = threadIdx.x & 31;
+    if (p >= n) return;
+    const double ap = alpha[p], zp = z[p];
+    const double *qp = Q + p * ldq;
+    const double *pp = Pn + p * ldpn;
+    double *out = dX ? dX + int64_t(perm[p]) * lddx : nullptr;
+    double nrm = 0.0, dot = 0.0;
+    for (int q = l; q < d; q += 32) {
+        const double xc = double(X[p * d + q]) - sum[q] * inv_n;
+        nrm += xc * xc;
+        dot += xc * pp[2 + q];
+        if (out) {
+            const double t = ap * (qp[1 + q] - xc * qp[0]) - zp * (pp[2 + q] - xc * pp[0]) -
+                             ap * (pp[d + 3 + q] - xc * pp[d + 2]);
+            out[q] = inv_h2 * t;
+        }
+    }
+    nrm = warp_sum(nrm);
+    dot = warp_sum(dot);
+    if (l == 0) {
+        atomicAdd(&acc[2], zp * (nrm * pp[0] - 2.0 * dot + pp[1]));
+        atomicAdd(&acc[3], zp * ap);
+    }
+}
+
+}  // namespace
+
+// out (ma x nv, row stride ldo) = K(Xa, Xb) V for V (nb x nv, row stride
+// ldv): no lambda, no leaf mask.  Mixed: XAa / XBb are the augmented
+// operands (rows in role 0, columns in role 1); V is split into FP16 hi/lo
+// parts and K into a hi/lo pair, so the product keeps about FP32 accuracy.
+// FP64: Xa64 / Xb64 on the CUDA cores.
+int kprod(HssImpl *H, const __half *XAa, const double *Xa64, int64_t ma, const __half *XBb, const double *Xb64,
+          int64_t nb, const double *V, int64_t ldv, int nv, double *out, int64_t ldo) {
+    Ctx *c = H->c;
+    if (ma == 0 || nv == 0) return KRR_OK;
+    if (H->mixed()) {
+        const int cols = 2 * nv;
+        const int rpad = int(round_up(cols, 64));
+        const int64_t ldrt = round_up(nb, 8);
+        DBuf<float> Rs(c, size_t(nb) * cols), Sm(c, size_t(ma) * cols);
+        DBuf<__half> RT(c, size_t(rpad) * ldrt);
+        if (!Rs.get() || !Sm.get() || !RT.get()) return fail(KRR_ERR_OOM, "kernel product: out of memory");
+        { split16_kernel<<<unsigned(cdiv(nb * nv, 256)), 256, 0, c->stream>>>(V, nb, nv, ldv, Rs.get(), cols); ::krr::count_launch(); }
+        KRR_TRY(transpose_half(c, Rs.get(), nb, cols, cols, RT.get(), rpad, ldrt));
+        KRR_TRY(sample_mixed_prepared(c, XAa, ma, XBb, nb, H->d, RT.get(), cols, ldrt, nullptr, nullptr, Sm.get(),
+                                      cols, true));
+        { combine_kernel<float><<<unsigned(cdiv(ma * nv, 256)), 256, 0, c->stream>>>(Sm.get(), cols, 1, nullptr, 0,
+                                                                                   0.0, ma, nv, out, ldo); ::krr::count_launch(); }
+    } else {
+        DBuf<double> Sm(c, size_t(ma) * nv);
+        if (!Sm.get()) return fail(KRR_ERR_OOM, "kernel product: out of memory");
+        KRR_TRY(launch_sample_f64(c, Xa64, ma, Xb64, nb, H->d, H->opt.h, V, nv, ldv, nullptr, nullptr, Sm.get(), nv));
+        { combine_kernel<double><<<unsigned(cdiv(ma * nv, 256)), 256, 0, c->stream>>>(Sm.get(), nv, 0, nullptr, 0,
+                                                                                    0.0, ma, nv, out, ldo); ::krr::count_launch(); }
+    }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
+int heldout_grad_impl(HssImpl *H, const float *Xt, int64_t m, const double *y, const double *yt, double tol,
+                      int max_refine, double *loss, double *dh, double *dlambda, double *dX, int64_t lddx,
+                      double *alpha, double *resid) {
+    Ctx *c = H->c;
+    if (!H->factored) KRR_TRY(hss_factor_impl(H));
+    const int64_t n = H->n;
+    const int d = H->d;
+    const bool full = dh || dlambda || dX;
+    const double h = H->opt.h;
+    const int ldv = 2 * d + 3;  // [alpha, alpha |xc|^2, alpha xc, z, z xc]
+    DBuf<double> yp(c, n), ap(c, n), zp(c, n), av(c, n), V(c, size_t(n) * ldv), P(c, size_t(m) * (d + 2)),
+        W(c, size_t(m) * (d + 1)), Q(c, size_t(n) * (d + 1)), Pn(c, size_t(n) * ldv), sum(c, d), acc(c, 4);
+    if (!yp.get() || !ap.get() || !zp.get() || !av.get() || !V.get() || !P.get() || !W.get() || !Q.get() ||
+        !Pn.get() || !sum.get() || !acc.get())
+        return fail(KRR_ERR_OOM, "krr_heldout_grad: out of memory");
+    // held-out operands: augmented (mixed) or widened (FP64)
+    DBuf<__half> tA, tB;
+    DBuf<double> t64;
+    if (H->mixed()) {
+        if (!tA.reset(c, size_t(m) * H->kpad) || (full && !tB.reset(c, size_t(m) * H->kpad)))
+            return fail(KRR_ERR_OOM, "krr_heldout_grad: out of memory");
+        KRR_TRY(augment(c, Xt, m, d, h, 0, tA.get(), H->kpad));
+        if (full) KRR_TRY(augment(c, Xt, m, d, h, 1, tB.get(), H->kpad));
+    } else {
+        if (!t64.reset(c, size_t(m) * d)) return fail(KRR_ERR_OOM, "krr_heldout_grad: out of memory");
+        KRR_TRY(widen(c, Xt, m * d, t64.get()));
+    }
+    const float *X = H->Xp32.get();
+    const double inv_n = 1.0 / double(n);
+    KRR_CUDA(cudaMemsetAsync(sum.get(), 0, d * sizeof(double), c->stream));
+    KRR_CUDA(cudaMemsetAsync(acc.get(), 0, 4 * sizeof(double), c->stream));
+    { colsum_kernel<<<unsigned(std::min<int64_t>(cdiv(n * d, 256), 2 * c->num_sms)), 256, d * sizeof(double),
+                      c->stream>>>(X, n, d, sum.get()); ::krr::count_launch(); }
+    // alpha = (K + lambda I)^{-1} y
+    KRR_TRY((gather_rows<double, double>(c, y, 1, H->perm.get(), n, 1, yp.get(), 1)));
+    double r1 = -1.0, r2 = -1.0;
+    KRR_TRY(solve_perm(H, yp.get(), 1, ap.get(), tol, max_refine, r1));
+    const unsigned gw_n = unsigned(cdiv(n * 32, 256)), gw_m = unsigned(cdiv(m * 32, 256));
+    { grad_cols_kernel<<<gw_n, 256, 0, c->stream>>>(X, n, d, sum.get(), inv_n, ap.get(), 0, V.get(), ldv); ::krr::count_launch(); }
+    // P = K(Xt, X) [alpha, alpha |xc|^2, alpha xc]; g, W, loss, first h term
+    const int nvp = full ? d + 2 : 1;
+    KRR_TRY(kprod(H, tA.get(), t64.get(), m, H->XB.get(), H->Xp64.get(), n, V.get(), ldv, nvp, P.get(), d + 2));
+    { grad_test_kernel<<<gw_m, 256, 0, c->stream>>>(Xt, m, d, sum.get(), inv_n, P.get(), d + 2, yt, full ? 1 : 0,
+                                                    W.get(), d + 1, acc.get()); ::krr::count_launch(); }
+    if (full) {
+        // Q = K(X, Xt) [g, g xtc]; a = Q(:, 0); z = (K + lambda I)^{-1} a
+        KRR_TRY(kprod(H, H->XA.get(), H->Xp64.get(), n, tB.get(), t64.get(), m, W.get(), d + 1, d + 1, Q.get(),
+                      d + 1));
+        KRR_CUDA(cudaMemcpy2DAsync(av.get(), sizeof(double), Q.get(), size_t(d + 1) * sizeof(double), sizeof(double),
+                                   size_t(n), cudaMemcpyDeviceToDevice, c->stream));
+        const int steps1 = H->refine_steps;
+        KRR_TRY(solve_perm(H, av.get(), 1, zp.get(), tol, max_refine, r2));
+        H->refine_steps += steps1;
+        { grad_cols_kernel<<<gw_n, 256, 0, c->stream>>>(X, n, d, sum.get(), inv_n, zp.get(), 1, V.get(), ldv); ::krr::count_launch(); }
+        // Pn = K(X, X) V (no lambda: d/dh and d/dX of lambda I vanish)
+        KRR_TRY(kprod(H, H->XA.get(), H->Xp64.get(), n, H->XB.get(), H->Xp64.get(), n, V.get(), ldv, ldv, Pn.get(),
+                      ldv));
+        { grad_train_kernel<<<gw_n, 256, 0, c->stream>>>(X, n, d, sum.get(), inv_n, ap.get(), zp.get(), Q.get(), d + 1,
+                                                         Pn.get(), ldv, 1.0 / (h * h), H->perm.get(), dX, lddx,
+                                                         acc.get()); ::krr::count_launch(); }
+    }
+    KRR_CUDA(cudaGetLastError());
+    if (alpha) KRR_TRY((scatter_rows<double, double>(c, ap.get(), 1, H->perm.get(), n, 1, alpha, 1)));
+    double hacc[4];
+    KRR_CUDA(cudaMemcpyAsync(hacc, acc.get(), sizeof hacc, cudaMemcpyDeviceToHost, c->stream));
+    KRR_TRY(take_status(c, "krr_heldout_grad"));
+    *loss = hacc[0];
+    if (dh) *dh = (hacc[1] - hacc[2]) / (h * h * h);
+    if (dlambda) *dlambda = -hacc[3];
+    if (resid) *resid = std::max(r1, r2);
+    if (tol > 0 && (r1 > tol || r2 > tol))
+        return fail(KRR_ERR_NO_CONVERGENCE, "krr_heldout_grad: a solve did not reach tol");
+    return KRR_OK;
 }
 
 int64_t hss_memory_bytes(const HssImpl *H) {
@@ -1351,14 +1615,9 @@ int hss_update_lambda(krr_hss *H, double lambda) {
 int hss_factor(krr_hss *H) {
     if (!H) return fail(KRR_ERR_INVALID_ARG, "hss_factor: NULL");
     KRR_TRY(hss_factor_impl(&H->h));
-    DevStatus st{};
-    KRR_CUDA(cudaMemcpy(&st, H->h.c->status, sizeof st, cudaMemcpyDeviceToHost));
-    if (st.code != 0) {
-        KRR_CUDA(cudaMemset(H->h.c->status, 0, sizeof(DevStatus)));
-        H->h.factored = false;
-        return fail(st.code, "hss_factor: device error (site " + std::to_string(st.where) + ")");
-    }
-    return KRR_OK;
+    const int s = take_status(H->h.c, "hss_factor");
+    if (s != KRR_OK) H->h.factored = false;
+    return s;
 }
 
 int hss_solve(krr_hss *H, const double *y, int32_t nrhs, int64_t ldy, double *alpha, int64_t lda, double tol,
@@ -1374,6 +1633,15 @@ int krr_predict(krr_hss *H, const float *Xt, int64_t m, const double *alpha, int
         return fail(KRR_ERR_INVALID_ARG, "krr_predict: bad arguments");
     if (m == 0) return KRR_OK;
     return hss_predict_impl(&H->h, Xt, m, alpha, nrhs, lda, out, ldo);
+}
+
+int krr_heldout_grad(krr_hss *H, const float *Xt, int64_t m, const double *y, const double *yt, double tol,
+                     int32_t max_refine, double *loss, double *dh, double *dlambda, double *dX, int64_t lddx,
+                     double *alpha, double *resid) {
+    if (!H || !Xt || !y || !yt || !loss || m < 1 || max_refine < 0 || (dX && lddx < H->h.d))
+        return fail(KRR_ERR_INVALID_ARG, "krr_heldout_grad: bad arguments");
+    if (m > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "krr_heldout_grad: m too large");
+    return heldout_grad_impl(&H->h, Xt, m, y, yt, tol, max_refine, loss, dh, dlambda, dX, lddx, alpha, resid);
 }
 
 int hss_stats(const krr_hss *H, krr_hss_stats *st) {

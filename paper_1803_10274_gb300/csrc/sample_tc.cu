@@ -524,6 +524,9 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     if (ns > tc::kMaxStages) ns = tc::kMaxStages;
     if (ns < 2) return fail(KRR_ERR_INVALID_ARG, "sample_tc: tile does not fit in shared memory");
     P.nstage = ns;
+    // The issuer runs the distance GEMM ndist - 1 tiles ahead of the
+    // product, so those tiles' stages must all be resident at once.
+    if (P.ndist > ns) P.ndist = ns;
     P.off_bar = P.off_stage + ns * P.stage_bytes;
     size_t smem = size_t(P.off_bar) + tc::BAR_COUNT * 8 + 16 + 1024;
     // The kernel allocates all 512 tensor-memory columns, so two CTAs must

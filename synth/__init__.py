@@ -23,12 +23,17 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["mixture", "image_like", "gaussian_block", "labels_pm1"]
+__all__ = ["mixture", "image_like", "gaussian_block", "labels_pm1", "labels_one_vs_rest"]
 
 
 def labels_pm1(component: np.ndarray) -> np.ndarray:
     """+1 for even component index, -1 for odd."""
     return np.where(component % 2 == 0, 1.0, -1.0)
+
+
+def labels_one_vs_rest(component: np.ndarray, cls: int) -> np.ndarray:
+    """+1 for component ``cls``, -1 otherwise (one-vs-all labels)."""
+    return np.where(component == cls, 1.0, -1.0)
 
 
 def mixture(n: int, d: int, n_comp: int, sigma: float, seed: int,

@@ -84,6 +84,22 @@ def test_single_leaf_is_dense_lu(K, ctx):
     H.close()
 
 
+@pytest.mark.parametrize("prec,rtol", [("KRR_FP64", 1e-12), ("KRR_MIXED", 1e-6)])
+def test_narrow_kernel_is_identity(K, ctx, prec, rtol):
+    """h -> 0: K -> I (Eq. (1)).  On the lattice {-1, 0, 1}^6 (729 points,
+    unit spacing) with h = 0.1 every off-diagonal entry is below e^-50, so
+    every off-diagonal block is numerically zero (with an absolute pivot
+    floor of 1e-12), every rank is 0, and one ULV solve gives
+    alpha = y / (1 + lambda) (FP32 arithmetic on the mixed path)."""
+    g = np.array(np.meshgrid(*([[-1.0, 0.0, 1.0]] * 6), indexing="ij")).reshape(6, -1).T
+    X32 = (g + 0.01 * np.random.default_rng(2).standard_normal(g.shape)).astype(np.float32)
+    y = np.random.default_rng(3).standard_normal(len(X32))
+    H, A, res = _fit(K, ctx, X32, y[:, None], 0.1, 0.5, 0.05, 64, getattr(K, prec), 0.0, eps_abs=1e-12)
+    assert H.stats()["max_rank"] == 0
+    np.testing.assert_allclose(A[:, 0], y / 1.5, rtol=rtol)
+    H.close()
+
+
 def test_lambda_update_equals_recompression(K, ctx):
     """Section 5.3: changing lambda only changes the diagonal, so updating
     lambda and refactoring matches compressing at the new lambda (same

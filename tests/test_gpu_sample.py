@@ -75,6 +75,27 @@ def test_mixed_masked_and_lambda(K, ctx):
     assert np.all(np.abs(S2.cpu().numpy() - ref2) <= _mixed_tol(ref2_abs, R))
 
 
+@pytest.mark.parametrize("n,d,r,masked", [(4096, 40, 128, True),    # two chunks, two stages
+                                           (4096, 54, 64, True),     # three chunks, two row-tile buffers
+                                           (4096, 54, 128, False),   # three chunks, one row-tile buffer
+                                           (3000, 80, 64, True)])    # four chunks
+def test_mixed_wide_rows_many_tiles_per_cta(K, ctx, n, d, r, masked):
+    """Every CTA walks several tiles, so the stage / distance-buffer rings
+    wrap; wide feature rows leave room for only two stages."""
+    X = synth.mixture(n, d, 7, 0.7, 30 + d)[0]
+    X = ((X - X.mean(0)) / X.std(0)).astype(np.float32)
+    R = synth.gaussian_block(n, r, 8).astype(np.float32)
+    h = 3.0 * np.sqrt(d / 54.0)
+    leaf = (np.arange(n) // 100).astype(np.int32) if masked else None
+    S = K.krr_sample(ctx, _cuda(X), _cuda(X), h, 0.0, _cuda(R), *(2 * [_cuda(leaf)] if masked else []))
+    ctx.sync()
+    rows = np.concatenate([np.arange(0, 130), np.arange(n - 130, n),
+                           np.random.default_rng(1).choice(n, 100, replace=False)])
+    ref, ref_abs = kernel.kernel_product(X, X, h, R, leaf, leaf, rows=rows, want_abs=True)
+    err = np.abs(S.cpu().numpy()[rows] - ref)
+    assert np.all(err <= _mixed_tol(ref_abs, R))
+
+
 def test_mixed_full_size_sampled_rows(K, ctx):
     """The 65536-point, 8-feature, 64-column product the benchmark times,
     checked on 192 sampled rows (first, last and random)."""
