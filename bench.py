@@ -49,6 +49,32 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def kernel_source_hash():
+    """sha1 of the fused kernel's source: DRAM counters taken from an ncu
+    capture are valid only for the kernel they were measured on."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1803_10274_gb300", "csrc", "sample_tc.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def _traffic():
+    """DRAM bytes per launch (n=65536, r=256) from profiles/sample_tc_traffic.txt,
+    or None when that capture was taken on a different kernel source."""
+    vals = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "sample_tc_traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 2:
+                    vals[parts[0]] = parts[1]
+    except OSError:
+        return None
+    if vals.get("kernel_source_sha1") != kernel_source_hash():
+        return None
+    v = vals.get("bytes_per_launch_n65536_r256")
+    return int(v) if v else None
+
+
 def _inputs():
     import synth
     X, y, Xt, yt, _, _ = synth.mixture(WL["n"], WL["d"], WL["comps"], WL["sigma"], WL["seed"], WL["m_test"])
@@ -213,16 +239,7 @@ def run_ours(args):
         samp[r] = (2.0 * n * n * (d + r) / t / 1e12, t)
     ach, tk = samp[256]
     peak = float(peaks["bf16_tflops"])
-    traffic = None
-    try:
-        # DRAM bytes per launch from the ncu capture summarized in profiles/
-        with open(os.path.join(ROOT, "profiles", "sample_tc_traffic.txt")) as f:
-            for line in f:
-                k, v = line.split()
-                if k == "bytes_per_launch_n65536_r256":
-                    traffic = int(v)
-    except Exception:
-        pass
+    traffic = _traffic()
 
     # ---- end to end through host buffers (H2D inputs, D2H weights + predictions inside the timed region)
     Xh = torch.from_numpy(X).pin_memory()
@@ -247,6 +264,10 @@ def run_ours(args):
     e2e = sum(e_times) / len(e_times)
     h2d = X.nbytes + Xt.nbytes + Y.nbytes
     d2h = ah.numel() * 8 + dh.numel() * 8
+
+    # ---- held-out loss gradient (COVTYPE-shaped) and the million-point product
+    extras = {} if args.no_extras else {"gradient": bench_gradient(K, ctx, l2),
+                                        "million_point_product": bench_million(K, ctx)}
 
     # ---- FP64 plain path, same step (one run: it is slow)
     plain = None
@@ -282,6 +303,7 @@ def run_ours(args):
         "phases_ms": {k: st[k] for k in ("t_cluster_ms", "t_sample_ms", "t_compress_ms", "t_factor_ms",
                                          "t_solve_ms")},
         "fp64_plain": plain,
+        **extras,
         "sampling": {"tflops_r64": samp[64][0], "ms_r64": 1e3 * samp[64][1], "tflops_r256": samp[256][0],
                      "ms_r256": 1e3 * samp[256][1], "algorithmic_flops": "2 n^2 (d + r)",
                      "share_of_step": t_sample_frac},
@@ -299,6 +321,81 @@ def run_ours(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+GRAD_WL = dict(n=16384, d=54, comps=7, cls=2, seed=4, m_test=4096, h=3.0, lam=1.0, eps_c=0.1, leaf=128, tol=1e-6)
+
+
+def bench_gradient(K, ctx, l2, reps=3):
+    """Held-out squared loss and its gradient in h, lambda and X on the
+    COVTYPE-shaped workload (n=16384, d=54 standardized, 7-component
+    mixture, one-vs-rest labels for class 2, 4096 held out; h=3, lambda=1):
+    one timed step = HSS compression + krr_heldout_grad (two preconditioned
+    solves to 1e-6 and the augmented fused products)."""
+    import torch
+    import synth
+    from oracle import prep
+    W = GRAD_WL
+    X, _, Xt, _, c, ct = synth.mixture(W["n"], W["d"], W["comps"], 0.7, W["seed"], W["m_test"])
+    y, yt = synth.labels_one_vs_rest(c, W["cls"]), synth.labels_one_vs_rest(ct, W["cls"])
+    # standardizing the inputs is data preparation, not part of the timed step
+    Z, Zt, _, _ = prep.standardize(X, Xt)
+    Xd = torch.from_numpy(Z.astype(np.float32)).cuda()
+    Xtd = torch.from_numpy(Zt.astype(np.float32)).cuda()
+    yd, ytd = torch.from_numpy(y).cuda(), torch.from_numpy(yt).cuda()
+    o = K.default_options(h=W["h"], lambda_=W["lam"], eps_c=W["eps_c"], leaf=W["leaf"], precision=K.KRR_MIXED)
+
+    def once(full):
+        _flush_l2(l2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        H = K.hss_compress(ctx, Xd, o)
+        r = H.heldout_grad(Xtd, yd, ytd, tol=W["tol"], max_refine=400, grad=full)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        st = H.stats()
+        H.close()
+        return e0.elapsed_time(e1) / 1e3, r, st
+
+    once(True)
+    tg = [once(True) for _ in range(reps)]
+    tl = [once(False) for _ in range(reps)]
+    t, r, st = tg[-1]
+    return {"workload": "COVTYPE-shaped mixture n=16384, d=54, 4096 held out, h=3, lambda=1, HSS eps_c=0.1, "
+                        "solves to 1e-6",
+            "seconds_loss_and_grad": statistics.median(x[0] for x in tg),
+            "seconds_loss_only": statistics.median(x[0] for x in tl),
+            "loss": r["loss"], "dL_dh": r["dh"], "dL_dlambda": r["dlambda"],
+            "gmres_iters_both_solves": st["refine_steps"], "max_rank": st["max_rank"]}
+
+
+def bench_million(K, ctx, n=1 << 20, r=256, reps=2):
+    """One fused product S = K R at n = 1,048,576, d = 8, r = 256 (about
+    5.8e14 algorithmic flops), inputs resident, CUDA events."""
+    import torch
+    import synth
+    d = 8
+    X = synth.mixture(n, d, 16, 0.7, 6)[0]
+    X = ((X - X.mean(0)) / X.std(0)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    R = torch.from_numpy(synth.gaussian_block(n, r, 6).astype(np.float32)).cuda()
+    S = torch.empty(n, r, device="cuda")
+    K.krr_sample(ctx, Xd, Xd, 1.0, 0.0, R, S=S)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        K.krr_sample(ctx, Xd, Xd, 1.0, 0.0, R, S=S)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(ts)
+    del R, S
+    torch.cuda.empty_cache()
+    return {"n": n, "d": d, "r": r, "seconds": t, "tflops": 2.0 * n * n * (d + r) / t / 1e12,
+            "algorithmic_flops": "2 n^2 (d + r)"}
 
 
 def sample_only(n, r):
@@ -374,6 +471,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the gradient workload and the million-point product")
     ap.add_argument("--sample-only", nargs=2, type=int, metavar=("N", "R"),
                     help="only run the fused sampling product at n=N, r=R (5 launches; for profilers)")
     args = ap.parse_args()

@@ -111,6 +111,21 @@ def test_mixed_full_size_sampled_rows(K, ctx):
     assert np.all(err <= _mixed_tol(ref_abs, R))
 
 
+def test_mixed_one_million_points_sampled_rows(K, ctx):
+    """n = 1,048,576, d = 8, r = 256 (the batched workload's single large
+    product): 48 sampled rows against the oracle."""
+    n, d, r = 1 << 20, 8, 256
+    X = synth.mixture(n, d, 16, 0.7, 6)[0]
+    X = ((X - X.mean(0)) / X.std(0)).astype(np.float32)
+    R = synth.gaussian_block(n, r, 6).astype(np.float32)
+    S = K.krr_sample(ctx, _cuda(X), _cuda(X), 1.0, 0.0, _cuda(R))
+    ctx.sync()
+    rows = np.concatenate([[0, 127, 128, n - 1], np.random.default_rng(2).choice(n, 44, replace=False)])
+    ref, ref_abs = kernel.kernel_product(X, X, 1.0, R, rows=rows, want_abs=True)
+    err = np.abs(S[torch.from_numpy(rows).cuda()].cpu().numpy() - ref)
+    assert np.all(err <= _mixed_tol(ref_abs, R))
+
+
 @pytest.mark.parametrize("ma,nb,d,r", [(500, 700, 8, 64), (129, 65, 54, 10)])
 def test_f64_matches_oracle(K, ctx, ma, nb, d, r):
     Xa = synth.mixture(ma, d, 4, 0.7, 1)[0]
