@@ -122,6 +122,18 @@ int krr_cluster(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
                 int32_t leaf, uint64_t seed, int32_t *perm,
                 int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes);
 
+/* Batched form: the rows of X split into nprob contiguous problems
+ * (offsets: host int64[nprob + 1], offsets[0] = 0, offsets[nprob] = n, every
+ * problem non-empty).  The top of the tree is a balanced binary tree over
+ * the problems; below, every problem is ordered exactly as krr_cluster
+ * orders it alone (quantization and seed counters are per problem), and
+ * perm keeps every row inside its problem.  One set of launches serves all
+ * problems.  Synchronizes. */
+int krr_cluster_batched(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
+                        int32_t nprob, const int64_t *offsets, int32_t leaf,
+                        uint64_t seed, int32_t *perm, int32_t max_nodes,
+                        krr_tree_arrays tree, int32_t *n_nodes);
+
 /* ---------------------------------------------------------------------
  * Fused kernel-times-block product (the HSS sampling step, Section 1.1
  * and Section 3.1: the randomized construction needs A R for a block R of
@@ -207,6 +219,33 @@ void krr_default_options(krr_options *opts);
  * Synchronizes (the adaptive sampling reads ranks back per level). */
 int hss_compress(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
                  const krr_options *opts, krr_hss **out);
+
+/* Many independent problems in one handle (batching): problem p owns rows
+ * [offsets[p], offsets[p+1]) of X (host int64[nprob + 1], offsets[0] = 0,
+ * offsets[nprob] = n, every problem non-empty) and has the Gaussian width
+ * h[p] (host double[nprob]); opts->h is ignored, lambda and the other
+ * options are shared.  The handle holds the block-diagonal matrix
+ * diag(K_p + lambda I): one tree over all problems (krr_cluster_batched),
+ * every fused product one persistent launch over the tiles of the
+ * diagonal blocks only, every level of the compression, factorization and
+ * solve one set of launches over the nodes of all problems.  Problems that
+ * share their points but differ in h are passed as separate problems.
+ * hss_factor, hss_solve (alpha in original row order, i.e. problem by
+ * problem; the tolerance applies to each right-hand side over the whole
+ * batch), hss_stats and hss_destroy work as for one problem; predict
+ * with krr_predict_batched.  Synchronizes. */
+int hss_compress_batched(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
+                         int32_t nprob, const int64_t *offsets,
+                         const double *h, const krr_options *opts,
+                         krr_hss **out);
+
+/* Decision values of a batched handle: test rows [test_offsets[p],
+ * test_offsets[p+1]) of Xt (device float m x d) against problem p's
+ * training points and weights only (test_offsets: host int64[nprob + 1],
+ * nondecreasing, from 0 to m; a problem may have no test rows). */
+int krr_predict_batched(krr_hss *H, const float *Xt, int64_t m,
+                        const int64_t *test_offsets, const double *alpha,
+                        int32_t nrhs, int64_t lda, double *out, int64_t ldo);
 
 /* Change lambda without recompressing (Section 5.3: only the diagonal
  * changes).  Invalidates the factorization; call hss_factor again. */

@@ -53,12 +53,16 @@ SIGNATURES = {
     "krr_sync": (i32, [P]),
     "krr_standardize": (i32, [P, P, i64, i32, P, i64, P, P]),
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),
+    "krr_cluster_batched": (i32, [P, P, i64, i32, i32, P, i32, u64, P, i32, krr_tree_arrays,
+                                  ctypes.POINTER(i32)]),
     "krr_sample": (i32, [P, P, i64, P, i64, i32, f64, f64, P, i32, i64, P, P, P, i64]),
     "krr_sample_f64": (i32, [P, P, i64, P, i64, i32, f64, f64, P, i32, i64, P, P, P, i64]),
     "krr_sample_noalloc": (i32, [P, P, i64, P, i64, i32, f64, f64, P, i32, i64, P, P, P, i64]),
     "krr_random_block": (i32, [P, i64, i32, i32, u64, ctypes.c_int, P, i64]),
     "krr_default_options": (None, [ctypes.POINTER(krr_options)]),
     "hss_compress": (i32, [P, P, i64, i32, ctypes.POINTER(krr_options), ctypes.POINTER(P)]),
+    "hss_compress_batched": (i32, [P, P, i64, i32, i32, P, P, ctypes.POINTER(krr_options), ctypes.POINTER(P)]),
+    "krr_predict_batched": (i32, [P, P, i64, P, P, i32, i64, P, i64]),
     "hss_update_lambda": (i32, [P, f64]),
     "hss_factor": (i32, [P]),
     "hss_solve": (i32, [P, P, i32, i64, P, i64, f64, i32, ctypes.POINTER(f64)]),

@@ -15,7 +15,7 @@ from ._lib import KRR_FP64, KRR_MIXED, KRRError, check, lib
 
 __all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "krr_standardize", "krr_cluster", "krr_sample",
            "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "HSS", "hss_compress", "default_options",
-           "HeldOutLoss", "krr_heldout_loss", "lib"]
+           "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]
 
 
 _shutting_down = [False]
@@ -105,6 +105,28 @@ def krr_cluster(ctx, X, leaf, seed):
     ta = _lib.krr_tree_arrays(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for k, v in arrs.items()})
     nn = ctypes.c_int32()
     check(lib().krr_cluster(ctx.h, _ptr(X), n, d, leaf, seed, _ptr(perm), cap, ta, ctypes.byref(nn)))
+    return perm, {k: v[:nn.value].copy() for k, v in arrs.items()}
+
+
+def _i64_array(v):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int64))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def krr_cluster_batched(ctx, X, offsets, leaf, seed):
+    """Two-means order of many problems at once (rows split by offsets)."""
+    import numpy as np
+    _need(X, torch.float32, "X")
+    n, d = X.shape
+    off, offp = _i64_array(offsets)
+    perm = torch.empty(n, dtype=torch.int32, device=X.device)
+    cap = max(2 * n, 1)
+    arrs = {k: np.zeros(cap, np.int32) for k in ("begin", "end", "left", "right", "parent", "level")}
+    ta = _lib.krr_tree_arrays(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for k, v in arrs.items()})
+    nn = ctypes.c_int32()
+    check(lib().krr_cluster_batched(ctx.h, _ptr(X), n, d, len(off) - 1, offp, leaf, seed, _ptr(perm), cap, ta,
+                                    ctypes.byref(nn)))
     return perm, {k: v[:nn.value].copy() for k, v in arrs.items()}
 
 
@@ -236,6 +258,37 @@ class HSS:
             self.close()
         except Exception:
             pass
+
+
+class BatchedHSS(HSS):
+    """A handle over many problems (hss_compress_batched)."""
+
+    def __init__(self, ctx, handle, n, offsets):
+        super().__init__(ctx, handle, n)
+        self.offsets = offsets
+
+    def predict(self, Xt, alpha, test_offsets):
+        _need(Xt, torch.float32, "Xt")
+        _need(alpha, torch.float64, "alpha")
+        toff, toffp = _i64_array(test_offsets)
+        out = torch.empty(Xt.shape[0], alpha.shape[1], dtype=torch.float64, device=Xt.device)
+        check(lib().krr_predict_batched(self.h, _ptr(Xt), Xt.shape[0], toffp, _ptr(alpha), alpha.shape[1],
+                                        alpha.stride(0), _ptr(out), out.stride(0)))
+        return out
+
+
+def hss_compress_batched(ctx, X, offsets, h, opts):
+    """One handle for the block-diagonal system of many problems: rows
+    [offsets[p], offsets[p+1]) of X with Gaussian width h[p]."""
+    import numpy as np
+    _need(X, torch.float32, "X")
+    n, d = X.shape
+    off, offp = _i64_array(offsets)
+    hw = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+    hnd = ctypes.c_void_p()
+    check(lib().hss_compress_batched(ctx.h, _ptr(X), n, d, len(off) - 1, offp, hw.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.byref(opts), ctypes.byref(hnd)))
+    return BatchedHSS(ctx, hnd, n, off)
 
 
 def hss_compress(ctx, X, opts):

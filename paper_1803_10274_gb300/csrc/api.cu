@@ -50,7 +50,7 @@ void dfree(Ctx *c, void *p) {
 
 int sample_mixed_prepared(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int d,
                           const __half *RT, int r_total, int64_t ldrt, const int32_t *leaf_a,
-                          const int32_t *leaf_b, float *S, int64_t lds, bool split_k) {
+                          const int32_t *leaf_b, float *S, int64_t lds, bool split_k, const BlockDiag *bd) {
     if (ma == 0 || r_total == 0) return KRR_OK;
     KRR_CUDA(cudaMemset2DAsync(S, size_t(lds) * 4, 0, size_t(r_total) * 4, size_t(ma), c->stream));
     if (nb == 0) return KRR_OK;
@@ -60,7 +60,7 @@ int sample_mixed_prepared(Ctx *c, const __half *XA, int64_t ma, const __half *XB
         const int rv = r_total - col < rmax ? r_total - col : rmax;
         const int rpad = int(round_up(rv, 64));
         KRR_TRY(launch_sample_tc(c, XA, ma, XB, nb, nchunk, aug_kmma(d), RT + int64_t(col) * ldrt, rpad, ldrt, rv,
-                                 leaf_a, leaf_b, S + col, lds, split_k));
+                                 leaf_a, leaf_b, S + col, lds, split_k, bd));
     }
     return KRR_OK;
 }

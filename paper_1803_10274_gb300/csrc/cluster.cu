@@ -21,6 +21,12 @@
 //     (2 cnt)) per coordinate.  An empty group at the end means halves.
 //   * stable partition, group 0 first; children recurse while size > leaf.
 // Nodes are numbered in postorder (Figure 2) on the host at the end.
+//
+// Many problems at once: rows split into contiguous segments (one per
+// problem); the top of the tree is a balanced binary tree over the
+// segments, each segment is then ordered on its own.  Quantization and the
+// seed counters are per segment (counter (b - segment start, m)), so each
+// segment's subtree and order are exactly those of the segment alone.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -63,6 +69,36 @@ __global__ void quantize_kernel(const float *X, int64_t cnt, double scale, int64
     if (k < cnt) q[k] = __double2ll_rn(double(X[k]) * scale);
 }
 
+// Per segment (blockIdx.y): max |x| as float bits, and a non-finite flag.
+__global__ void absmax_seg_kernel(const float *X, int d, const int64_t *seg, unsigned int *maxbits, int *nonfinite) {
+    const int p = blockIdx.y;
+    const int64_t b = seg[p] * d, e = seg[p + 1] * d;
+    unsigned int m = 0;
+    int bad = 0;
+    for (int64_t k = b + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < e; k += int64_t(gridDim.x) * blockDim.x) {
+        const float v = X[k];
+        if (!isfinite(v)) bad = 1;
+        m = max(m, __float_as_uint(fabsf(v)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(maxbits + p, m);
+        if (bad) atomicOr(nonfinite, 1);
+    }
+}
+
+// Per segment (blockIdx.y): q = rint(x 2^kexp[p]).
+__global__ void quantize_seg_kernel(const float *X, int d, const int64_t *seg, const int *kexp, int64_t *q) {
+    const int p = blockIdx.y;
+    const int64_t b = seg[p] * d, e = seg[p + 1] * d;
+    const double scale = ldexp(1.0, kexp[p]);
+    for (int64_t k = b + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < e; k += int64_t(gridDim.x) * blockDim.x)
+        q[k] = __double2ll_rn(double(X[k]) * scale);
+}
+
 struct NodeState {
     int64_t c0[kMaxD], c1[kMaxD];
     int64_t sum0[kMaxD], sum1[kMaxD];
@@ -71,15 +107,15 @@ struct NodeState {
 };
 
 // One block per node: seeds and initial state.
-__global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const int64_t *nsize, NodeState *ns,
-                            uint64_t seed) {
+__global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const int64_t *nsize, const int64_t *nbase,
+                            NodeState *ns, uint64_t seed) {
     const int v = blockIdx.x;
     const int64_t b = nbeg[v], m = nsize[v];
     NodeState &S = ns[v];
     __shared__ unsigned long long warp_tot[kTB / 32];
     __shared__ unsigned long long s_total;
     __shared__ int64_t s_second;
-    const U64x4 w = philox4x64_10(uint64_t(b), uint64_t(m), 0, 0, seed, kStreamCluster);
+    const U64x4 w = philox4x64_10(uint64_t(b - nbase[v]), uint64_t(m), 0, 0, seed, kStreamCluster);
     const int64_t first = b + int64_t(__umul64hi(w.v[0], uint64_t(m)));
     const int64_t *c0 = q + first * d;
     auto dist0 = [&](int64_t i) -> unsigned long long {
@@ -351,41 +387,58 @@ __global__ void mark_nodes_kernel(int nn, const int64_t *nbeg, const int64_t *ns
 
 }  // namespace
 
+// Quantization exponent for m points in d dimensions with max |x| = maxabs:
+// the largest k for which 4 d m (2^k max|x|)^2 stays below 2^63.
+static int quant_exponent(float maxabs, int d, int64_t m) {
+    int L = 0;
+    uint64_t v = uint64_t(4) * uint64_t(d) * uint64_t(m) - 1;
+    while (v) { ++L; v >>= 1; }
+    const int t = (63 - L) / 2;
+    if (!(maxabs > 0.f)) return 0;
+    int e;
+    std::frexp(double(maxabs), &e);
+    return t - e;
+}
+
 int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, int32_t *perm_out,
             std::vector<int32_t> &tb, std::vector<int32_t> &te, std::vector<int32_t> &tl, std::vector<int32_t> &tr,
-            std::vector<int32_t> &tp, std::vector<int32_t> &tv) {
+            std::vector<int32_t> &tp, std::vector<int32_t> &tv, const std::vector<int64_t> *segments) {
     tb.clear(); te.clear(); tl.clear(); tr.clear(); tp.clear(); tv.clear();
     if (n == 0) return KRR_OK;
     if (d > kMaxD) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_cluster: d > 64");
     cudaStream_t st = c->stream;
-    // --- quantization
-    DBuf<unsigned int> mx(c, 1);
-    DBuf<int> bad(c, 1);
-    if (!mx.get() || !bad.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
-    KRR_CUDA(cudaMemsetAsync(mx.get(), 0, 4, st));
+    // segments (one, the whole set, unless given)
+    std::vector<int64_t> seg = segments ? *segments : std::vector<int64_t>{0, n};
+    const int nseg = int(seg.size()) - 1;
+    if (nseg < 1 || seg[0] != 0 || seg[nseg] != n) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: bad segments");
+    for (int p = 0; p < nseg; ++p)
+        if (seg[p + 1] <= seg[p]) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: empty segment");
+    // --- quantization (per segment)
+    DBuf<unsigned int> mx(c, nseg);
+    DBuf<int> bad(c, 1), dkexp(c, nseg);
+    DBuf<int64_t> dseg(c, nseg + 1);
+    if (!mx.get() || !bad.get() || !dkexp.get() || !dseg.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+    KRR_CUDA(cudaMemcpyAsync(dseg.get(), seg.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, st));
+    KRR_CUDA(cudaMemsetAsync(mx.get(), 0, nseg * 4, st));
     KRR_CUDA(cudaMemsetAsync(bad.get(), 0, 4, st));
-    { absmax_kernel<<<std::min<int64_t>(1024, cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, mx.get(), bad.get()); ::krr::count_launch(); }
+    int64_t longest = 0;
+    for (int p = 0; p < nseg; ++p) longest = std::max(longest, seg[p + 1] - seg[p]);
+    const dim3 sg(unsigned(std::min<int64_t>(1024, cdiv(longest * d, kTB))), unsigned(nseg));
+    { absmax_seg_kernel<<<sg, kTB, 0, st>>>(X, d, dseg.get(), mx.get(), bad.get()); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
-    unsigned int hmx = 0;
+    std::vector<unsigned int> hmx(nseg);
     int hbad = 0;
-    KRR_CUDA(cudaMemcpyAsync(&hmx, mx.get(), 4, cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaMemcpyAsync(hmx.data(), mx.get(), nseg * 4, cudaMemcpyDeviceToHost, st));
     KRR_CUDA(cudaMemcpyAsync(&hbad, bad.get(), 4, cudaMemcpyDeviceToHost, st));
     KRR_CUDA(cudaStreamSynchronize(st));
     if (hbad) return fail(KRR_ERR_NONFINITE_INPUT, "krr_cluster: NaN or Inf in X");
-    float maxabs;
-    std::memcpy(&maxabs, &hmx, 4);
-    int L = 0;
-    {
-        uint64_t v = uint64_t(4) * uint64_t(d) * uint64_t(n) - 1;
-        while (v) { ++L; v >>= 1; }
+    std::vector<int> hk(nseg);
+    for (int p = 0; p < nseg; ++p) {
+        float maxabs;
+        std::memcpy(&maxabs, &hmx[p], 4);
+        hk[p] = quant_exponent(maxabs, d, seg[p + 1] - seg[p]);
     }
-    const int t = (63 - L) / 2;
-    int kexp = 0;
-    if (maxabs > 0.f) {
-        int e;
-        std::frexp(double(maxabs), &e);
-        kexp = t - e;
-    }
+    KRR_CUDA(cudaMemcpyAsync(dkexp.get(), hk.data(), nseg * 4, cudaMemcpyHostToDevice, st));
     DBuf<int64_t> q(c, size_t(n) * d), q2(c, size_t(n) * d);
     DBuf<int32_t> pa(c, n), pb(c, n), node_of(c, n), zflag(c, n);
     DBuf<int8_t> label(c, n);
@@ -393,7 +446,10 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
     if (!q.get() || !q2.get() || !pa.get() || !pb.get() || !node_of.get() || !zflag.get() || !label.get() ||
         !zscan.get() || !bsum.get())
         return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
-    { quantize_kernel<<<unsigned(cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, std::ldexp(1.0, kexp), q.get()); ::krr::count_launch(); }
+    if (nseg == 1)
+        { quantize_kernel<<<unsigned(cdiv(n * d, kTB)), kTB, 0, st>>>(X, n * d, std::ldexp(1.0, hk[0]), q.get()); ::krr::count_launch(); }
+    else
+        { quantize_seg_kernel<<<sg, kTB, 0, st>>>(X, d, dseg.get(), dkexp.get(), q.get()); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     {
         std::vector<int32_t> idp(n);
@@ -405,28 +461,54 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
     int32_t *pc = pa.get(), *pn = pb.get();
 
     // --- tree, created level by level (ids in creation order; postorder at the end)
-    struct Node { int64_t b, m; int left, right, parent, level; };
+    struct Node { int64_t b, m, base; int left, right, parent, level; };
     std::vector<Node> nodes;
-    nodes.push_back({0, n, -1, -1, -1, 0});
     std::vector<int> active;
-    if (n > leaf) active.push_back(0);
+    // balanced binary tree over the segments; the segments' roots start the two-means recursion
+    {
+        struct Item { int s0, s1, node; };
+        nodes.push_back({0, n, 0, -1, -1, -1, 0});
+        std::vector<Item> todo{{0, nseg, 0}};
+        while (!todo.empty()) {
+            const Item it = todo.back();
+            todo.pop_back();
+            if (it.s1 - it.s0 == 1) {
+                nodes[it.node].base = seg[it.s0];
+                if (nodes[it.node].m > leaf) active.push_back(it.node);
+                continue;
+            }
+            const int mid = (it.s0 + it.s1) / 2;
+            const int li = int(nodes.size());
+            const int lv = nodes[it.node].level + 1;
+            nodes.push_back({seg[it.s0], seg[mid] - seg[it.s0], 0, -1, -1, it.node, lv});
+            nodes.push_back({seg[mid], seg[it.s1] - seg[mid], 0, -1, -1, it.node, lv});
+            nodes[it.node].left = li;
+            nodes[it.node].right = li + 1;
+            todo.push_back({mid, it.s1, li + 1});
+            todo.push_back({it.s0, mid, li});
+        }
+        std::sort(active.begin(), active.end(), [&](int a, int b) { return nodes[a].b < nodes[b].b; });
+    }
     DBuf<int32_t> running(c, 1);
     if (!running.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
     while (!active.empty()) {
         const int nn = int(active.size());
-        std::vector<int64_t> hb(nn), hs(nn);
+        std::vector<int64_t> hb(nn), hs(nn), hbase(nn);
         for (int k = 0; k < nn; ++k) {
             hb[k] = nodes[active[k]].b;
             hs[k] = nodes[active[k]].m;
+            hbase[k] = nodes[active[k]].base;
         }
-        DBuf<int64_t> db(c, nn), ds(c, nn), dcnt0(c, nn);
+        DBuf<int64_t> db(c, nn), ds(c, nn), dbase(c, nn), dcnt0(c, nn);
         DBuf<NodeState> dns(c, nn);
-        if (!db.get() || !ds.get() || !dcnt0.get() || !dns.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+        if (!db.get() || !ds.get() || !dbase.get() || !dcnt0.get() || !dns.get())
+            return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
         KRR_CUDA(cudaMemcpyAsync(db.get(), hb.data(), nn * 8, cudaMemcpyHostToDevice, st));
         KRR_CUDA(cudaMemcpyAsync(ds.get(), hs.data(), nn * 8, cudaMemcpyHostToDevice, st));
+        KRR_CUDA(cudaMemcpyAsync(dbase.get(), hbase.data(), nn * 8, cudaMemcpyHostToDevice, st));
         KRR_CUDA(cudaMemsetAsync(node_of.get(), 0xFF, n * 4, st));
         { mark_nodes_kernel<<<nn, kTB, 0, st>>>(nn, db.get(), ds.get(), node_of.get()); ::krr::count_launch(); }
-        { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dns.get(), seed); ::krr::count_launch(); }
+        { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         for (int iter = 0; iter <= kMaxIter; ++iter) {
             KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
@@ -458,8 +540,8 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
             const Node par = nodes[v];
             const int64_t c0 = hc0[k];
             const int li = int(nodes.size());
-            nodes.push_back({par.b, c0, -1, -1, v, par.level + 1});
-            nodes.push_back({par.b + c0, par.m - c0, -1, -1, v, par.level + 1});
+            nodes.push_back({par.b, c0, par.base, -1, -1, v, par.level + 1});
+            nodes.push_back({par.b + c0, par.m - c0, par.base, -1, -1, v, par.level + 1});
             nodes[v].left = li;
             nodes[v].right = li + 1;
             if (c0 > leaf) next.push_back(li);
@@ -506,13 +588,14 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
 
 using namespace krr;
 
-extern "C" int krr_cluster(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t leaf, uint64_t seed,
-                           int32_t *perm, int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes) {
+static int cluster_entry(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t leaf, uint64_t seed,
+                         int32_t *perm, int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes,
+                         const std::vector<int64_t> *seg) {
     if (!k || (n > 0 && (!X || !perm)) || n < 0 || d <= 0 || leaf < 1 || !n_nodes)
         return fail(KRR_ERR_INVALID_ARG, "krr_cluster: bad arguments");
     if (n > 0x7FFFFFFF) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: n too large");
     std::vector<int32_t> tb, te, tl, tr, tp, tv;
-    KRR_TRY(cluster(&k->c, X, n, d, leaf, seed, perm, tb, te, tl, tr, tp, tv));
+    KRR_TRY(cluster(&k->c, X, n, d, leaf, seed, perm, tb, te, tl, tr, tp, tv, seg));
     const int N = int(tb.size());
     *n_nodes = N;
     if (N > max_nodes) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: max_nodes too small");
@@ -527,4 +610,17 @@ extern "C" int krr_cluster(krr_ctx *k, const float *X, int64_t n, int32_t d, int
         tree.level[i] = tv[i];
     }
     return KRR_OK;
+}
+
+extern "C" int krr_cluster(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t leaf, uint64_t seed,
+                           int32_t *perm, int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes) {
+    return cluster_entry(k, X, n, d, leaf, seed, perm, max_nodes, tree, n_nodes, nullptr);
+}
+
+extern "C" int krr_cluster_batched(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t nprob,
+                                   const int64_t *offsets, int32_t leaf, uint64_t seed, int32_t *perm,
+                                   int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes) {
+    if (nprob < 1 || !offsets) return fail(KRR_ERR_INVALID_ARG, "krr_cluster_batched: bad arguments");
+    std::vector<int64_t> seg(offsets, offsets + nprob + 1);
+    return cluster_entry(k, X, n, d, leaf, seed, perm, max_nodes, tree, n_nodes, &seg);
 }

@@ -46,7 +46,7 @@ namespace krr {
 
 int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, int32_t *perm_out,
             std::vector<int32_t> &tb, std::vector<int32_t> &te, std::vector<int32_t> &tl, std::vector<int32_t> &tr,
-            std::vector<int32_t> &tp, std::vector<int32_t> &tv);
+            std::vector<int32_t> &tp, std::vector<int32_t> &tv, const std::vector<int64_t> *segments);
 
 namespace {
 
@@ -195,6 +195,15 @@ __global__ void __launch_bounds__(cta::kNT) id_prep_kernel(const NodeDesc *nd, c
     for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += blockDim.x) W[e] = Sorig[(e / r) * lds + e % r];
     if (N.is_leaf)
         for (int a = threadIdx.x; a < m; a += blockDim.x) I[N.rows + a] = N.leaf_begin + a;
+}
+
+// Nodes that stay whole: rank 0, local rows in their natural order.
+__global__ void noid_kernel(const NodeDesc *nd, int32_t *I) {
+    const NodeDesc &N = nd[blockIdx.x];
+    for (int a = threadIdx.x; a < N.m; a += blockDim.x) {
+        I[N.piv + a] = a;
+        if (N.is_leaf) I[N.rows + a] = N.leaf_begin + a;
+    }
 }
 
 // Large-node path, last step: T from the QR, in-sample and held-out errors,
@@ -457,6 +466,13 @@ __global__ void convert_kernel(const Tin *a, int64_t n, Tout *b) {
     if (e < n) b[e] = Tout(a[e]);
 }
 
+// X(i, :) *= s[grp[i]]  (a problem's coordinates divided by its width)
+template <class T>
+__global__ void scale_rows_kernel(T *X, int64_t n, int d, const int32_t *grp, const double *s) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e < n * d) X[e] = T(double(X[e]) * s[grp[e / d]]);
+}
+
 __global__ void axpy_kernel(double *a, const double *b, int64_t n) {
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e < n) a[e] += b[e];
@@ -506,6 +522,32 @@ struct HssImpl {
     DBuf<__half> ws_rt;
     int ws_nrhs = -1;
     double lambda = 0;
+    // Many independent problems in one block-diagonal system: problem p
+    // owns rows [boff[p], boff[p+1]) (original and cluster order alike),
+    // its coordinates are stored divided by its width bh[p] and every
+    // kernel evaluation uses width 1.  nprob == 0: a single problem.
+    int nprob = 0;
+    std::vector<int64_t> boff;
+    std::vector<double> bh;
+    DBuf<int32_t> bgrp, tl_lo, tl_hi;
+    DBuf<int64_t> dboff, tl_off;
+    int64_t tl_tiles = 0;
+    BlockDiag bd_train() const {
+        BlockDiag b;
+        b.grp_a = b.grp_b = bgrp.get();
+        b.off_b = dboff.get();
+        b.tl_lo = tl_lo.get();
+        b.tl_hi = tl_hi.get();
+        b.tl_off = tl_off.get();
+        b.tiles = tl_tiles;
+        return b;
+    }
+    const BlockDiag *bd_or_null(const BlockDiag &b) const { return nprob > 0 ? &b : nullptr; }
+    // nodes whose rows are whole problems (a problem's root, the nodes that
+    // join problems): their off-diagonal blocks are zero, so they take rank
+    // 0 without an ID and are eliminated whole
+    std::vector<char> top;
+    bool is_top(int v) const { return !top.empty() && top[v]; }
     int max_rank = 0, refine_steps = 0;
     double max_test_err = 0;
     double t_cluster = 0, t_sample = 0, t_compress = 0, t_factor = 0, t_solve = 0;
@@ -521,6 +563,67 @@ double now_ms() {
 // Read (and clear) the context's device status word; an error latched by a
 // kernel (a wait past its limit, a zero pivot, an input out of range)
 // fails the call.  Synchronizes.
+// Tile list of a block-diagonal product (rows of A and columns of B split
+// into the same problems, offsets offa / offb): row tile rt meets column
+// tiles [lo, hi], the column range of the problems its rows belong to.
+int make_tile_list(Ctx *c, const std::vector<int64_t> &offa, const std::vector<int64_t> &offb, DBuf<int32_t> &lo,
+                   DBuf<int32_t> &hi, DBuf<int64_t> &off, int64_t &total) {
+    const int P = int(offa.size()) - 1;
+    const int64_t ma = offa[P];
+    const int64_t nrt = cdiv(ma, kTcTile);
+    std::vector<int32_t> hl(nrt), hh(nrt);
+    std::vector<int64_t> ho(nrt + 1);
+    total = 0;
+    int p = 0;
+    for (int64_t rt = 0; rt < nrt; ++rt) {
+        const int64_t r0 = rt * kTcTile, r1 = std::min(r0 + kTcTile, ma) - 1;
+        while (offa[p + 1] <= r0) ++p;
+        int q = p;
+        while (offa[q + 1] <= r1) ++q;
+        const int64_t c0 = offb[p], c1 = offb[q + 1];
+        if (c1 <= c0) return fail(KRR_ERR_INVALID_ARG, "block-diagonal product: a problem has no columns");
+        hl[rt] = int32_t(c0 / kTcTile);
+        hh[rt] = int32_t((c1 - 1) / kTcTile);
+        ho[rt] = total;
+        total += hh[rt] - hl[rt] + 1;
+    }
+    ho[nrt] = total;
+    if (!lo.reset(c, nrt) || !hi.reset(c, nrt) || !off.reset(c, nrt + 1))
+        return fail(KRR_ERR_OOM, "block-diagonal product: out of memory");
+    KRR_CUDA(cudaMemcpyAsync(lo.get(), hl.data(), nrt * 4, cudaMemcpyHostToDevice, c->stream));
+    KRR_CUDA(cudaMemcpyAsync(hi.get(), hh.data(), nrt * 4, cudaMemcpyHostToDevice, c->stream));
+    KRR_CUDA(cudaMemcpyAsync(off.get(), ho.data(), (nrt + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
+// Problem id of every row for row offsets off (device int32[off.back()]).
+int make_groups(Ctx *c, const std::vector<int64_t> &off, DBuf<int32_t> &grp) {
+    const int64_t n = off.back();
+    std::vector<int32_t> h(n);
+    for (size_t p = 0; p + 1 < off.size(); ++p)
+        for (int64_t i = off[p]; i < off[p + 1]; ++i) h[i] = int32_t(p);
+    if (!grp.reset(c, n)) return fail(KRR_ERR_OOM, "block-diagonal product: out of memory");
+    KRR_CUDA(cudaMemcpyAsync(grp.get(), h.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
+// Divide each problem's rows of X (device rows x d, in place) by its width.
+template <class T>
+int scale_by_width(Ctx *c, T *X, int64_t rows, int d, const int32_t *grp, const std::vector<double> &h) {
+    std::vector<double> inv(h.size());
+    for (size_t p = 0; p < h.size(); ++p) inv[p] = 1.0 / h[p];
+    DBuf<double> dinv(c, inv.size());
+    if (!dinv.get()) return fail(KRR_ERR_OOM, "block-diagonal product: out of memory");
+    KRR_CUDA(cudaMemcpyAsync(dinv.get(), inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    if (rows > 0)
+        { scale_rows_kernel<T><<<unsigned(cdiv(rows * d, 256)), 256, 0, c->stream>>>(X, rows, d, grp, dinv.get()); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
 int take_status(Ctx *c, const char *what) {
     DevStatus st{};
     KRR_CUDA(cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
@@ -602,18 +705,19 @@ template <class T>
 int sample_columns(HssImpl *H, int c0, int c1) {
     Ctx *c = H->c;
     const int dr = c1 - c0;
+    const BlockDiag bd = H->bd_train();
     if (H->mixed()) {
         KRR_TRY(random_block(c, H->n, dr, c0, H->opt.seed, KRR_MIXED, H->R32.get() + c0, H->r_cap));
         KRR_TRY(transpose_half(c, H->R32.get() + c0, H->n, dr, H->r_cap, H->RT.get() + int64_t(c0) * H->ldrt,
                                int(round_up(dr, 64)), H->ldrt));
         KRR_TRY(sample_mixed_prepared(c, H->XA.get(), H->n, H->XB.get(), H->n, H->d,
                                       H->RT.get() + int64_t(c0) * H->ldrt, dr, H->ldrt, H->leaf_of.get(),
-                                      H->leaf_of.get(), H->S32.get() + c0, H->r_cap));
+                                      H->leaf_of.get(), H->S32.get() + c0, H->r_cap, false, H->bd_or_null(bd)));
     } else {
         KRR_TRY(random_block(c, H->n, dr, c0, H->opt.seed, KRR_FP64, H->R64.get() + c0, H->r_cap));
         KRR_TRY(launch_sample_f64(c, H->Xp64.get(), H->n, H->Xp64.get(), H->n, H->d, H->opt.h,
                                   H->R64.get() + c0, dr, H->r_cap, H->leaf_of.get(), H->leaf_of.get(),
-                                  H->S64.get() + c0, H->r_cap));
+                                  H->S64.get() + c0, H->r_cap, H->bd_or_null(bd)));
     }
     return KRR_OK;
 }
@@ -673,7 +777,7 @@ int id_sweep(HssImpl *H, bool &need_more) {
         }
         KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), H->desc.size() * sizeof(NodeDesc),
                                  cudaMemcpyHostToDevice, c->stream));
-        const int nn = int(lv.size());
+        int nn = int(lv.size());
         if (nn == 0) continue;
         lvdesc.resize(nn);
         for (int a = 0; a < nn; ++a) lvdesc[a] = H->desc[lv[a]];
@@ -681,13 +785,17 @@ int id_sweep(HssImpl *H, bool &need_more) {
         if (!dl.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
         KRR_CUDA(cudaMemcpyAsync(dl.get(), lvdesc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
         const bool is_root_level = (h == H->H);
+        // the nodes of this level that get an ID (all but the whole-problem ones)
+        std::vector<int> lid;
+        for (int v : lv)
+            if (!H->is_top(v)) lid.push_back(v);
         if (h > 0) {
             { extract_b_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), X, H->d, inv2h2, F, H->IA.get(),
                                                                   H->ddesc.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
         }
         int mmax = 0;
-        for (int v : lv) mmax = std::max(mmax, H->desc[v].m);
+        for (int v : lid) mmax = std::max(mmax, H->desc[v].m);
         tr.mark("extract_b", h, nn, mmax);
         if (is_root_level) break;  // the root needs B only
         const int r = H->r;
@@ -696,7 +804,7 @@ int id_sweep(HssImpl *H, bool &need_more) {
             KRR_CUDA(cudaGetLastError());
             // S_a(J_a) - B_ab Rhat_b ;  S_b(J_b) - B_ab^T Rhat_a
             GemmBatch<T> gb;
-            for (int v : lv) {
+            for (int v : lid) {
                 const NodeDesc &N = H->desc[v];
                 const NodeDesc &A = H->desc[N.child_a], &B = H->desc[N.child_b];
                 T *Sl = F + N.sloc;
@@ -705,6 +813,27 @@ int id_sweep(HssImpl *H, bool &need_more) {
             }
             KRR_TRY(gb.launch(c));
             tr.mark("parent_sloc", h, nn, mmax);
+        }
+        if (int(lid.size()) != nn) {
+            // whole-problem nodes: rank 0 without an ID; the rest of the level continues alone
+            std::vector<NodeDesc> tops;
+            for (int v : lv)
+                if (H->is_top(v)) {
+                    H->desc[v].k = 0;
+                    tops.push_back(H->desc[v]);
+                }
+            DBuf<NodeDesc> dt(c, tops.size());
+            if (!dt.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+            KRR_CUDA(cudaMemcpyAsync(dt.get(), tops.data(), tops.size() * sizeof(NodeDesc), cudaMemcpyHostToDevice,
+                                     c->stream));
+            { noid_kernel<<<unsigned(tops.size()), 128, 0, c->stream>>>(dt.get(), H->IA.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+            nn = int(lid.size());
+            if (nn == 0) continue;
+            lvdesc.resize(nn);
+            for (int a = 0; a < nn; ++a) lvdesc[a] = H->desc[lid[a]];
+            KRR_CUDA(cudaMemcpyAsync(dl.get(), lvdesc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice,
+                                     c->stream));
         }
         if (mmax == 0) {
             // every node of the level is empty (its children have rank 0)
@@ -765,7 +894,7 @@ int id_sweep(HssImpl *H, bool &need_more) {
         KRR_CUDA(cudaMemcpyAsync(he.data(), derr.get(), 2 * nn * 4, cudaMemcpyDeviceToHost, c->stream));
         KRR_CUDA(cudaStreamSynchronize(c->stream));
         for (int a = 0; a < nn; ++a) {
-            H->desc[lv[a]].k = hr[a];
+            H->desc[lid[a]].k = hr[a];
             H->max_rank = std::max(H->max_rank, hr[a]);
             const double e_test = he[2 * a], e_in = he[2 * a + 1];
             H->max_test_err = std::max(H->max_test_err, e_test);
@@ -778,7 +907,7 @@ int id_sweep(HssImpl *H, bool &need_more) {
         {
             // R-hat += T R_loc(redundant)
             GemmBatch<T> gb;
-            for (int v : lv) {
+            for (int v : lid) {
                 const NodeDesc &N = H->desc[v];
                 const int k = N.k, nr = N.m - N.k;
                 gb.add(k, H->r, nr, T(1), F + N.tmat, nr, false, F + N.rg + int64_t(k) * H->r, H->r, false, T(1),
@@ -993,7 +1122,8 @@ int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64
 // lambda != 0 (Xa == Xp) adds lambda V.  Mixed: V is split into two FP16
 // parts so the product keeps FP32 precision in V.
 int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, const double *V, int64_t ldv, int nrhs,
-              double *out, int64_t ldo, double lambda, const double *y, int64_t ldy, double *res_norms) {
+              double *out, int64_t ldo, double lambda, const double *y, int64_t ldy, double *res_norms,
+              const BlockDiag *bd, const double *Xa64_rows = nullptr) {
     Ctx *c = H->c;
     const int64_t n = H->n;
     if (H->mixed()) {
@@ -1024,7 +1154,7 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
         { split16_kernel<<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(V, n, nrhs, ldv, Rs, cols); ::krr::count_launch(); }
         KRR_TRY(transpose_half(c, Rs, n, cols, cols, RTs, rpad, H->ldrt));
         KRR_TRY(sample_mixed_prepared(c, XAa, ma, H->XB.get(), n, H->d, RTs, cols, H->ldrt, nullptr, nullptr,
-                                      Sm, cols, true));
+                                      Sm, cols, true, bd));
         if (y)
             { residual_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
                 y, ldy, Sm, cols, 1, V, ldv, ma, nrhs, lambda, out, ldo, res_norms); ::krr::count_launch(); }
@@ -1034,14 +1164,14 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
     } else {
         DBuf<double> Sm(c, size_t(ma) * nrhs), Xa64;
         if (!Sm.get()) return fail(KRR_ERR_OOM, "hss: out of memory");
-        const double *Xa = H->Xp64.get();
-        if (Xa32 != H->Xp32.get()) {
+        const double *Xa = Xa64_rows ? Xa64_rows : H->Xp64.get();
+        if (!Xa64_rows && Xa32 != H->Xp32.get()) {
             if (!Xa64.reset(c, size_t(ma) * H->d)) return fail(KRR_ERR_OOM, "hss: out of memory");
             KRR_TRY(widen(c, Xa32, ma * H->d, Xa64.get()));
             Xa = Xa64.get();
         }
         KRR_TRY(launch_sample_f64(c, Xa, ma, H->Xp64.get(), n, H->d, H->opt.h, V, nrhs, ldv, nullptr, nullptr,
-                                  Sm.get(), nrhs));
+                                  Sm.get(), nrhs, bd));
         if (y)
             { residual_kernel<double><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
                 y, ldy, Sm.get(), nrhs, 0, V, ldv, ma, nrhs, lambda, out, ldo, res_norms); ::krr::count_launch(); }
@@ -1053,16 +1183,28 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
     return KRR_OK;
 }
 
-int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, HssImpl *H) {
+int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, HssImpl *H,
+              const std::vector<int64_t> *boff = nullptr, const std::vector<double> *bh = nullptr) {
     H->c = c;
     H->opt = *o;
     H->n = n;
     H->d = d;
     H->lambda = o->lambda;
+    if (boff) {
+        H->nprob = int(boff->size()) - 1;
+        H->boff = *boff;
+        H->bh = *bh;
+        H->opt.h = 1.0;  // coordinates are divided by each problem's width below
+        KRR_TRY(make_groups(c, H->boff, H->bgrp));
+        if (!H->dboff.reset(c, H->boff.size())) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(H->dboff.get(), H->boff.data(), H->boff.size() * 8, cudaMemcpyHostToDevice,
+                                 c->stream));
+        KRR_TRY(make_tile_list(c, H->boff, H->boff, H->tl_lo, H->tl_hi, H->tl_off, H->tl_tiles));
+    }
     const double t0 = now_ms();
     if (!H->perm.reset(c, n) || !H->leaf_of.reset(c, n) || !H->Xp32.reset(c, size_t(n) * d))
         return fail(KRR_ERR_OOM, "hss_compress: out of memory");
-    KRR_TRY(cluster(c, X, n, d, o->leaf, o->seed, H->perm.get(), H->tb, H->te, H->tl, H->tr, H->tp, H->tv));
+    KRR_TRY(cluster(c, X, n, d, o->leaf, o->seed, H->perm.get(), H->tb, H->te, H->tl, H->tr, H->tp, H->tv, boff));
     H->t_cluster = now_ms() - t0;
     const int nn = int(H->tb.size());
     H->root = nn - 1;
@@ -1073,6 +1215,13 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
     H->H = H->height[H->root];
     H->by_height.assign(H->H + 1, {});
     for (int v = 0; v < nn; ++v) H->by_height[H->height[v]].push_back(v);
+    if (H->nprob > 0) {
+        // whole-problem nodes: [begin, end) a union of whole problems
+        std::vector<char> bound(n + 1, 0);
+        for (int64_t b : H->boff) bound[b] = 1;
+        H->top.assign(nn, 0);
+        for (int v = 0; v < nn; ++v) H->top[v] = bound[H->tb[v]] && bound[H->te[v]];
+    }
     H->desc.assign(nn, NodeDesc{});
     for (int v = 0; v < nn; ++v) {
         NodeDesc &N = H->desc[v];
@@ -1097,6 +1246,8 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
         KRR_CUDA(cudaStreamSynchronize(c->stream));
     }
     KRR_TRY((gather_rows<float, float>(c, X, d, H->perm.get(), n, d, H->Xp32.get(), d)));
+    // batched: each problem's coordinates divided by its width (FP64 path: in FP64, below)
+    if (H->nprob > 0 && H->mixed()) KRR_TRY(scale_by_width(c, H->Xp32.get(), n, d, H->bgrp.get(), H->bh));
     H->r_cap = int(round_up(std::max(o->r0, o->r_max), 64));
     H->r = int(round_up(o->r0, 64));
     H->nrhs_cap = 64;
@@ -1107,14 +1258,15 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
             !H->R32.reset(c, size_t(n) * H->r_cap) || !H->S32.reset(c, size_t(n) * H->r_cap) ||
             !H->RT.reset(c, size_t(round_up(H->r_cap, 64)) * H->ldrt))
             return fail(KRR_ERR_OOM, "hss_compress: out of memory");
-        KRR_TRY(augment(c, H->Xp32.get(), n, d, o->h, 0, H->XA.get(), H->kpad));
-        KRR_TRY(augment(c, H->Xp32.get(), n, d, o->h, 1, H->XB.get(), H->kpad));
+        KRR_TRY(augment(c, H->Xp32.get(), n, d, H->opt.h, 0, H->XA.get(), H->kpad));
+        KRR_TRY(augment(c, H->Xp32.get(), n, d, H->opt.h, 1, H->XB.get(), H->kpad));
         KRR_TRY(compress<float>(H));
     } else {
         if (!H->Xp64.reset(c, size_t(n) * d) || !H->R64.reset(c, size_t(n) * H->r_cap) ||
             !H->S64.reset(c, size_t(n) * H->r_cap))
             return fail(KRR_ERR_OOM, "hss_compress: out of memory");
         KRR_TRY(widen(c, H->Xp32.get(), n * d, H->Xp64.get()));
+        if (H->nprob > 0) KRR_TRY(scale_by_width(c, H->Xp64.get(), n, d, H->bgrp.get(), H->bh));
         KRR_TRY(compress<double>(H));
     }
     // the samples are no longer needed
@@ -1138,6 +1290,7 @@ int hss_factor_impl(HssImpl *H) {
 int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, int max_refine, double &rmax) {
     Ctx *c = H->c;
     const int64_t n = H->n;
+    const BlockDiag btrain = H->bd_train();
     DBuf<double> res(c, size_t(n) * nrhs), norms(c, 2 * nrhs);
     if (!res.get() || !norms.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
     auto ulv = [&](const double *b, double *x) -> int {
@@ -1193,7 +1346,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
             // r = y - A alpha (precise product); V0 = r / |r|
             KRR_CUDA(cudaMemsetAsync(norms.get(), 0, 2 * nrhs * sizeof(double), c->stream));
             KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, ap, nrhs, nrhs, res.get(), nrhs, H->lambda,
-                              yp, nrhs, norms.get()));
+                              yp, nrhs, norms.get(), H->bd_or_null(btrain)));
             std::vector<double> hn(2 * nrhs);
             KRR_CUDA(cudaMemcpyAsync(hn.data(), norms.get(), 2 * nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
             KRR_CUDA(cudaStreamSynchronize(c->stream));
@@ -1218,7 +1371,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                 KRR_TRY(ulv(Vj, Zv.get()));
                 tr.mark("g_ulv", j, 0, 0);
                 KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, Zv.get(), nrhs, nrhs, Wv.get(), nrhs, H->lambda,
-                                  nullptr, 0, nullptr));
+                                  nullptr, 0, nullptr, H->bd_or_null(btrain)));
                 tr.mark("g_apply", j, 0, 0);
                 // two passes of classical Gram-Schmidt
                 std::fill(hd.begin(), hd.end(), 0.0);
@@ -1316,7 +1469,7 @@ int hss_solve_impl(HssImpl *H, const double *y, int nrhs, int64_t ldy, double *a
 }
 
 int hss_predict_impl(HssImpl *H, const float *Xt, int64_t m, const double *alpha, int nrhs, int64_t lda, double *out,
-                     int64_t ldo) {
+                     int64_t ldo, const BlockDiag *bd = nullptr, const double *Xt64 = nullptr) {
     Ctx *c = H->c;
     const int64_t n = H->n;
     DBuf<double> ap(c, size_t(n) * nrhs);
@@ -1327,7 +1480,40 @@ int hss_predict_impl(HssImpl *H, const float *Xt, int64_t m, const double *alpha
         if (!xa.reset(c, size_t(m) * H->kpad)) return fail(KRR_ERR_OOM, "krr_predict: out of memory");
         KRR_TRY(augment(c, Xt, m, H->d, H->opt.h, 0, xa.get(), H->kpad));
     }
-    return hss_apply(H, Xt, xa.get(), m, ap.get(), nrhs, nrhs, out, ldo, 0.0, nullptr, 0, nullptr);
+    return hss_apply(H, Xt, xa.get(), m, ap.get(), nrhs, nrhs, out, ldo, 0.0, nullptr, 0, nullptr, bd, Xt64);
+}
+
+// Decision values of a block-diagonal system: test rows [toff[p], toff[p+1])
+// against problem p's training points only.
+int hss_predict_batched_impl(HssImpl *H, const float *Xt, int64_t m, const std::vector<int64_t> &toff,
+                             const double *alpha, int nrhs, int64_t lda, double *out, int64_t ldo) {
+    Ctx *c = H->c;
+    const int d = H->d;
+    DBuf<float> xs(c, size_t(m) * d);
+    DBuf<int32_t> tgrp, lo, hi;
+    DBuf<int64_t> off;
+    if (!xs.get()) return fail(KRR_ERR_OOM, "krr_predict_batched: out of memory");
+    DBuf<double> xs64;
+    KRR_CUDA(cudaMemcpyAsync(xs.get(), Xt, size_t(m) * d * 4, cudaMemcpyDeviceToDevice, c->stream));
+    KRR_TRY(make_groups(c, toff, tgrp));
+    if (H->mixed()) {
+        KRR_TRY(scale_by_width(c, xs.get(), m, d, tgrp.get(), H->bh));
+    } else {
+        if (!xs64.reset(c, size_t(m) * d)) return fail(KRR_ERR_OOM, "krr_predict_batched: out of memory");
+        KRR_TRY(widen(c, Xt, m * d, xs64.get()));
+        KRR_TRY(scale_by_width(c, xs64.get(), m, d, tgrp.get(), H->bh));
+    }
+    BlockDiag b;
+    KRR_TRY(make_tile_list(c, toff, H->boff, lo, hi, off, b.tiles));
+    b.grp_a = tgrp.get();
+    b.grp_b = H->bgrp.get();
+    b.off_b = H->dboff.get();
+    b.tl_lo = lo.get();
+    b.tl_hi = hi.get();
+    b.tl_off = off.get();
+    KRR_TRY(hss_predict_impl(H, xs.get(), m, alpha, nrhs, lda, out, ldo, &b, xs64.get()));
+    KRR_CUDA(cudaStreamSynchronize(c->stream));  // the temporaries above die here
+    return KRR_OK;
 }
 
 // ------------------------------------------------------------ gradient
@@ -1604,6 +1790,49 @@ int hss_compress(krr_ctx *k, const float *X, int64_t n, int32_t d, const krr_opt
     return KRR_OK;
 }
 
+int hss_compress_batched(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t nprob, const int64_t *offsets,
+                         const double *h, const krr_options *o, krr_hss **out) {
+    if (out) *out = nullptr;
+    if (!k || !X || !o || !out || !offsets || !h || n <= 0 || d <= 0 || nprob < 1)
+        return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: bad arguments");
+    if (!(o->lambda > 0) || !(o->eps_c > 0) || o->eps_abs < 0 || o->leaf < 1 || o->r0 < 1 || o->p < 0 ||
+        o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64))
+        return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: bad options");
+    if (o->precision == KRR_MIXED && d > kMaxMixedDim)
+        return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress_batched: mixed path supports d <= 82");
+    if (n > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: n too large");
+    std::vector<int64_t> off(offsets, offsets + nprob + 1);
+    std::vector<double> hw(h, h + nprob);
+    if (off[0] != 0 || off[nprob] != n) return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: bad offsets");
+    for (int p = 0; p < nprob; ++p)
+        if (off[p + 1] <= off[p] || !(hw[p] > 0))
+            return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: empty problem or width <= 0");
+    krr_hss *H = new (std::nothrow) krr_hss();
+    if (!H) return fail(KRR_ERR_OOM, "hss_compress_batched: host allocation failed");
+    const int s = hss_build(&k->c, X, n, d, o, &H->h, &off, &hw);
+    if (s != KRR_OK) {
+        delete H;
+        return s;
+    }
+    *out = H;
+    return KRR_OK;
+}
+
+int krr_predict_batched(krr_hss *H, const float *Xt, int64_t m, const int64_t *test_offsets, const double *alpha,
+                        int32_t nrhs, int64_t lda, double *out, int64_t ldo) {
+    if (!H || !test_offsets || !alpha || m < 0 || nrhs < 1 || nrhs > 64 || lda < nrhs || ldo < nrhs ||
+        (m > 0 && (!Xt || !out)))
+        return fail(KRR_ERR_INVALID_ARG, "krr_predict_batched: bad arguments");
+    if (H->h.nprob == 0) return fail(KRR_ERR_INVALID_ARG, "krr_predict_batched: not a batched handle");
+    const int P = H->h.nprob;
+    std::vector<int64_t> toff(test_offsets, test_offsets + P + 1);
+    if (toff[0] != 0 || toff[P] != m) return fail(KRR_ERR_INVALID_ARG, "krr_predict_batched: bad offsets");
+    for (int p = 0; p < P; ++p)
+        if (toff[p + 1] < toff[p]) return fail(KRR_ERR_INVALID_ARG, "krr_predict_batched: bad offsets");
+    if (m == 0) return KRR_OK;
+    return hss_predict_batched_impl(&H->h, Xt, m, toff, alpha, nrhs, lda, out, ldo);
+}
+
 int hss_update_lambda(krr_hss *H, double lambda) {
     if (!H || !(lambda > 0)) return fail(KRR_ERR_INVALID_ARG, "hss_update_lambda: bad arguments");
     H->h.lambda = lambda;
@@ -1631,6 +1860,7 @@ int krr_predict(krr_hss *H, const float *Xt, int64_t m, const double *alpha, int
                 int64_t ldo) {
     if (!H || !Xt || !alpha || !out || m < 0 || nrhs < 1 || nrhs > 64 || lda < nrhs || ldo < nrhs)
         return fail(KRR_ERR_INVALID_ARG, "krr_predict: bad arguments");
+    if (H->h.nprob > 0) return fail(KRR_ERR_INVALID_ARG, "krr_predict: batched handle (use krr_predict_batched)");
     if (m == 0) return KRR_OK;
     return hss_predict_impl(&H->h, Xt, m, alpha, nrhs, lda, out, ldo);
 }
@@ -1641,6 +1871,7 @@ int krr_heldout_grad(krr_hss *H, const float *Xt, int64_t m, const double *y, co
     if (!H || !Xt || !y || !yt || !loss || m < 1 || max_refine < 0 || (dX && lddx < H->h.d))
         return fail(KRR_ERR_INVALID_ARG, "krr_heldout_grad: bad arguments");
     if (m > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "krr_heldout_grad: m too large");
+    if (H->h.nprob > 0) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_heldout_grad: batched handle");
     return heldout_grad_impl(&H->h, Xt, m, y, yt, tol, max_refine, loss, dh, dlambda, dX, lddx, alpha, resid);
 }
 

@@ -27,12 +27,30 @@ inline int aug_chunks(int d) { return int(cdiv(aug_used(d), 64)); }
 inline int aug_kpad(int d) { return 64 * aug_chunks(d); }
 constexpr int kMaxMixedDim = 82;  // 3d + 6 <= 256: at most four 64-element chunks
 
+// A block-diagonal product: many independent problems whose rows are
+// contiguous ranges of A and of B; a pair (i, j) is kept only when
+// grp_a[i] == grp_b[j].  The tensor-core kernel walks only the 128 x 128
+// tiles that meet a diagonal block: row tile rt covers column tiles
+// [tl_lo[rt], tl_hi[rt]], numbered from tl_off[rt] (tl_off has one entry
+// per row tile plus the total).  off_b (nprob + 1 entries) gives the first
+// row of each problem in B, for the FP64 kernel.  All device arrays.
+constexpr int kTcTile = 128;  // rows and columns of one tile of the tensor-core product
+
+struct BlockDiag {
+    const int32_t *grp_a = nullptr, *grp_b = nullptr;
+    const int64_t *off_b = nullptr;
+    const int32_t *tl_lo = nullptr, *tl_hi = nullptr;
+    const int64_t *tl_off = nullptr;
+    int64_t tiles = 0;
+};
+
 int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
-                     const int32_t *leaf_b, float *S, int64_t lds, bool split_k = false);
+                     const int32_t *leaf_b, float *S, int64_t lds, bool split_k = false,
+                     const BlockDiag *bd = nullptr);
 int launch_sample_f64(Ctx *c, const double *Xa, int64_t ma, const double *Xb, int64_t nb, int d, double h,
                       const double *R, int r, int64_t ldr, const int32_t *leaf_a, const int32_t *leaf_b, double *S,
-                      int64_t lds);
+                      int64_t lds, const BlockDiag *bd = nullptr);
 
 // Mixed-precision product on already-prepared operands: S = W o K R over
 // any number of columns (split into launches of <= 256 columns).  S is
@@ -40,6 +58,7 @@ int launch_sample_f64(Ctx *c, const double *Xa, int64_t ma, const double *Xb, in
 // as an FP16 pair K_hi + K_lo (about 2^-22 relative instead of 2^-11).
 int sample_mixed_prepared(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int d,
                           const __half *RT, int r_total, int64_t ldrt, const int32_t *leaf_a,
-                          const int32_t *leaf_b, float *S, int64_t lds, bool split_k = false);
+                          const int32_t *leaf_b, float *S, int64_t lds, bool split_k = false,
+                          const BlockDiag *bd = nullptr);
 
 }  // namespace krr

@@ -15,7 +15,8 @@ constexpr int F_BM = 64, F_BC = 64, F_BJ = 32, F_MAXD = 64;
 __global__ void __launch_bounds__(256) sample_f64_kernel(const double *Xa, int64_t ma, const double *Xb, int64_t nb,
                                                          int d, double inv2h2, const double *R, int r, int64_t ldr,
                                                          const int32_t *leaf_a, const int32_t *leaf_b, double *S,
-                                                         int64_t lds) {
+                                                         int64_t lds, const int32_t *grp_a, const int32_t *grp_b,
+                                                         const int64_t *off_b) {
     __shared__ double sxa[F_BM][F_MAXD + 1];
     __shared__ double sxb[F_BJ][F_MAXD + 1];
     __shared__ double sk[F_BM][F_BJ + 1];
@@ -29,15 +30,21 @@ __global__ void __launch_bounds__(256) sample_f64_kernel(const double *Xa, int64
         const int ii = k / d, kk = k % d;
         sxa[ii][kk] = (i0 + ii < ma) ? Xa[(i0 + ii) * d + kk] : 0.0;
     }
-    for (int64_t j0 = 0; j0 < nb; j0 += F_BJ) {
+    // block-diagonal product: only the columns of the problems of this row block
+    int64_t jlo = 0, jhi = nb;
+    if (grp_a) {
+        jlo = off_b[grp_a[i0]];
+        jhi = off_b[grp_a[min(i0 + F_BM, ma) - 1] + 1];
+    }
+    for (int64_t j0 = jlo; j0 < jhi; j0 += F_BJ) {
         __syncthreads();
         for (int k = tid; k < F_BJ * d; k += 256) {
             const int jj = k / d, kk = k % d;
-            sxb[jj][kk] = (j0 + jj < nb) ? Xb[(j0 + jj) * d + kk] : 0.0;
+            sxb[jj][kk] = (j0 + jj < jhi) ? Xb[(j0 + jj) * d + kk] : 0.0;
         }
         for (int k = tid; k < F_BJ * F_BC; k += 256) {
             const int jj = k / F_BC, cc = k % F_BC;
-            sr[jj][cc] = (j0 + jj < nb && c0 + cc < r) ? R[(j0 + jj) * ldr + c0 + cc] : 0.0;
+            sr[jj][cc] = (j0 + jj < jhi && c0 + cc < r) ? R[(j0 + jj) * ldr + c0 + cc] : 0.0;
         }
         __syncthreads();
         for (int k = tid; k < F_BM * F_BJ; k += 256) {
@@ -49,8 +56,9 @@ __global__ void __launch_bounds__(256) sample_f64_kernel(const double *Xa, int64
             }
             double kv = exp(-s * inv2h2);
             const int64_t i = i0 + ii, j = j0 + jj;
-            if (j >= nb || i >= ma) kv = 0.0;
+            if (j >= jhi || i >= ma) kv = 0.0;
             else if (leaf_a && leaf_b && leaf_a[i] == leaf_b[j]) kv = 0.0;
+            else if (grp_a && grp_a[i] != grp_b[j]) kv = 0.0;
             sk[ii][jj] = kv;
         }
         __syncthreads();
@@ -75,12 +83,13 @@ __global__ void __launch_bounds__(256) sample_f64_kernel(const double *Xa, int64
 
 int launch_sample_f64(Ctx *c, const double *Xa, int64_t ma, const double *Xb, int64_t nb, int d, double h,
                       const double *R, int r, int64_t ldr, const int32_t *leaf_a, const int32_t *leaf_b, double *S,
-                      int64_t lds) {
+                      int64_t lds, const BlockDiag *bd) {
     if (d > F_MAXD) return fail(KRR_ERR_NOT_IMPLEMENTED, "sample_f64: d > 64");
     if (ma == 0 || r == 0) return KRR_OK;
     dim3 grid(unsigned(cdiv(ma, F_BM)), unsigned(cdiv(r, F_BC)));
     { sample_f64_kernel<<<grid, 256, 0, c->stream>>>(Xa, ma, Xb, nb, d, 1.0 / (2.0 * h * h), R, r, ldr, leaf_a, leaf_b,
-                                                   S, lds); ::krr::count_launch(); }
+                                                   S, lds, bd ? bd->grp_a : nullptr,
+                                                   bd ? bd->grp_b : nullptr, bd ? bd->off_b : nullptr); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }

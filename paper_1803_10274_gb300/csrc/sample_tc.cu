@@ -29,6 +29,7 @@
 #include <cuda.h>
 
 #include "common.cuh"
+#include "prep.cuh"
 #include "tc_ptx.cuh"
 
 namespace krr {
@@ -41,6 +42,8 @@ constexpr int kChunk = 64;           // FP16 elements per 128-byte swizzled row
 constexpr int kChunkBytes = 128 * 128;
 constexpr int kMaxStages = 6;
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
+
+static_assert(kBM == kTcTile && kBN == kTcTile, "tile lists assume square 128-row tiles");
 
 struct Params {
     int64_t ma, nb;
@@ -57,6 +60,14 @@ struct Params {
     int a_bufs;   // row-tile (A) buffers in shared memory: 2, or 1 for wide feature rows
     uint32_t off_a, off_stage, stage_bytes, off_bar;
     const int32_t *leaf_a, *leaf_b;
+    // block-diagonal products (many independent problems in one launch):
+    // problem id per row of A and B (keep a pair only within a problem),
+    // and the tile list: row tile rt covers column tiles [tl_lo, tl_hi],
+    // its tiles numbered from tl_off[rt]; NULL = every tile of the grid
+    const int32_t *grp_a, *grp_b;
+    const int32_t *tl_lo, *tl_hi;
+    const int64_t *tl_off;
+    int64_t n_tiles;
     float *S;
     int64_t lds;
     DevStatus *status;
@@ -113,22 +124,37 @@ __device__ __forceinline__ void mask_pack(uint32_t (&pk)[16], uint32_t m) {
     }
 }
 
-// Bits of the columns whose leaf equals row i's leaf, for a tile whose
-// leaf ranges overlap (rows and columns are in the same cluster order).
+// Bits of the columns to drop for row i: the same leaf of the cluster
+// tree (tiles whose leaf ranges overlap; rows and columns are in the same
+// cluster order) or another problem (tiles that straddle a problem
+// boundary).
 __device__ __forceinline__ void tile_mask(const Params &P, int rt, int ct, int g, int64_t i, uint32_t &mlo,
                                        uint32_t &mhi) {
     const int64_t ia = int64_t(rt) * kBM, ib = min(ia + kBM - 1, P.ma - 1);
     const int64_t ja = int64_t(ct) * kBN, jb = min(ja + kBN - 1, P.nb - 1);
-    const int32_t lo = max(__ldg(P.leaf_a + ia), __ldg(P.leaf_b + ja));
-    const int32_t hi = min(__ldg(P.leaf_a + ib), __ldg(P.leaf_b + jb));
     mlo = mhi = 0;
-    if (lo > hi) return;
-    const int32_t li = __ldg(P.leaf_a + min(i, P.ma - 1));
+    bool leaf_x = false, grp_x = false;
+    if (P.leaf_a != nullptr) {
+        const int32_t lo = max(__ldg(P.leaf_a + ia), __ldg(P.leaf_b + ja));
+        const int32_t hi = min(__ldg(P.leaf_a + ib), __ldg(P.leaf_b + jb));
+        leaf_x = lo <= hi;
+    }
+    if (P.grp_a != nullptr) {
+        const int32_t g0 = __ldg(P.grp_a + ia);
+        grp_x = !(g0 == __ldg(P.grp_a + ib) && g0 == __ldg(P.grp_b + ja) && g0 == __ldg(P.grp_b + jb));
+    }
+    if (!leaf_x && !grp_x) return;
+    const int64_t ic = min(i, P.ma - 1);
+    const int32_t li = leaf_x ? __ldg(P.leaf_a + ic) : 0;
+    const int32_t gi = grp_x ? __ldg(P.grp_a + ic) : 0;
     const int64_t j0 = int64_t(ct) * kBN + 64 * g;
 #pragma unroll 1
     for (int c = 0; c < 32; ++c) {
-        if (j0 + c < P.nb && __ldg(P.leaf_b + j0 + c) == li) mlo |= 1u << c;
-        if (j0 + 32 + c < P.nb && __ldg(P.leaf_b + j0 + 32 + c) == li) mhi |= 1u << c;
+        const int64_t j = j0 + c, j2 = j0 + 32 + c;
+        if (j < P.nb && ((leaf_x && __ldg(P.leaf_b + j) == li) || (grp_x && __ldg(P.grp_b + j) != gi)))
+            mlo |= 1u << c;
+        if (j2 < P.nb && ((leaf_x && __ldg(P.leaf_b + j2) == li) || (grp_x && __ldg(P.grp_b + j2) != gi)))
+            mhi |= 1u << c;
     }
 }
 
@@ -159,30 +185,50 @@ __device__ __forceinline__ void flush_s(const Params &P, uint64_t *bars, volatil
 }
 
 // Position in a CTA's range of tile steps, advanced incrementally (no
-// integer division in the loops): tile (rt, ct), shared-memory stage and
-// distance-buffer rings with their phase bits, row-tile segment count.
+// integer division in the loops): tile (rt, ct), the column-tile range
+// [lo, hi] of row tile rt, shared-memory stage and distance-buffer rings
+// with their phase bits, row-tile segment count.
 struct Cursor {
-    int loc, rt, ct, stage, db, seg;
+    int loc, rt, ct, lo, hi, stage, db, seg;
     uint32_t sphase, dphase;
     bool first, last;
-    __device__ __forceinline__ void init(int64_t t0, int nct) {
+    __device__ __forceinline__ void init(const Params &P, int64_t t0, int nct) {
         loc = 0;
-        rt = int(t0 / nct);
-        ct = int(t0 % nct);
+        if (P.tl_off != nullptr) {
+            int a = 0, b = int(P.n_row_tiles) - 1;  // last row tile whose first tile is <= t0
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (__ldg(P.tl_off + mid) <= t0) a = mid;
+                else b = mid - 1;
+            }
+            rt = a;
+            lo = __ldg(P.tl_lo + rt);
+            hi = __ldg(P.tl_hi + rt);
+            ct = lo + int(t0 - __ldg(P.tl_off + rt));
+        } else {
+            rt = int(t0 / nct);
+            ct = int(t0 % nct);
+            lo = 0;
+            hi = nct - 1;
+        }
         stage = db = 0;
         sphase = dphase = 0;
         seg = 0;
     }
     // flags of the current tile; `first` opens a new row-tile segment
-    __device__ __forceinline__ void flags(int nloc, int nct) {
-        first = (loc == 0) || (ct == 0);
-        last = (loc == nloc - 1) || (ct == nct - 1);
+    __device__ __forceinline__ void flags(int nloc) {
+        first = (loc == 0) || (ct == lo);
+        last = (loc == nloc - 1) || (ct == hi);
     }
-    __device__ __forceinline__ void next(int nct, int NS, int ND) {
+    __device__ __forceinline__ void next(const Params &P, int nloc, int NS, int ND) {
         ++loc;
-        if (++ct == nct) {
-            ct = 0;
+        if (++ct > hi) {
             ++rt;
+            if (P.tl_off != nullptr && loc < nloc) {
+                lo = __ldg(P.tl_lo + rt);
+                hi = __ldg(P.tl_hi + rt);
+            }
+            ct = lo;
         }
         if (++stage == NS) {
             stage = 0;
@@ -207,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int nct = int(P.n_col_tiles);
-    const int64_t T = P.n_row_tiles * P.n_col_tiles;
+    const int64_t T = P.n_tiles;
     const int64_t t0 = T * blockIdx.x / gridDim.x;
     const int nloc = int(T * (blockIdx.x + 1) / gridDim.x - t0);
     const int NS = P.nstage, ND = P.ndist;
@@ -249,10 +295,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0 && lane == 0 && nloc > 0) {
         // ------------------------------------------------ TMA producer
         Cursor c;
-        c.init(t0, nct);
+        c.init(P, t0, nct);
         int issued = 0, a_issued = -1;
-        for (; c.loc < nloc; c.next(nct, NS, 1)) {
-            c.flags(nloc, nct);
+        for (; c.loc < nloc; c.next(P, nloc, NS, 1)) {
+            c.flags(nloc);
             if (c.first) {
                 const int seg = c.seg++;
                 const int ab = P.a_bufs == 2 ? (seg & 1) : 0;
@@ -294,11 +340,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t idesc_d = idesc_f16_f32(kBM, kBN);
         const uint32_t idesc_p = idesc_f16_f32(kBM, P.r);
         Cursor cd, cp;  // distance-side and product-side positions
-        cd.init(t0, nct);
-        cp.init(t0, nct);
+        cd.init(P, t0, nct);
+        cp.init(P, t0, nct);
         bool ok = true;
         auto issue_dist = [&]() -> bool {
-            cd.flags(nloc, nct);
+            cd.flags(nloc);
             if (cd.first) {
                 ++cd.seg;
                 const int sg = cd.seg - 1;
@@ -319,13 +365,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_commit(&bars[BAR_DFULL + cd.db]);
             if (cd.last) tc_commit(&bars[BAR_AEMPTY + abuf]);
-            cd.next(nct, NS, ND);
+            cd.next(P, nloc, NS, ND);
             return true;
         };
         for (int k = 0; ok && k < ND - 1 && k < nloc; ++k) ok = issue_dist();
-        for (; ok && cp.loc < nloc; cp.next(nct, NS, ND)) {
+        for (; ok && cp.loc < nloc; cp.next(P, nloc, NS, ND)) {
             if (cd.loc < nloc && !issue_dist()) break;
-            cp.flags(nloc, nct);
+            cp.flags(nloc);
             if (cp.first) {
                 const int seg = cp.seg++;
                 const uint32_t par = P.s_bufs == 2 ? uint32_t((seg >> 1) & 1) : uint32_t(seg & 1);
@@ -374,20 +420,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_off = uint32_t(32 * q) << 16;
         const int rh = P.r >> 1;
         Cursor c;
-        c.init(t0, nct);
+        c.init(P, t0, nct);
         uint32_t va[32], vb[32];
         bool ok = warp_wait(&bars[BAR_DFULL + 0], 0u, abort_flag, kWaitBudget, P.status, 7);
         if (ok) {
             tc_fence_after();
             tmem_ld32(tmem + lane_off + uint32_t(P.dist_col0 + 64 * g), va);
         }
-        for (; ok && c.loc < nloc; c.next(nct, 1, ND)) {
-            c.flags(nloc, nct);
+        for (; ok && c.loc < nloc; c.next(P, nloc, 1, ND)) {
+            c.flags(nloc);
             if (c.first) ++c.seg;
             const uint32_t base = tmem + lane_off + uint32_t(P.dist_col0 + c.db * kBN + 64 * g);
             const int64_t i = int64_t(c.rt) * kBM + 32 * q + lane;
             uint32_t mlo = 0, mhi = 0;
-            if (P.leaf_a != nullptr) tile_mask(P, c.rt, c.ct, g, i, mlo, mhi);
+            if (P.leaf_a != nullptr || P.grp_a != nullptr) tile_mask(P, c.rt, c.ct, g, i, mlo, mhi);
             tmem_wait_ld_regs(va);                 // chunk 0 of this tile
             tmem_ld32(base + 32, vb);              // chunk 1 in flight
             uint32_t pk[16];
@@ -485,7 +531,7 @@ int make_map(CUtensorMap *m, const void *base, int64_t cols, int64_t rows, int64
 // nchunk elements each); RT: FP16, rpad x ldrt (row c = column c of R).
 int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
-                     const int32_t *leaf_b, float *S, int64_t lds, bool split_k) {
+                     const int32_t *leaf_b, float *S, int64_t lds, bool split_k, const BlockDiag *bd) {
     if (rpad % 64 != 0 || rpad < 64 || rpad > 256) return fail(KRR_ERR_INVALID_ARG, "sample_tc: r must be 64..256, /64");
     if (nchunk < 1 || nchunk > 4) return fail(KRR_ERR_INVALID_ARG, "sample_tc: feature dimension too large");
     if (ma <= 0 || nb <= 0) return KRR_OK;
@@ -535,6 +581,15 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     if (smem < 120 * 1024) smem = 120 * 1024;
     P.leaf_a = leaf_a;
     P.leaf_b = leaf_b;
+    P.n_tiles = P.n_row_tiles * P.n_col_tiles;
+    if (bd) {
+        P.grp_a = bd->grp_a;
+        P.grp_b = bd->grp_b;
+        P.tl_lo = bd->tl_lo;
+        P.tl_hi = bd->tl_hi;
+        P.tl_off = bd->tl_off;
+        P.n_tiles = bd->tiles;
+    }
     P.S = S;
     P.lds = lds;
     P.status = c->status;
@@ -545,7 +600,8 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
                                       227 * 1024));
         attr_set = true;
     }
-    const int64_t T = P.n_row_tiles * P.n_col_tiles;
+    const int64_t T = P.n_tiles;
+    if (T <= 0) return KRR_OK;
     const int grid = int(T < c->num_sms ? T : c->num_sms);
     { tc::sample_tc_kernel<<<grid, tc::kThreads, smem, c->stream>>>(mA, mB, mR, P); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
