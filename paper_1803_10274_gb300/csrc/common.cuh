@@ -87,8 +87,11 @@ __device__ __forceinline__ void dev_fail(DevStatus *st, int code, int where) {
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Count of kernel launches made by this library (all threads).
+// Count of kernel launches made by this library (all threads); kernels
+// replayed from a captured CUDA graph count once per replay.
 void count_launch();
+void count_launches(long long k);
+long long launches_so_far();
 inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 
 // --------------------------------------------------- Philox4x64-10 (device)

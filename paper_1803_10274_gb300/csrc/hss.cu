@@ -552,6 +552,23 @@ struct HssImpl {
     double max_test_err = 0;
     double t_cluster = 0, t_sample = 0, t_compress = 0, t_factor = 0, t_solve = 0;
     bool mixed() const { return opt.precision == KRR_MIXED; }
+    // The ULV solve as a captured CUDA graph, replayed on the context's
+    // stream (valid for one plan, one pair of fixed buffers, one nrhs).
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t ulv_exec = nullptr;
+    const void *g_y = nullptr, *g_x = nullptr;
+    int g_nrhs = -1;
+    long long g_kernels = 0;
+    DBuf<double> ws_b64, ws_x64;
+    void drop_graph() {
+        if (ulv_exec) cudaGraphExecDestroy(ulv_exec);
+        ulv_exec = nullptr;
+        g_nrhs = -1;
+    }
+    ~HssImpl() {
+        drop_graph();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 namespace {
@@ -1040,6 +1057,7 @@ template <class T>
 int build_solve_plan(HssImpl *H, int nrhs) {
     Ctx *c = H->c;
     T *F = farena<T>(H);
+    H->drop_graph();  // the captured solve refers to the old plan
     H->plan.clear();
     H->plan.resize(H->H + 1);
     for (int h = 0; h <= H->H; ++h) {
@@ -1112,6 +1130,48 @@ int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64
         { scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(P.dl.get(), H->ddesc.get(), nrhs, F); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
+    return KRR_OK;
+}
+
+// ulv_solve through a captured CUDA graph: captured on a private stream the
+// first time (and whenever the plan, the buffers or nrhs change), then
+// replayed on the context's stream.  y and x must be the same fixed
+// buffers on every call for the replay to be reused.
+template <class T>
+int ulv_solve_graph(HssImpl *H, const T *y, T *x, int nrhs) {
+    Ctx *c = H->c;
+    if (H->plan_nrhs != nrhs) KRR_TRY(build_solve_plan<T>(H, nrhs));
+    if (!H->ulv_exec || H->g_y != y || H->g_x != x || H->g_nrhs != nrhs) {
+        H->drop_graph();
+        if (!H->cap_stream) KRR_CUDA(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t keep = c->stream;
+        c->stream = H->cap_stream;
+        const long long k0 = launches_so_far();
+        cudaError_t e = cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal);
+        int s = e == cudaSuccess ? ulv_solve<T>(H, y, nrhs, nrhs, x, nrhs) : KRR_OK;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(H->cap_stream, &g) : e;
+        c->stream = keep;
+        H->g_kernels = launches_so_far() - k0;
+        count_launches(-H->g_kernels);  // recorded, not run: counted at each replay
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+        if (s != KRR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture", __FILE__, __LINE__);
+        const cudaError_t e3 = cudaGraphInstantiate(&H->ulv_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) {
+            H->ulv_exec = nullptr;
+            return cuda_fail(e3, "cudaGraphInstantiate", __FILE__, __LINE__);
+        }
+        H->g_y = y;
+        H->g_x = x;
+        H->g_nrhs = nrhs;
+    }
+    KRR_CUDA(cudaGraphLaunch(H->ulv_exec, c->stream));
+    count_launches(H->g_kernels);
     return KRR_OK;
 }
 
@@ -1280,6 +1340,7 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
 
 int hss_factor_impl(HssImpl *H) {
     H->plan_nrhs = -1;  // the cached solve plan refers to the old factors
+    H->drop_graph();
     return H->mixed() ? factor<float>(H) : factor<double>(H);
 }
 
@@ -1300,12 +1361,18 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                 return fail(KRR_ERR_OOM, "hss_solve: out of memory");
             float *bf = H->ws_bf.get(), *xf = H->ws_xf.get();
             { convert_kernel<double, float><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(b, n * nrhs, bf); ::krr::count_launch(); }
-            KRR_TRY(ulv_solve<float>(H, bf, nrhs, nrhs, xf, nrhs));
+            KRR_TRY(ulv_solve_graph<float>(H, bf, xf, nrhs));
             { convert_kernel<float, double><<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(xf, n * nrhs, x); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             return KRR_OK;
         }
-        return ulv_solve<double>(H, b, nrhs, nrhs, x, nrhs);
+        if (H->ws_b64.n < size_t(n) * nrhs &&
+            (!H->ws_b64.reset(c, size_t(n) * nrhs) || !H->ws_x64.reset(c, size_t(n) * nrhs)))
+            return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(H->ws_b64.get(), b, size_t(n) * nrhs * 8, cudaMemcpyDeviceToDevice, c->stream));
+        KRR_TRY(ulv_solve_graph<double>(H, H->ws_b64.get(), H->ws_x64.get(), nrhs));
+        KRR_CUDA(cudaMemcpyAsync(x, H->ws_x64.get(), size_t(n) * nrhs * 8, cudaMemcpyDeviceToDevice, c->stream));
+        return KRR_OK;
     };
     rmax = -1.0;
     H->refine_steps = 0;
