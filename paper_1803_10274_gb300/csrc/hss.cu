@@ -197,6 +197,187 @@ __global__ void __launch_bounds__(cta::kNT) id_prep_kernel(const NodeDesc *nd, c
         for (int a = threadIdx.x; a < m; a += blockDim.x) I[N.rows + a] = N.leaf_begin + a;
 }
 
+// Row ID from the Gram matrix (one CTA of NT threads per node).  With
+// G = S S^T over the sample columns that enter the decomposition (rows of
+// S_loc, G in F + drr), a left-looking Cholesky of G with diagonal
+// pivoting picks at each step the row with the largest remaining squared
+// norm, exactly the row a column-pivoted QR of S^T would pick, and its
+// factor L is R^T of that QR (P G P^T = L L^T = R^T R).  So the rank rule
+// (|R_jj| > eps |R_11| and > eps_abs), T = R11^{-1} R12 and the in-sample
+// error sqrt(remaining diagonal / trace G) are those of the QR, from
+// O(m^2) data instead of O(m r).  L (position x step) goes to the w
+// workspace with row stride r, the remaining diagonal to norm.
+template <class T, int NT>
+__device__ void argmax_nt(T &val, int &idx) {
+    __shared__ T sv[NT / 32];
+    __shared__ int si[NT / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, val, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = val; si[threadIdx.x >> 5] = idx; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        val = threadIdx.x < NT / 32 ? sv[threadIdx.x] : T(-1);
+        idx = threadIdx.x < NT / 32 ? si[threadIdx.x] : 0x7fffffff;
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, val, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+        }
+        if (threadIdx.x == 0) { sv[0] = val; si[0] = idx; }
+    }
+    __syncthreads();
+    val = sv[0];
+    idx = si[0];
+    __syncthreads();
+}
+
+template <class T, int NT>
+__device__ T sum_nt(T v) {
+    __shared__ T sh[NT / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = T(0);
+    for (int w = 0; w < NT / 32; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) gram_id_kernel(NodeDesc *nd, const NodeDesc *all, const T *S, const T *R,
+                                                     int64_t ldsr, int r, T *F, int32_t *I, T eps, T eps_abs,
+                                                     int kmax, int *ranks, float *test_err) {
+    NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    const int rid = r - kHoldOut;
+    const T *G = F + N.drr;
+    T *L = F + N.w;
+    T *d = F + N.norm;
+    int32_t *piv = I + N.piv;
+    int32_t *rows = I + N.rows;
+    extern __shared__ unsigned char gram_smem[];
+    T *lj = reinterpret_cast<T *>(gram_smem);  // row j of L (steps 0 .. j-1)
+    __shared__ int s_k;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (N.is_leaf)
+        for (int a = threadIdx.x; a < m; a += NT) rows[a] = N.leaf_begin + a;
+    T tot0 = T(0);
+    for (int i = threadIdx.x; i < m; i += NT) {
+        piv[i] = i;
+        const T g = G[int64_t(i) * m + i];
+        d[i] = g > T(0) ? g : T(0);
+        tot0 += d[i];
+    }
+    if (threadIdx.x == 0) s_k = 0;
+    tot0 = sum_nt<T, NT>(tot0);  // synchronizes
+    T r11 = T(0);
+    const int jmax = min(min(m, rid), kmax);
+    for (int j = 0; j < jmax; ++j) {
+        T best = T(-1);
+        int bi = 0x7fffffff;
+        for (int i = j + threadIdx.x; i < m; i += NT)
+            if (d[i] > best) { best = d[i]; bi = i; }
+        argmax_nt<T, NT>(best, bi);
+        const T nrm = sqrt(best > T(0) ? best : T(0));
+        if (j == 0) r11 = nrm;
+        if (!(nrm > eps * r11) || !(nrm > eps_abs)) break;
+        const int p = bi;
+        if (p != j) {
+            for (int t = threadIdx.x; t < j; t += NT) {
+                const T a = L[int64_t(j) * r + t];
+                L[int64_t(j) * r + t] = L[int64_t(p) * r + t];
+                L[int64_t(p) * r + t] = a;
+            }
+            if (threadIdx.x == 0) {
+                const int a = piv[j]; piv[j] = piv[p]; piv[p] = a;
+                const T b = d[j]; d[j] = d[p]; d[p] = b;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < j; t += NT) lj[t] = L[int64_t(j) * r + t];
+        if (threadIdx.x == 0) L[int64_t(j) * r + j] = nrm;
+        __syncthreads();
+        const int pj = piv[j];
+        const T inv = T(1) / nrm;
+        // column j below the pivot: (G(piv i, piv j) - L(i, :j) . L(j, :j)) / L_jj
+        for (int i = j + 1 + w; i < m; i += NT / 32) {
+            const T *li = L + int64_t(i) * r;
+            T dot = T(0);
+            for (int t = l; t < j; t += 32) dot += li[t] * lj[t];
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            if (l == 0) {
+                const T v = (G[int64_t(piv[i]) * m + pj] - dot) * inv;
+                L[int64_t(i) * r + j] = v;
+                d[i] -= v * v;
+            }
+        }
+        if (threadIdx.x == 0) s_k = j + 1;
+        __syncthreads();
+    }
+    const int k = s_k;
+    T rest = T(0);
+    for (int i = k + threadIdx.x; i < m; i += NT) rest += d[i] > T(0) ? d[i] : T(0);
+    rest = sum_nt<T, NT>(rest);
+    const T in_err = tot0 > T(0) ? sqrt(rest / tot0) : T(0);
+    // T = R11^{-1} R12 with R = L^T: back substitution per redundant row
+    T *Tm = F + N.tmat;
+    const int nr = m - k;
+    for (int c = threadIdx.x; c < nr; c += NT) {
+        for (int a = k - 1; a >= 0; --a) {
+            T sacc = L[int64_t(k + c) * r + a];
+            for (int b = a + 1; b < k; ++b) sacc -= L[int64_t(b) * r + a] * Tm[int64_t(b) * nr + c];
+            Tm[int64_t(a) * nr + c] = sacc / L[int64_t(a) * r + a];
+        }
+    }
+    __syncthreads();
+    // held-out columns [rid, r): || S_r - T^T S_s || / || S || with rows through piv
+    const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
+    const int64_t lds = N.is_leaf ? ldsr : r;
+    const int nh = r - rid;
+    T err = T(0), tot = T(0);
+    for (int e = threadIdx.x; e < m * nh; e += NT) {
+        const int c = e / nh, t = rid + e % nh;
+        const T v = Sorig[int64_t(piv[c]) * lds + t];
+        tot += v * v;
+        if (c >= k) {
+            T sacc = v;
+            for (int a = 0; a < k; ++a) sacc -= Tm[int64_t(a) * nr + (c - k)] * Sorig[int64_t(piv[a]) * lds + t];
+            err += sacc * sacc;
+        }
+    }
+    err = sum_nt<T, NT>(err);
+    tot = sum_nt<T, NT>(tot);
+    if (threadIdx.x == 0) {
+        N.k = k;
+        ranks[blockIdx.x] = k;
+        test_err[2 * blockIdx.x] = float(tot > T(0) ? sqrt(err / tot) : T(0));
+        test_err[2 * blockIdx.x + 1] = float(in_err);
+    }
+    for (int a = threadIdx.x; a < k; a += NT) I[N.jsk + a] = rows[piv[a]];
+    for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += NT) {
+        const int a = int(e / r), t = int(e % r);
+        F[N.skel + e] = Sorig[int64_t(piv[a]) * lds + t];
+    }
+    // R_loc rows in pivot order: R(I) at a leaf, [Rhat_a; Rhat_b] at a parent
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
+    T *Rg = F + N.rg;
+    T *Rh = F + N.rhat;
+    for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += NT) {
+        const int a = int(e / r), t = int(e % r);
+        const int src = piv[a];
+        T v;
+        if (N.is_leaf) v = R[(int64_t(N.leaf_begin) + src) * ldsr + t];
+        else if (src < A->k) v = F[A->rhat + int64_t(src) * r + t];
+        else v = F[B->rhat + int64_t(src - A->k) * r + t];
+        Rg[e] = v;
+        if (a < k) Rh[e] = v;
+    }
+}
+
 // Nodes that stay whole: rank 0, local rows in their natural order.
 __global__ void noid_kernel(const NodeDesc *nd, int32_t *I) {
     const NodeDesc &N = nd[blockIdx.x];
@@ -852,10 +1033,36 @@ int id_sweep(HssImpl *H, bool &need_more) {
             KRR_CUDA(cudaMemcpyAsync(dl.get(), lvdesc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice,
                                      c->stream));
         }
+        // The Gram form needs eps^2 well above the rounding of the Gram
+        // matrix; tighter tolerances take the QR of the samples.
+        const bool gram = H->opt.eps_c >= (H->mixed() ? 1e-2 : 1e-5);
         if (mmax == 0) {
             // every node of the level is empty (its children have rank 0)
             KRR_CUDA(cudaMemsetAsync(dranks.get(), 0, nn * sizeof(int), c->stream));
             KRR_CUDA(cudaMemsetAsync(derr.get(), 0, 2 * nn * sizeof(float), c->stream));
+        } else if (gram) {
+            // G = S_loc S_loc^T over the columns that enter the decomposition
+            const int rid = r - kHoldOut;
+            GemmBatch<T> gg;
+            for (int a = 0; a < nn; ++a) {
+                const NodeDesc &N = lvdesc[a];
+                const T *So = N.is_leaf ? S + int64_t(N.leaf_begin) * H->r_cap : F + N.sloc;
+                const int64_t lds = N.is_leaf ? H->r_cap : r;
+                gg.add(N.m, N.m, rid, T(1), So, lds, false, So, lds, true, T(0), F + N.drr, N.m);
+            }
+            KRR_TRY(gg.launch(c));
+            const size_t smem = size_t(std::min(std::min(mmax, rid), kmax)) * sizeof(T);
+            if (mmax <= 256)
+                { gram_id_kernel<T, 256><<<nn, 256, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, r, F,
+                                                                       H->IA.get(), T(H->opt.eps_c),
+                                                                       T(H->opt.eps_abs), kmax, dranks.get(),
+                                                                       derr.get()); ::krr::count_launch(); }
+            else
+                { gram_id_kernel<T, 1024><<<nn, 1024, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, r,
+                                                                         F, H->IA.get(), T(H->opt.eps_c),
+                                                                         T(H->opt.eps_abs), kmax, dranks.get(),
+                                                                         derr.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
         } else if (mmax < kBigNode && nn >= c->num_sms) {
             const size_t smem = size_t(r) * sizeof(T);
             static bool attr = false;
