@@ -246,122 +246,138 @@ __device__ T sum_nt(T v) {
     return t;
 }
 
+// Blocked form (LAPACK-style, right-looking between panels): panels of
+// kPanel pivots run in one CTA per node (gram_panel_kernel), each followed
+// by the update G -= L_p L_p^T of the panel's columns as one grouped GEMM
+// over all nodes of the level.  Nothing is interchanged: rows keep their
+// local index q, L is stored column-major by q (L(q, t) at w[t m + q]),
+// a chosen row's remaining diagonal becomes -inf, and piv lists the chosen
+// rows in pivot order (the rest follow in index order at the end).
+constexpr int kPanel = 32;
+
+template <class T>
+struct GramState {
+    int k, done;
+    T r11, tot0;
+};
+
 template <class T, int NT>
-__global__ void __launch_bounds__(NT) gram_id_kernel(NodeDesc *nd, const NodeDesc *all, const T *S, const T *R,
-                                                     int64_t ldsr, int r, T *F, int32_t *I, T eps, T eps_abs,
-                                                     int kmax, int *ranks, float *test_err) {
-    NodeDesc &N = nd[blockIdx.x];
+__global__ void __launch_bounds__(NT) gram_init_kernel(const NodeDesc *nd, T *F, int32_t *I, GramState<T> *st) {
+    const NodeDesc &N = nd[blockIdx.x];
     const int m = N.m;
-    const int rid = r - kHoldOut;
     const T *G = F + N.drr;
-    T *L = F + N.w;
     T *d = F + N.norm;
-    int32_t *piv = I + N.piv;
-    int32_t *rows = I + N.rows;
-    extern __shared__ unsigned char gram_smem[];
-    T *lj = reinterpret_cast<T *>(gram_smem);  // row j of L (steps 0 .. j-1)
-    __shared__ int s_k;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (N.is_leaf)
-        for (int a = threadIdx.x; a < m; a += NT) rows[a] = N.leaf_begin + a;
-    T tot0 = T(0);
+    T tot = T(0);
     for (int i = threadIdx.x; i < m; i += NT) {
-        piv[i] = i;
+        if (N.is_leaf) I[N.rows + i] = N.leaf_begin + i;
         const T g = G[int64_t(i) * m + i];
         d[i] = g > T(0) ? g : T(0);
-        tot0 += d[i];
+        tot += d[i];
     }
-    if (threadIdx.x == 0) s_k = 0;
-    tot0 = sum_nt<T, NT>(tot0);  // synchronizes
-    T r11 = T(0);
+    tot = sum_nt<T, NT>(tot);
+    if (threadIdx.x == 0) {
+        st[blockIdx.x].k = 0;
+        st[blockIdx.x].done = m == 0 ? 1 : 0;
+        st[blockIdx.x].r11 = T(0);
+        st[blockIdx.x].tot0 = tot;
+    }
+}
+
+// Pivots [j0, j0 + kPanel) of every unfinished node: column j of L is
+// (G(q, p_j) - sum_{t in [j0, j)} L(q, t) L(p_j, t)) / L(p_j, j) over the
+// rows not yet chosen, G already updated by the earlier panels.  Stops at
+// the rank rule or at jmax.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) gram_panel_kernel(const NodeDesc *nd, T *F, int32_t *I, GramState<T> *st,
+                                                        int j0, int rid, int kmax, T eps, T eps_abs) {
+    GramState<T> &S = st[blockIdx.x];
+    if (S.done) return;
+    const NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    const T *A = F + N.drr;
+    T *Lc = F + N.w;
+    T *d = F + N.norm;
+    int32_t *piv = I + N.piv;
     const int jmax = min(min(m, rid), kmax);
-    for (int j = 0; j < jmax; ++j) {
+    const int jend = min(j0 + kPanel, jmax);
+    T r11 = S.r11;
+    int j = j0;
+    for (; j < jend; ++j) {
         T best = T(-1);
         int bi = 0x7fffffff;
-        for (int i = j + threadIdx.x; i < m; i += NT)
-            if (d[i] > best) { best = d[i]; bi = i; }
-        argmax_nt<T, NT>(best, bi);
+        for (int q = threadIdx.x; q < m; q += NT)
+            if (d[q] > best) { best = d[q]; bi = q; }
+        argmax_nt<T, NT>(best, bi);  // synchronizes
         const T nrm = sqrt(best > T(0) ? best : T(0));
         if (j == 0) r11 = nrm;
         if (!(nrm > eps * r11) || !(nrm > eps_abs)) break;
         const int p = bi;
-        if (p != j) {
-            for (int t = threadIdx.x; t < j; t += NT) {
-                const T a = L[int64_t(j) * r + t];
-                L[int64_t(j) * r + t] = L[int64_t(p) * r + t];
-                L[int64_t(p) * r + t] = a;
-            }
-            if (threadIdx.x == 0) {
-                const int a = piv[j]; piv[j] = piv[p]; piv[p] = a;
-                const T b = d[j]; d[j] = d[p]; d[p] = b;
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < j; t += NT) lj[t] = L[int64_t(j) * r + t];
-        if (threadIdx.x == 0) L[int64_t(j) * r + j] = nrm;
-        __syncthreads();
-        const int pj = piv[j];
         const T inv = T(1) / nrm;
-        // column j below the pivot: (G(piv i, piv j) - L(i, :j) . L(j, :j)) / L_jj
-        for (int i = j + 1 + w; i < m; i += NT / 32) {
-            const T *li = L + int64_t(i) * r;
-            T dot = T(0);
-            for (int t = l; t < j; t += 32) dot += li[t] * lj[t];
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-            if (l == 0) {
-                const T v = (G[int64_t(piv[i]) * m + pj] - dot) * inv;
-                L[int64_t(i) * r + j] = v;
-                d[i] -= v * v;
+        const T *gp = A + int64_t(p) * m;  // row p of the symmetric G: column p
+        for (int q = threadIdx.x; q < m; q += NT) {
+            if (q == p) {
+                Lc[int64_t(j) * m + q] = nrm;
+                continue;
             }
+            if (!(d[q] >= T(0))) continue;  // already chosen
+            T sacc = gp[q];
+            for (int t = j0; t < j; ++t) sacc -= Lc[int64_t(t) * m + q] * Lc[int64_t(t) * m + p];
+            const T v = sacc * inv;
+            Lc[int64_t(j) * m + q] = v;
+            const T dq = d[q] - v * v;
+            d[q] = dq > T(0) ? dq : T(0);
         }
-        if (threadIdx.x == 0) s_k = j + 1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            piv[j] = p;
+            d[p] = -INFINITY;
+        }
         __syncthreads();
     }
-    const int k = s_k;
-    T rest = T(0);
-    for (int i = k + threadIdx.x; i < m; i += NT) rest += d[i] > T(0) ? d[i] : T(0);
-    rest = sum_nt<T, NT>(rest);
-    const T in_err = tot0 > T(0) ? sqrt(rest / tot0) : T(0);
-    // T = R11^{-1} R12 with R = L^T: back substitution per redundant row
-    T *Tm = F + N.tmat;
-    const int nr = m - k;
-    for (int c = threadIdx.x; c < nr; c += NT) {
-        for (int a = k - 1; a >= 0; --a) {
-            T sacc = L[int64_t(k + c) * r + a];
-            for (int b = a + 1; b < k; ++b) sacc -= L[int64_t(b) * r + a] * Tm[int64_t(b) * nr + c];
-            Tm[int64_t(a) * nr + c] = sacc / L[int64_t(a) * r + a];
-        }
+    if (threadIdx.x == 0) {
+        S.r11 = r11;
+        S.k = j;
+        if (j < jend || j == jmax) S.done = 1;
+    }
+}
+
+// After the factorization, in three steps.  gram_prep_kernel: the unchosen
+// rows appended to piv, skeleton ids and samples, R_loc in pivot order and
+// R-hat's first rows, L gathered into pivot order (m x k row-major in the
+// dmat slot) and the right-hand side L21^T in T's place.  Then T =
+// R11^{-1} R12 (R = L^T) by blocked back substitution: per block of
+// kTrsmBlock rows from the bottom, the triangular diagonal block in one CTA
+// per node (gram_trsm_diag_kernel) and the update of the rows above as a
+// grouped GEMM.  gram_test_kernel: in-sample and held-out errors.
+constexpr int kTrsmBlock = 64;
+
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) gram_prep_kernel(const NodeDesc *nd, const NodeDesc *all,
+                                                       const GramState<T> *st, const T *S, const T *R, int64_t ldsr,
+                                                       int r, T *F, int32_t *I) {
+    const NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    const int k = st[blockIdx.x].k;
+    const T *Lc = F + N.w;
+    const T *d = F + N.norm;
+    int32_t *piv = I + N.piv;
+    int32_t *pos = I + N.ipiv;
+    const int32_t *rows = I + N.rows;
+    if (threadIdx.x == 0) {
+        int a = k;
+        for (int q = 0; q < m; ++q)
+            if (d[q] >= T(0)) piv[a++] = q;
     }
     __syncthreads();
-    // held-out columns [rid, r): || S_r - T^T S_s || / || S || with rows through piv
+    for (int a = threadIdx.x; a < m; a += NT) pos[piv[a]] = a;
     const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
     const int64_t lds = N.is_leaf ? ldsr : r;
-    const int nh = r - rid;
-    T err = T(0), tot = T(0);
-    for (int e = threadIdx.x; e < m * nh; e += NT) {
-        const int c = e / nh, t = rid + e % nh;
-        const T v = Sorig[int64_t(piv[c]) * lds + t];
-        tot += v * v;
-        if (c >= k) {
-            T sacc = v;
-            for (int a = 0; a < k; ++a) sacc -= Tm[int64_t(a) * nr + (c - k)] * Sorig[int64_t(piv[a]) * lds + t];
-            err += sacc * sacc;
-        }
-    }
-    err = sum_nt<T, NT>(err);
-    tot = sum_nt<T, NT>(tot);
-    if (threadIdx.x == 0) {
-        N.k = k;
-        ranks[blockIdx.x] = k;
-        test_err[2 * blockIdx.x] = float(tot > T(0) ? sqrt(err / tot) : T(0));
-        test_err[2 * blockIdx.x + 1] = float(in_err);
-    }
+    T *Sk = F + N.skel;
     for (int a = threadIdx.x; a < k; a += NT) I[N.jsk + a] = rows[piv[a]];
     for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += NT) {
         const int a = int(e / r), t = int(e % r);
-        F[N.skel + e] = Sorig[int64_t(piv[a]) * lds + t];
+        Sk[e] = Sorig[int64_t(piv[a]) * lds + t];
     }
-    // R_loc rows in pivot order: R(I) at a leaf, [Rhat_a; Rhat_b] at a parent
     const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
     const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
     T *Rg = F + N.rg;
@@ -375,6 +391,83 @@ __global__ void __launch_bounds__(NT) gram_id_kernel(NodeDesc *nd, const NodeDes
         else v = F[B->rhat + int64_t(src - A->k) * r + t];
         Rg[e] = v;
         if (a < k) Rh[e] = v;
+    }
+    __syncthreads();
+    T *Lp = F + N.dmat;
+    for (int64_t e = threadIdx.x; e < int64_t(m) * k; e += NT) {  // reads of Lc coalesced over q
+        const int b = int(e / m), q = int(e % m);
+        const int a = pos[q];
+        Lp[int64_t(a) * k + b] = (b <= a) ? Lc[e] : T(0);
+    }
+    __syncthreads();
+    T *Tm = F + N.tmat;
+    const int nr = m - k;
+    for (int64_t e = threadIdx.x; e < int64_t(k) * nr; e += NT) {
+        const int a = int(e / nr), c = int(e % nr);
+        Tm[e] = Lp[int64_t(k + c) * k + a];
+    }
+}
+
+// Rows [a0, min(a1, k)) of T: back substitution with the diagonal block of L11^T.
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) gram_trsm_diag_kernel(const NodeDesc *nd, const GramState<T> *st, T *F, int a0,
+                                                            int a1) {
+    const NodeDesc &N = nd[blockIdx.x];
+    const int k = st[blockIdx.x].k;
+    const int hi = min(a1, k);
+    if (hi <= a0) return;
+    const int nr = N.m - k;
+    const T *Lp = F + N.dmat;
+    T *Tm = F + N.tmat;
+    for (int c = threadIdx.x; c < nr; c += NT) {
+        for (int a = hi - 1; a >= a0; --a) {
+            T sacc = Tm[int64_t(a) * nr + c];
+            for (int b = a + 1; b < hi; ++b) sacc -= Lp[int64_t(b) * k + a] * Tm[int64_t(b) * nr + c];
+            Tm[int64_t(a) * nr + c] = sacc / Lp[int64_t(a) * k + a];
+        }
+    }
+}
+
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) gram_test_kernel(NodeDesc *nd, const GramState<T> *st, const T *S,
+                                                       int64_t ldsr, int r, T *F, const int32_t *I, int *ranks,
+                                                       float *test_err) {
+    NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    const int rid = r - kHoldOut;
+    const int k = st[blockIdx.x].k;
+    const T tot0 = st[blockIdx.x].tot0;
+    const T *d = F + N.norm;
+    const int32_t *piv = I + N.piv;
+    T rest = T(0);
+    for (int q = threadIdx.x; q < m; q += NT) rest += d[q] >= T(0) ? d[q] : T(0);
+    rest = sum_nt<T, NT>(rest);
+    const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
+    const int64_t lds = N.is_leaf ? ldsr : r;
+    const T *Sk = F + N.skel;
+    const T *Tm = F + N.tmat;
+    const int nr = m - k;
+    const int nh = r - rid;
+    T err = T(0), tot = T(0);
+    for (int e = threadIdx.x; e < nr * nh; e += NT) {
+        const int c = e % nr, t = rid + e / nr;
+        const T v = Sorig[int64_t(piv[k + c]) * lds + t];
+        tot += v * v;
+        T sacc = v;
+        for (int a = 0; a < k; ++a) sacc -= Tm[int64_t(a) * nr + c] * Sk[int64_t(a) * r + t];
+        err += sacc * sacc;
+    }
+    for (int e = threadIdx.x; e < k * nh; e += NT) {
+        const T v = Sk[int64_t(e / nh) * r + rid + e % nh];
+        tot += v * v;
+    }
+    err = sum_nt<T, NT>(err);
+    tot = sum_nt<T, NT>(tot);
+    if (threadIdx.x == 0) {
+        N.k = k;
+        ranks[blockIdx.x] = k;
+        test_err[2 * blockIdx.x] = float(tot > T(0) ? sqrt(err / tot) : T(0));
+        test_err[2 * blockIdx.x + 1] = float(tot0 > T(0) ? sqrt(rest / tot0) : T(0));
     }
 }
 
@@ -1051,17 +1144,63 @@ int id_sweep(HssImpl *H, bool &need_more) {
                 gg.add(N.m, N.m, rid, T(1), So, lds, false, So, lds, true, T(0), F + N.drr, N.m);
             }
             KRR_TRY(gg.launch(c));
-            const size_t smem = size_t(std::min(std::min(mmax, rid), kmax)) * sizeof(T);
-            if (mmax <= 256)
-                { gram_id_kernel<T, 256><<<nn, 256, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, r, F,
-                                                                       H->IA.get(), T(H->opt.eps_c),
-                                                                       T(H->opt.eps_abs), kmax, dranks.get(),
-                                                                       derr.get()); ::krr::count_launch(); }
-            else
-                { gram_id_kernel<T, 1024><<<nn, 1024, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, r,
-                                                                         F, H->IA.get(), T(H->opt.eps_c),
-                                                                         T(H->opt.eps_abs), kmax, dranks.get(),
-                                                                         derr.get()); ::krr::count_launch(); }
+            tr.mark("id_gram", h, nn, mmax);
+            DBuf<GramState<T>> gs(c, nn);
+            if (!gs.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+            const bool wide = mmax > 256;
+            if (wide) { gram_init_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get()); ::krr::count_launch(); }
+            else { gram_init_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+            const int jmax = std::min(std::min(mmax, rid), kmax);
+            std::vector<GramState<T>> hs(nn);
+            std::vector<char> live(nn, 1);
+            for (int j0 = 0; j0 < jmax; j0 += kPanel) {
+                if (wide) { gram_panel_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs)); ::krr::count_launch(); }
+                else { gram_panel_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs)); ::krr::count_launch(); }
+                KRR_CUDA(cudaGetLastError());
+                KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
+                                         c->stream));
+                KRR_CUDA(cudaStreamSynchronize(c->stream));
+                // update of the nodes still running: G -= L_p L_p^T (L_p: m x kPanel, column-major)
+                GemmBatch<T> gt;
+                for (int a = 0; a < nn; ++a) {
+                    if (hs[a].done) continue;
+                    const NodeDesc &N = lvdesc[a];
+                    const T *Lp = F + N.w + int64_t(j0) * N.m;
+                    gt.add(N.m, N.m, kPanel, T(-1), Lp, N.m, true, Lp, N.m, false, T(1), F + N.drr, N.m);
+                }
+                if (gt.v.empty()) break;
+                KRR_TRY(gt.launch(c));
+            }
+            tr.mark("id_panels", h, nn, mmax);
+            KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
+                                     c->stream));
+            KRR_CUDA(cudaStreamSynchronize(c->stream));
+            if (wide) { gram_prep_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), H->ddesc.get(), gs.get(), S, R, H->r_cap, r, F, H->IA.get()); ::krr::count_launch(); }
+            else { gram_prep_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), H->ddesc.get(), gs.get(), S, R, H->r_cap, r, F, H->IA.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+            int kmx = 0;
+            for (int a = 0; a < nn; ++a) kmx = std::max(kmx, hs[a].k);
+            for (int a1 = int(round_up(kmx, kTrsmBlock)); a1 > 0; a1 -= kTrsmBlock) {
+                const int a0 = a1 - kTrsmBlock;
+                { gram_trsm_diag_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), gs.get(), F, a0, a1); ::krr::count_launch(); }
+                KRR_CUDA(cudaGetLastError());
+                if (a0 == 0) break;
+                // rows [0, a0) of T -= (L(a0:a1, 0:a0))^T T(a0:a1, :)
+                GemmBatch<T> gu;
+                for (int a = 0; a < nn; ++a) {
+                    const NodeDesc &N = lvdesc[a];
+                    const int k = hs[a].k, nr = N.m - k;
+                    const int hi = std::min(a1, k);
+                    if (hi <= a0 || nr <= 0) continue;
+                    gu.add(a0, nr, hi - a0, T(-1), F + N.dmat + int64_t(a0) * k, k, true,
+                           F + N.tmat + int64_t(a0) * nr, nr, false, T(1), F + N.tmat, nr);
+                }
+                KRR_TRY(gu.launch(c));
+            }
+            tr.mark("id_trsm", h, nn, mmax);
+            if (wide) { gram_test_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), gs.get(), S, H->r_cap, r, F, H->IA.get(), dranks.get(), derr.get()); ::krr::count_launch(); }
+            else { gram_test_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), gs.get(), S, H->r_cap, r, F, H->IA.get(), dranks.get(), derr.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
         } else if (mmax < kBigNode && nn >= c->num_sms) {
             const size_t smem = size_t(r) * sizeof(T);
