@@ -207,11 +207,17 @@ typedef struct {
     int32_t r_max;     /* cap on random columns                             */
     uint64_t seed;     /* seeds clustering and the random block             */
     int32_t precision; /* krr_precision                                     */
-    int32_t reserved;
+    int32_t flags;     /* KRR_TRUNCATE_AT_RMAX, or 0                        */
 } krr_options;
 
+/* krr_options.flags: when the ranks are not revealed within r_max samples,
+ * keep every decomposition truncated at the budget (rank r_max - 16 - p + 1
+ * at most; a coarser approximation, still a usable preconditioner for the
+ * refined solve) instead of failing with KRR_ERR_RANK_BUDGET. */
+#define KRR_TRUNCATE_AT_RMAX 1
+
 /* Fill opts with defaults: eps_c 0.03, eps_abs 0, leaf 128, r0 64, p 10,
- * r_max 2048, seed 1, KRR_MIXED; h and lambda set to 1. */
+ * r_max 2048, seed 1, KRR_MIXED, flags 0; h and lambda set to 1. */
 void krr_default_options(krr_options *opts);
 
 /* Cluster X (device float n x d, original order, already standardized if
@@ -323,6 +329,9 @@ typedef struct {
     int32_t n_nodes, n_levels, max_rank, samples, rounds, refine_steps;
     int64_t memory_bytes; /* D, U and B generators (Section 4.2 metric) */
     double t_cluster_ms, t_sample_ms, t_compress_ms, t_factor_ms, t_solve_ms;
+    int32_t truncated;    /* 1: ranks kept at the r_max budget
+                             (KRR_TRUNCATE_AT_RMAX)                      */
+    int32_t pad;
 } krr_hss_stats;
 
 int hss_stats(const krr_hss *H, krr_hss_stats *st);

@@ -18,6 +18,7 @@ KRR_OK = 0
 STATUS = {0: "KRR_OK", 1: "KRR_ERR_INVALID_ARG", 2: "KRR_ERR_NONFINITE_INPUT", 3: "KRR_ERR_OOM",
           4: "KRR_ERR_SINGULAR", 5: "KRR_ERR_RANK_BUDGET", 6: "KRR_ERR_TIMEOUT", 7: "KRR_ERR_CUDA",
           8: "KRR_ERR_NOT_IMPLEMENTED", 9: "KRR_ERR_NO_CONVERGENCE"}
+KRR_TRUNCATE_AT_RMAX = 1
 KRR_MIXED, KRR_FP64 = 0, 1
 
 P = ctypes.c_void_p
@@ -36,13 +37,14 @@ class krr_tree_arrays(ctypes.Structure):
 
 class krr_options(ctypes.Structure):
     _fields_ = [("h", f64), ("lam", f64), ("eps_c", f64), ("eps_abs", f64), ("leaf", i32), ("r0", i32),
-                ("p", i32), ("r_max", i32), ("seed", u64), ("precision", i32), ("reserved", i32)]
+                ("p", i32), ("r_max", i32), ("seed", u64), ("precision", i32), ("flags", i32)]
 
 
 class krr_hss_stats(ctypes.Structure):
     _fields_ = [("n", i64), ("n_nodes", i32), ("n_levels", i32), ("max_rank", i32), ("samples", i32),
                 ("rounds", i32), ("refine_steps", i32), ("memory_bytes", i64), ("t_cluster_ms", f64),
-                ("t_sample_ms", f64), ("t_compress_ms", f64), ("t_factor_ms", f64), ("t_solve_ms", f64)]
+                ("t_sample_ms", f64), ("t_compress_ms", f64), ("t_factor_ms", f64), ("t_solve_ms", f64),
+                ("truncated", i32), ("pad", i32)]
 
 
 SIGNATURES = {

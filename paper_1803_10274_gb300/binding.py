@@ -11,9 +11,9 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import KRR_FP64, KRR_MIXED, KRRError, check, lib
+from ._lib import KRR_FP64, KRR_MIXED, KRR_TRUNCATE_AT_RMAX, KRRError, check, lib
 
-__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "krr_standardize", "krr_cluster", "krr_sample",
+__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_TRUNCATE_AT_RMAX", "krr_standardize", "krr_cluster", "krr_sample",
            "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "HSS", "hss_compress", "default_options",
            "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]
 

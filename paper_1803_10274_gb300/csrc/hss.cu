@@ -783,6 +783,7 @@ struct HssImpl {
     DBuf<double> F64;
     DBuf<int32_t> IA;
     int nrhs_cap = 0;
+    int64_t arena_f = 0, arena_i = 0;  // elements of F32/F64 and IA in use
     bool factored = false;
     // cached solve plan (rebuilt when the factorization or nrhs changes)
     struct LevelPlan {
@@ -822,7 +823,11 @@ struct HssImpl {
     // 0 without an ID and are eliminated whole
     std::vector<char> top;
     bool is_top(int v) const { return !top.empty() && top[v]; }
+    // IDs from the Gram matrix need eps^2 well above its rounding; tighter
+    // tolerances take the QR of the samples
+    bool use_gram() const { return opt.eps_c >= (mixed() ? 1e-2 : 1e-5); }
     int max_rank = 0, refine_steps = 0;
+    bool truncated = false;
     double max_test_err = 0;
     double t_cluster = 0, t_sample = 0, t_compress = 0, t_factor = 0, t_solve = 0;
     bool mixed() const { return opt.precision == KRR_MIXED; }
@@ -954,41 +959,52 @@ float *farena<float>(HssImpl *H) { return H->F32.get(); }
 template <>
 double *farena<double>(HssImpl *H) { return H->F64.get(); }
 
-// Lay out every node's arena slots given the ranks known so far (levels
-// up to `upto` final).  Capacities depend only on m, r and nrhs_cap.
-int layout(HssImpl *H, int nrhs_cap, size_t &fsize, size_t &isize) {
+// Lay out the arena slots of the nodes at height h, whose m is exact once
+// their children's ranks are known, after the slots already taken (running
+// offsets fo, io in elements).  Capacities depend on m, r and nrhs_cap.
+void layout_level(HssImpl *H, int h, int nrhs_cap, int64_t &fo, int64_t &io) {
     const int64_t r = H->r;
-    int64_t fo = 0, io = 0;
-    for (int h = 0; h <= H->H; ++h) {
-        for (int v : H->by_height[h]) {
-            NodeDesc &N = H->desc[v];
-            const int64_t m = N.m;
-            auto take = [&](int64_t cnt) { const int64_t o = fo; fo += (cnt + 63) & ~int64_t(63); return o; };
-            auto itake = [&](int64_t cnt) { const int64_t o = io; io += (cnt + 15) & ~int64_t(15); return o; };
-            N.sloc = N.is_leaf ? -1 : take(m * r);
-            N.skel = take(m * r);
-            N.rhat = take(m * r);
-            N.w = take(m * r);
-            N.rg = take(m * r);
-            N.tmat = take(m * m);
-            N.norm = take(m);
-            N.bmat = N.is_leaf ? -1 : take(int64_t(N.ka) * N.kb);
-            N.dmat = take(m * m);
-            N.dtil = take(m * m);
-            N.drs = take(m * m);
-            N.drr = take(m * m);
-            N.ymat = take(m * m);
-            N.zvec = take(m * nrhs_cap);
-            N.btil = take(m * nrhs_cap);
-            N.xloc = take(m * nrhs_cap);
-            N.piv = itake(m);
-            N.rows = itake(m);
-            N.jsk = itake(m);
-            N.ipiv = itake(m);
-        }
+    for (int v : H->by_height[h]) {
+        NodeDesc &N = H->desc[v];
+        const int64_t m = N.m;
+        auto take = [&](int64_t cnt) { const int64_t o = fo; fo += (cnt + 63) & ~int64_t(63); return o; };
+        auto itake = [&](int64_t cnt) { const int64_t o = io; io += (cnt + 15) & ~int64_t(15); return o; };
+        // whole-problem nodes take no ID: no sample slots beyond S_loc
+        const int64_t rs = H->is_top(v) ? 0 : r;
+        N.sloc = N.is_leaf ? -1 : take(m * r);
+        N.skel = take(m * rs);
+        N.rhat = take(m * rs);
+        N.w = take(m * (H->use_gram() ? std::min(m, rs) : rs));
+        N.rg = take(m * rs);
+        N.tmat = take(m * m);
+        N.norm = take(m);
+        N.bmat = N.is_leaf ? -1 : take(int64_t(N.ka) * N.kb);
+        N.dmat = take(m * m);
+        N.dtil = take(m * m);
+        N.drs = take(m * m);
+        N.drr = take(m * m);
+        N.ymat = take(m * m);
+        N.zvec = take(m * nrhs_cap);
+        N.btil = take(m * nrhs_cap);
+        N.xloc = take(m * nrhs_cap);
+        N.piv = itake(m);
+        N.rows = itake(m);
+        N.jsk = itake(m);
+        N.ipiv = itake(m);
     }
-    fsize = size_t(fo);
-    isize = size_t(io);
+}
+
+// Grow an arena to hold at least `need` elements, keeping its first `used`
+// elements (1.5x growth, so a sweep reallocates a few times at most).
+template <class T>
+int grow_arena(Ctx *c, DBuf<T> &a, int64_t used, int64_t need) {
+    if (int64_t(a.n) >= need) return KRR_OK;
+    const int64_t cap = std::max(need, int64_t(a.n) + int64_t(a.n) / 2);
+    DBuf<T> b(c, size_t(cap));
+    if (!b.get()) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+    if (used > 0 && a.get())
+        KRR_CUDA(cudaMemcpyAsync(b.get(), a.get(), size_t(used) * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    a = std::move(b);
     return KRR_OK;
 }
 
@@ -1016,7 +1032,7 @@ int sample_columns(HssImpl *H, int c0, int c1) {
 // One bottom-up ID sweep with the current r.  Returns KRR_OK and sets
 // `need_more` when some node's rank exceeds r - p.
 template <class T>
-int id_sweep(HssImpl *H, bool &need_more) {
+int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
     Ctx *c = H->c;
     need_more = false;
     const T *S = H->mixed() ? reinterpret_cast<const T *>(H->S32.get()) : reinterpret_cast<const T *>(H->S64.get());
@@ -1024,29 +1040,26 @@ int id_sweep(HssImpl *H, bool &need_more) {
     const T inv2h2 = T(1.0 / (2.0 * H->opt.h * H->opt.h));
     const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
     const int kmax = H->r - kHoldOut - H->opt.p + 1;  // one past the budget: a rank there means "need more"
-    // Arenas are laid out once per level from the actual sizes; since the
-    // parents' m depend on the children's ranks, lay out level by level
-    // into a growing arena.
-    size_t fsize = 0, isize = 0;
-    // first pass: leaves only have known m; allocate generous capacity
-    // for parents by bounding m with min(sum of children's m, 2 (r - p)).
-    for (int h = 1; h <= H->H; ++h)
-        for (int v : H->by_height[h]) {
-            NodeDesc &N = H->desc[v];
-            N.ka = std::max(0, std::min(H->desc[N.child_a].m, kmax));
-            N.kb = std::max(0, std::min(H->desc[N.child_b].m, kmax));
-            N.m = N.ka + N.kb;
+    // The arena is laid out level by level: a parent's m (the sum of its
+    // children's ranks) is exact when its level comes, so every slot has its
+    // final size and the arena grows as the sweep goes up.
+    int64_t fo = 0, io = 0;
+    T *F = nullptr;
+    auto arena = [&](int h) -> int {
+        layout_level(H, h, H->nrhs_cap, fo, io);
+        if (H->mixed()) {
+            KRR_TRY(grow_arena(c, H->F32, H->arena_f, fo));
+            F = reinterpret_cast<T *>(H->F32.get());
+        } else {
+            KRR_TRY(grow_arena(c, H->F64, H->arena_f, fo));
+            F = reinterpret_cast<T *>(H->F64.get());
         }
-    layout(H, H->nrhs_cap, fsize, isize);
-    T *F;
-    if (H->mixed()) {
-        if (H->F32.n < fsize && !H->F32.reset(c, fsize)) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
-        F = reinterpret_cast<T *>(H->F32.get());
-    } else {
-        if (H->F64.n < fsize && !H->F64.reset(c, fsize)) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
-        F = reinterpret_cast<T *>(H->F64.get());
-    }
-    if (H->IA.n < isize && !H->IA.reset(c, isize)) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        KRR_TRY(grow_arena(c, H->IA, H->arena_i, io));
+        H->arena_f = fo;
+        H->arena_i = io;
+        return KRR_OK;
+    };
+    H->arena_f = H->arena_i = 0;
     if (!H->ddesc.get() && !H->ddesc.reset(c, H->desc.size())) return fail(KRR_ERR_OOM, "hss_compress: out of memory");
     DBuf<int> dranks(c, H->desc.size());
     DBuf<float> derr(c, 2 * H->desc.size());
@@ -1066,10 +1079,11 @@ int id_sweep(HssImpl *H, bool &need_more) {
                 N.m = N.ka + N.kb;
             }
         }
-        KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), H->desc.size() * sizeof(NodeDesc),
-                                 cudaMemcpyHostToDevice, c->stream));
         int nn = int(lv.size());
         if (nn == 0) continue;
+        KRR_TRY(arena(h));
+        KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), H->desc.size() * sizeof(NodeDesc),
+                                 cudaMemcpyHostToDevice, c->stream));
         lvdesc.resize(nn);
         for (int a = 0; a < nn; ++a) lvdesc[a] = H->desc[lv[a]];
         DBuf<NodeDesc> dl(c, nn);
@@ -1128,7 +1142,7 @@ int id_sweep(HssImpl *H, bool &need_more) {
         }
         // The Gram form needs eps^2 well above the rounding of the Gram
         // matrix; tighter tolerances take the QR of the samples.
-        const bool gram = H->opt.eps_c >= (H->mixed() ? 1e-2 : 1e-5);
+        const bool gram = H->use_gram();
         if (mmax == 0) {
             // every node of the level is empty (its children have rank 0)
             KRR_CUDA(cudaMemsetAsync(dranks.get(), 0, nn * sizeof(int), c->stream));
@@ -1266,7 +1280,9 @@ int id_sweep(HssImpl *H, bool &need_more) {
             // markedly better than fresh ones
             if (e_test > kTestFactor * std::max(e_in, H->opt.eps_c)) need_more = true;
         }
-        if (need_more) return KRR_OK;
+        // a level that asks for more samples ends the sweep, unless this is
+        // the last round allowed (ranks then stay at the budget)
+        if (need_more && !keep_going) return KRR_OK;
         {
             // R-hat += T R_loc(redundant)
             GemmBatch<T> gb;
@@ -1303,7 +1319,12 @@ int compress(HssImpl *H) {
         ts += now_ms() - s0;
         ++H->rounds;
         bool more = false;
-        KRR_TRY(id_sweep<T>(H, more));
+        const bool last = H->r >= H->opt.r_max && (H->opt.flags & KRR_TRUNCATE_AT_RMAX);
+        KRR_TRY(id_sweep<T>(H, more, last));
+        if (last) {
+            H->truncated = more;
+            break;
+        }
         if (!more) break;
         if (H->r >= H->opt.r_max) return fail(KRR_ERR_RANK_BUDGET, "hss_compress: ranks not revealed within r_max");
         c0 = H->r;
@@ -1766,6 +1787,8 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
             rmax = 0;
             for (int q = 0; q < nrhs; ++q) {
                 beta[q] = std::sqrt(hn[2 * q]);
+                // a NaN would compare false against tol and pass for convergence
+                if (!std::isfinite(beta[q])) return fail(KRR_ERR_NO_CONVERGENCE, "hss_solve: non-finite residual");
                 rmax = std::max(rmax, beta[q] / ynrm[q]);
             }
             if (rmax <= tol || total_it >= max_refine) break;
@@ -1812,6 +1835,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                     double *Hq = Hm.data() + size_t(q) * (mres + 1) * mres;
                     double *col = Hq + size_t(j) * (mres + 1);
                     for (int i = 0; i <= j; ++i) col[i] = hd[size_t(i) * nrhs + q];
+                    if (!std::isfinite(wn[q])) return fail(KRR_ERR_NO_CONVERGENCE, "hss_solve: non-finite Krylov vector");
                     const double hn1 = std::sqrt(std::max(wn[q], 0.0));
                     col[j + 1] = hn1;
                     inv2[q] = hn1 > 0 ? 1.0 / hn1 : 0.0;
@@ -2304,6 +2328,8 @@ int hss_stats(const krr_hss *H, krr_hss_stats *st) {
     st->t_compress_ms = h.t_compress;
     st->t_factor_ms = h.t_factor;
     st->t_solve_ms = h.t_solve;
+    st->truncated = h.truncated ? 1 : 0;
+    st->pad = 0;
     return KRR_OK;
 }
 

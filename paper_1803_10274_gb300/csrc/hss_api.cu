@@ -17,7 +17,7 @@ void krr_default_options(krr_options *o) {
     o->r_max = 2048;
     o->seed = 1;
     o->precision = KRR_MIXED;
-    o->reserved = 0;
+    o->flags = 0;
 }
 
 }  // extern "C"

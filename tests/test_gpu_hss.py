@@ -161,6 +161,27 @@ def test_mixed_full_size(K, ctx):
     H.close()
 
 
+def test_truncate_at_budget_still_preconditions(K, ctx):
+    """KRR_TRUNCATE_AT_RMAX: with a sample budget far below the ranks the
+    compression keeps truncated decompositions instead of failing, and the
+    refined solve still reaches its tolerance (oracle residual)."""
+    X, y, *_ = synth.mixture(4096, 8, 16, 0.7, 2)
+    Z = prep.standardize(X)[0].astype(np.float32)
+    o = K.default_options(h=1.0, lambda_=4.0, eps_c=0.05, leaf=128, r0=64, r_max=128, precision=K.KRR_MIXED)
+    with pytest.raises(K.KRRError) as e:
+        K.hss_compress(ctx, torch.from_numpy(Z).cuda(), o)
+    assert e.value.code == 5
+    o.flags = K.KRR_TRUNCATE_AT_RMAX
+    H = K.hss_compress(ctx, torch.from_numpy(Z).cuda(), o)
+    st = H.stats()
+    assert st["truncated"] == 1 and st["samples"] == 128
+    H.factor()
+    a, res = H.solve(torch.from_numpy(y[:, None].copy()).cuda(), tol=1e-4, max_refine=600)
+    rho = solve.residual(Z.astype(np.float64), 1.0, 4.0, a.cpu().numpy(), y[:, None])
+    assert res <= 1e-4 and rho.max() <= 2e-4
+    H.close()
+
+
 def test_argument_and_budget_errors(K, ctx):
     X = synth.mixture(3000, 8, 8, 0.7, 1)[0]
     Xd = torch.from_numpy(((X - X.mean(0)) / X.std(0)).astype(np.float32)).cuda()
