@@ -267,7 +267,8 @@ def run_ours(args):
 
     # ---- held-out loss gradient (COVTYPE-shaped) and the million-point product
     extras = {} if args.no_extras else {"gradient": bench_gradient(K, ctx, l2),
-                                        "million_point_product": bench_million(K, ctx)}
+                                        "million_point_product": bench_million(K, ctx),
+                                        "batch": bench_batch(K, ctx, l2)}
 
     # ---- FP64 plain path, same step (one run: it is slow)
     plain = None
@@ -368,6 +369,90 @@ def bench_gradient(K, ctx, l2, reps=3):
             "seconds_loss_only": statistics.median(x[0] for x in tl),
             "loss": r["loss"], "dL_dh": r["dh"], "dL_dlambda": r["dlambda"],
             "gmres_iters_both_solves": st["refine_steps"], "max_rank": st["max_rank"]}
+
+
+BATCH_WL = dict(nprob=256, n_lo=512, n_hi=8192, dims=(8, 32, 128), hs=(0.5, 1.0, 2.0, 4.0), nrhs=16, lam=1.0,
+                eps_c=0.05, eps_abs=1e-2, r_max=1024, tol=1e-4, max_refine=600, seed=5)
+
+
+def batch_groups(W):
+    """The batched workload's data: one group per feature dimension, each a
+    list of (X, Y, h) systems; the 256 problems' sizes and dimensions are
+    drawn from the workload seed."""
+    import synth
+    from oracle import prep
+    rng = np.random.default_rng(W["seed"])
+    sizes = rng.integers(W["n_lo"], W["n_hi"] + 1, size=W["nprob"])
+    dims = rng.choice(W["dims"], size=W["nprob"])
+    groups = {}
+    for d in W["dims"]:
+        systems = []
+        for p in np.nonzero(dims == d)[0]:
+            X, y, *_ = synth.mixture(int(sizes[p]), int(d), 4, 0.7, 1000 + int(p))
+            Z = prep.standardize(X)[0].astype(np.float32)
+            Y = np.concatenate([y[:, None], rng.standard_normal((len(y), W["nrhs"] - 1))], 1)
+            for h in W["hs"]:
+                systems.append((Z, Y, h))
+        groups[int(d)] = systems
+    return groups
+
+
+def bench_batch(K, ctx, l2, reps=2):
+    """Many independent problems: 256 seeded mixture data sets with
+    n ~ U[512, 8192] and d drawn from {8, 32, 128}, each at four widths
+    h in {0.5, 1, 2, 4}, 16 right-hand sides, lambda = 1.  One batched
+    handle per (d, h) group: all its problems in one block-diagonal HSS
+    (compress + factor) and one GMRES to 1e-4 over the group.  A step is
+    every group the mixed path supports (d <= 82); groups whose GMRES stops
+    above the tolerance are reported with the residual they reached."""
+    import torch
+    W = BATCH_WL
+    groups, skipped = [], []
+    for d, systems in batch_groups(W).items():
+        if d > 82:
+            skipped.append({"d": d, "systems": len(systems),
+                            "reason": "feature dimension above the mixed path's limit (d <= 82)"})
+            continue
+        for h in W["hs"]:
+            sel = [(x, y) for x, y, hh in systems if hh == h]
+            off = np.concatenate([[0], np.cumsum([len(x) for x, _ in sel])]).astype(np.int64)
+            groups.append((d, h, torch.from_numpy(np.concatenate([x for x, _ in sel])).cuda(),
+                           torch.from_numpy(np.ascontiguousarray(np.concatenate([y for _, y in sel]))).cuda(), off))
+
+    def step():
+        out = []
+        for d, h, X, Y, off in groups:
+            o = K.default_options(lambda_=W["lam"], eps_c=W["eps_c"], eps_abs=W["eps_abs"], r_max=W["r_max"],
+                                  flags=K.KRR_TRUNCATE_AT_RMAX | K.KRR_LAMBDA_TOL, leaf=128, seed=W["seed"])
+            H = K.hss_compress_batched(ctx, X, off, [h] * (len(off) - 1), o)
+            H.factor()
+            a, res = H.solve(Y, tol=W["tol"], max_refine=W["max_refine"], raise_on_no_convergence=False)
+            st = H.stats()
+            H.close()
+            out.append({"d": d, "h": h, "problems": len(off) - 1, "rows": int(off[-1]), "resid": res,
+                        "converged": bool(0 <= res <= W["tol"]), "max_rank": st["max_rank"],
+                        "samples": st["samples"], "truncated": st["truncated"], "gmres_iters": st["refine_steps"]})
+        return out
+
+    step()
+    ts = []
+    for _ in range(reps):
+        _flush_l2(l2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        info = step()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(ts)
+    nsys = sum(g["problems"] for g in info)
+    return {"workload": "256 mixture problems, n ~ U[512, 8192], d in {8, 32, 128}, 4 widths each, 16 RHS, "
+                        "lambda 1; one batched handle per (d, h): HSS eps_c 0.05 relative to min(block, lambda), pivot "
+                        "floor 1e-2, <= 1024 samples (truncated beyond); GMRES to 1e-4 over each group, at most 600 iterations",
+            "seconds": t, "systems_per_second": nsys / t,
+            "systems_converged": sum(g["problems"] for g in info if g["converged"]), "systems": nsys,
+            "groups": info, "skipped": skipped}
 
 
 def bench_million(K, ctx, n=1 << 20, r=256, reps=2):
@@ -473,11 +558,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the gradient workload and the million-point product")
+    ap.add_argument("--batch-only", action="store_true", help="only run the batched-problems workload")
     ap.add_argument("--sample-only", nargs=2, type=int, metavar=("N", "R"),
                     help="only run the fused sampling product at n=N, r=R (5 launches; for profilers)")
     args = ap.parse_args()
     if args.sample_only:
         sample_only(*args.sample_only)
+    elif args.batch_only:
+        import torch
+        import paper_1803_10274_gb300 as K
+        torch.cuda.set_device(0)
+        ctx = K.Context()
+        l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        print(json.dumps(bench_batch(K, ctx, l2)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

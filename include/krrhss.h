@@ -207,7 +207,7 @@ typedef struct {
     int32_t r_max;     /* cap on random columns                             */
     uint64_t seed;     /* seeds clustering and the random block             */
     int32_t precision; /* krr_precision                                     */
-    int32_t flags;     /* KRR_TRUNCATE_AT_RMAX, or 0                        */
+    int32_t flags;     /* KRR_TRUNCATE_AT_RMAX | KRR_LAMBDA_TOL, or 0       */
 } krr_options;
 
 /* krr_options.flags: when the ranks are not revealed within r_max samples,
@@ -215,6 +215,14 @@ typedef struct {
  * at most; a coarser approximation, still a usable preconditioner for the
  * refined solve) instead of failing with KRR_ERR_RANK_BUDGET. */
 #define KRR_TRUNCATE_AT_RMAX 1
+/* krr_options.flags: measure the decompositions' accuracy against lambda as
+ * well: a decomposition stops only when its next pivot is below
+ * eps_c * min(|R_11|, lambda sqrt(s)), s the sample columns it uses (a pivot
+ * is about sigma sqrt(s) for a singular value sigma of the block).  For
+ * smooth kernels, whose blocks are large next to lambda, this keeps the
+ * approximation error of K + lambda I below about eps_c lambda per block, so
+ * the factorization stays a good preconditioner. */
+#define KRR_LAMBDA_TOL 2
 
 /* Fill opts with defaults: eps_c 0.03, eps_abs 0, leaf 128, r0 64, p 10,
  * r_max 2048, seed 1, KRR_MIXED, flags 0; h and lambda set to 1. */

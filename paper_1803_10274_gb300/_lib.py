@@ -15,10 +15,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkrrhss.so")
 
 KRR_OK = 0
+KRR_ERR_NO_CONVERGENCE = 9
 STATUS = {0: "KRR_OK", 1: "KRR_ERR_INVALID_ARG", 2: "KRR_ERR_NONFINITE_INPUT", 3: "KRR_ERR_OOM",
           4: "KRR_ERR_SINGULAR", 5: "KRR_ERR_RANK_BUDGET", 6: "KRR_ERR_TIMEOUT", 7: "KRR_ERR_CUDA",
           8: "KRR_ERR_NOT_IMPLEMENTED", 9: "KRR_ERR_NO_CONVERGENCE"}
 KRR_TRUNCATE_AT_RMAX = 1
+KRR_LAMBDA_TOL = 2
 KRR_MIXED, KRR_FP64 = 0, 1
 
 P = ctypes.c_void_p

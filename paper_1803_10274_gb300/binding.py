@@ -11,9 +11,9 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import KRR_FP64, KRR_MIXED, KRR_TRUNCATE_AT_RMAX, KRRError, check, lib
+from ._lib import KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_TRUNCATE_AT_RMAX, KRRError, check, lib
 
-__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_TRUNCATE_AT_RMAX", "krr_standardize", "krr_cluster", "krr_sample",
+__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "krr_standardize", "krr_cluster", "krr_sample",
            "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "HSS", "hss_compress", "default_options",
            "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]
 
@@ -199,14 +199,18 @@ class HSS:
     def update_lambda(self, lam):
         check(lib().hss_update_lambda(self.h, lam))
 
-    def solve(self, y, tol=0.0, max_refine=100):
-        """alpha (n x nrhs float64, original order) and the final residual."""
+    def solve(self, y, tol=0.0, max_refine=100, raise_on_no_convergence=True):
+        """alpha (n x nrhs float64, original order) and the final residual.
+        With raise_on_no_convergence=False a solve that stops above tol
+        returns its last iterate and residual instead of raising."""
         _need(y, torch.float64, "y")
         y = y.contiguous()
         alpha = torch.empty(y.shape, dtype=torch.float64, device=y.device)
         res = ctypes.c_double(-1.0)
-        check(lib().hss_solve(self.h, _ptr(y), y.shape[1], y.shape[1], _ptr(alpha), alpha.shape[1], tol,
-                              max_refine, ctypes.byref(res)))
+        code = lib().hss_solve(self.h, _ptr(y), y.shape[1], y.shape[1], _ptr(alpha), alpha.shape[1], tol,
+                               max_refine, ctypes.byref(res))
+        if code != _lib.KRR_ERR_NO_CONVERGENCE or raise_on_no_convergence:
+            check(code)
         return alpha, res.value
 
     def predict(self, Xt, alpha):

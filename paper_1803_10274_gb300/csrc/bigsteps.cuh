@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) qr_init_kernel(const QrItem *items, QrSta
 // One CTA per item: pivot choice, rank test, row swap, Householder vector.
 template <class T>
 __global__ void __launch_bounds__(256) qr_pivot_kernel(const QrItem *items, QrState *state, T *F, int32_t *I, int j,
-                                                       double eps, double eps_abs) {
+                                                       double eps, double eps_abs, double r11_cap) {
     const QrItem it = items[blockIdx.x];
     QrState &S = state[blockIdx.x];
     if (S.done) return;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) qr_pivot_kernel(const QrItem *items, QrSt
         if (norm2[i] > best) { best = norm2[i]; bi = i; }
     cta::argmax_block(best, bi);
     const double nrm = sqrt(double(best));
-    const double r11 = j == 0 ? nrm : S.r11;
+    const double r11 = j == 0 ? (nrm < r11_cap ? nrm : r11_cap) : S.r11;
     if (!(nrm > eps * r11) || !(nrm > eps_abs)) {
         if (threadIdx.x == 0) { S.done = 1; S.k = j; if (j == 0) S.r11 = nrm; }
         return;

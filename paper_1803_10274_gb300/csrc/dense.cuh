@@ -220,13 +220,13 @@ __device__ void id_T(int m, int k, const T *W, int64_t ldw, T *Tout) {
 // (held-out samples for an error estimate).  At step j the pivot is the remaining row with the
 // largest 2-norm of its coordinates [j, r) (norms recomputed after every
 // update; ties to the lowest index); the rank is the number of pivots with
-// norm > eps * (first pivot norm) and > eps_abs.  Rows are physically
+// norm > eps * min(first pivot norm, r11_cap) and > eps_abs.  Rows are physically
 // swapped, piv[a] gives the original position of row a.  On return the
 // first k rows hold R^T (row b, coordinate a = R[a][b]) and T = R11^{-1}
 // R12 (k x (m-k), row-major, ldt = m - k) is written to Tout.
 template <class T>
 __device__ int row_id(int m, int r, int rfull, T *W, int64_t ldw, T eps, T eps_abs, int *piv, T *norm2, T *Tout,
-                       int kmax, T *in_err) {
+                       int kmax, T *in_err, T r11_cap) {
     __shared__ int s_k;
     extern __shared__ unsigned char dyn_smem_raw[];
     T *v = reinterpret_cast<T *>(dyn_smem_raw);  // Householder vector, length r
@@ -256,7 +256,7 @@ __device__ int row_id(int m, int r, int rfull, T *W, int64_t ldw, T eps, T eps_a
             if (norm2[i] > best) { best = norm2[i]; bi = i; }
         argmax_block(best, bi);
         const T nrm = sqrt(best);
-        if (j == 0) r11 = nrm;
+        if (j == 0) r11 = nrm < r11_cap ? nrm : r11_cap;
         if (!(nrm > eps * r11) || !(nrm > eps_abs)) break;
         const int p = bi;
         if (p != j) {

@@ -132,7 +132,8 @@ __global__ void parent_sloc_kernel(const NodeDesc *nd, const NodeDesc *all, int 
 template <class T>
 __global__ void __launch_bounds__(cta::kNT) id_kernel(NodeDesc *nd, const NodeDesc *all, const T *S, const T *R,
                                                       int64_t ldsr, int r, T *F, int32_t *I, T eps, T eps_abs,
-                                                      int kmax, int *ranks, float *test_err, DevStatus *st) {
+                                                      int kmax, int *ranks, float *test_err, DevStatus *st,
+                                                      T r11_cap) {
     NodeDesc &N = nd[blockIdx.x];
     const int m = N.m;
     T *W = F + N.w;
@@ -152,7 +153,8 @@ __global__ void __launch_bounds__(cta::kNT) id_kernel(NodeDesc *nd, const NodeDe
     // the decomposition's error on fresh random directions
     const int rid = r - kHoldOut;
     __shared__ T s_in_err;
-    const int k = cta::row_id<T>(m, rid, r, W, r, eps, eps_abs, piv, F + N.norm, F + N.tmat, kmax, &s_in_err);
+    const int k = cta::row_id<T>(m, rid, r, W, r, eps, eps_abs, piv, F + N.norm, F + N.tmat, kmax, &s_in_err,
+                                 r11_cap);
     const T terr = cta::id_test_error<T>(m, k, W, r, F + N.tmat, rid, r);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(NT) gram_init_kernel(const NodeDesc *nd, T *F,
 // the rank rule or at jmax.
 template <class T, int NT>
 __global__ void __launch_bounds__(NT) gram_panel_kernel(const NodeDesc *nd, T *F, int32_t *I, GramState<T> *st,
-                                                        int j0, int rid, int kmax, T eps, T eps_abs) {
+                                                        int j0, int rid, int kmax, T eps, T eps_abs, T r11_cap) {
     GramState<T> &S = st[blockIdx.x];
     if (S.done) return;
     const NodeDesc &N = nd[blockIdx.x];
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(NT) gram_panel_kernel(const NodeDesc *nd, T *F
             if (d[q] > best) { best = d[q]; bi = q; }
         argmax_nt<T, NT>(best, bi);  // synchronizes
         const T nrm = sqrt(best > T(0) ? best : T(0));
-        if (j == 0) r11 = nrm;
+        if (j == 0) r11 = nrm < r11_cap ? nrm : r11_cap;
         if (!(nrm > eps * r11) || !(nrm > eps_abs)) break;
         const int p = bi;
         const T inv = T(1) / nrm;
@@ -826,6 +828,13 @@ struct HssImpl {
     // IDs from the Gram matrix need eps^2 well above its rounding; tighter
     // tolerances take the QR of the samples
     bool use_gram() const { return opt.eps_c >= (mixed() ? 1e-2 : 1e-5); }
+    // KRR_LAMBDA_TOL: a decomposition stops only below eps_c * min(|R_11|,
+    // lambda sqrt(rid)), i.e. also once the next singular value of the
+    // block (a pivot is about sigma sqrt(rid) in sample units) is below
+    // eps_c lambda; otherwise no cap
+    double r11_cap(int rid) const {
+        return (opt.flags & KRR_LAMBDA_TOL) ? lambda * std::sqrt(double(rid)) : INFINITY;
+    }
     int max_rank = 0, refine_steps = 0;
     bool truncated = false;
     double max_test_err = 0;
@@ -1169,8 +1178,8 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             std::vector<GramState<T>> hs(nn);
             std::vector<char> live(nn, 1);
             for (int j0 = 0; j0 < jmax; j0 += kPanel) {
-                if (wide) { gram_panel_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs)); ::krr::count_launch(); }
-                else { gram_panel_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs)); ::krr::count_launch(); }
+                if (wide) { gram_panel_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid))); ::krr::count_launch(); }
+                else { gram_panel_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid))); ::krr::count_launch(); }
                 KRR_CUDA(cudaGetLastError());
                 KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
                                          c->stream));
@@ -1225,7 +1234,8 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             }
             { id_kernel<T><<<nn, cta::kNT, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, r, F,
                                                               H->IA.get(), T(H->opt.eps_c), T(H->opt.eps_abs), kmax,
-                                                              dranks.get(), derr.get(), c->status); ::krr::count_launch(); }
+                                                              dranks.get(), derr.get(), c->status,
+                                                              T(H->r11_cap(r - kHoldOut))); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
         } else {
             // large nodes: the pivoted QR as batched pivot-step launches
@@ -1246,7 +1256,7 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             std::vector<big::QrState> hs(nn);
             for (int j = 0; j < jmax; ++j) {
                 { big::qr_pivot_kernel<T><<<nn, 256, 0, c->stream>>>(dqi.get(), dqs.get(), F, H->IA.get(), j,
-                                                                     H->opt.eps_c, H->opt.eps_abs); ::krr::count_launch(); }
+                                                                     H->opt.eps_c, H->opt.eps_abs, H->r11_cap(r - kHoldOut)); ::krr::count_launch(); }
                 { big::qr_apply_kernel<T><<<g, 256, 0, c->stream>>>(dqi.get(), dqs.get(), F, j); ::krr::count_launch(); }
                 if ((j & 15) == 15) {  // stop early once every node has found its rank
                     KRR_CUDA(cudaMemcpyAsync(hs.data(), dqs.get(), nn * sizeof(big::QrState), cudaMemcpyDeviceToHost,
@@ -1259,7 +1269,7 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             }
             // nodes still running at jmax stop there
             { big::qr_pivot_kernel<T><<<nn, 256, 0, c->stream>>>(dqi.get(), dqs.get(), F, H->IA.get(), jmax,
-                                                                 H->opt.eps_c, H->opt.eps_abs); ::krr::count_launch(); }
+                                                                 H->opt.eps_c, H->opt.eps_abs, H->r11_cap(r - kHoldOut)); ::krr::count_launch(); }
             { id_post_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), dqs.get(), S, R, H->r_cap,
                                                                 r, F, H->IA.get(), dranks.get(), derr.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());

@@ -182,6 +182,22 @@ def test_truncate_at_budget_still_preconditions(K, ctx):
     H.close()
 
 
+def test_lambda_relative_tolerance(K, ctx):
+    """KRR_LAMBDA_TOL (decompositions measured against lambda as well): the
+    compression and the refined solve work with and without it, and the
+    solve reaches its tolerance (oracle residual)."""
+    X, y, *_ = synth.mixture(4096, 8, 4, 0.7, 21)
+    Z = prep.standardize(X)[0].astype(np.float32)
+    for flags in (0, K.KRR_LAMBDA_TOL):
+        o = K.default_options(h=1.0, lambda_=1.0, eps_c=0.05, leaf=128, precision=K.KRR_MIXED, flags=flags)
+        H = K.hss_compress(ctx, torch.from_numpy(Z).cuda(), o)
+        H.factor()
+        a, res = H.solve(torch.from_numpy(y[:, None].copy()).cuda(), tol=1e-4, max_refine=600)
+        rho = solve.residual(Z.astype(np.float64), 1.0, 1.0, a.cpu().numpy(), y[:, None])
+        assert res <= 1e-4 and rho.max() <= 2e-4
+        H.close()
+
+
 def test_argument_and_budget_errors(K, ctx):
     X = synth.mixture(3000, 8, 8, 0.7, 1)[0]
     Xd = torch.from_numpy(((X - X.mean(0)) / X.std(0)).astype(np.float32)).cuda()
