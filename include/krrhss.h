@@ -149,7 +149,9 @@ int krr_cluster_batched(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
  *   leaf_a, leaf_b  device int32[ma], int32[nb] or both NULL
  * KRR_MIXED: R is rounded to FP16; distances use an FP16 hi/lo split with
  * FP32 accumulation on tcgen05 tensor cores, exp2 on the SFU, K rounded to
- * FP16, K R accumulated in FP32 in tensor memory.  Requires d <= 82,
+ * FP16, K R accumulated in FP32 in tensor memory.  Requires d <= 1024
+ * (rows longer than four 64-element chunks, d > 82, stream through shared
+ * memory chunk by chunk instead of staying resident),
  * 1 <= r and max |x|^2 / h^2 small enough for FP16 (else INVALID_ARG).
  * ------------------------------------------------------------------- */
 int krr_sample(krr_ctx *ctx, const float *Xa, int64_t ma, const float *Xb,

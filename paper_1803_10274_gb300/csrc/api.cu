@@ -57,12 +57,20 @@ int sample_mixed_prepared(Ctx *c, const __half *XA, int64_t ma, const __half *XB
     KRR_CUDA(cudaMemset2DAsync(S, size_t(lds) * 4, 0, size_t(r_total) * 4, size_t(ma), c->stream));
     if (nb == 0) return KRR_OK;
     const int nchunk = aug_chunks(d);
-    const int rmax = nchunk == 1 ? 256 : nchunk <= 3 ? 128 : 64;
+    // resident rows (up to four chunks): launches of up to 256 / 128 / 64
+    // columns as tensor memory and shared memory allow; wider rows stream
+    // chunk by chunk in launches of up to 128 columns
+    const bool wide = nchunk > 4;
+    const int rmax = wide ? 128 : nchunk == 1 ? 256 : nchunk <= 3 ? 128 : 64;
     for (int col = 0; col < r_total; col += rmax) {
         const int rv = r_total - col < rmax ? r_total - col : rmax;
         const int rpad = int(round_up(rv, 64));
-        KRR_TRY(launch_sample_tc(c, XA, ma, XB, nb, nchunk, aug_kmma(d), RT + int64_t(col) * ldrt, rpad, ldrt, rv,
-                                 leaf_a, leaf_b, S + col, lds, split_k, bd));
+        if (wide)
+            KRR_TRY(launch_sample_tc_wide(c, XA, ma, XB, nb, nchunk, aug_kmma(d), RT + int64_t(col) * ldrt, rpad, ldrt,
+                                          rv, leaf_a, leaf_b, S + col, lds, split_k, bd));
+        else
+            KRR_TRY(launch_sample_tc(c, XA, ma, XB, nb, nchunk, aug_kmma(d), RT + int64_t(col) * ldrt, rpad, ldrt, rv,
+                                     leaf_a, leaf_b, S + col, lds, split_k, bd));
     }
     return KRR_OK;
 }
@@ -141,7 +149,7 @@ int krr_sample(krr_ctx *k, const float *Xa, int64_t ma, const float *Xb, int64_t
     if ((leaf_a == nullptr) != (leaf_b == nullptr))
         return fail(KRR_ERR_INVALID_ARG, "krr_sample: give both leaf arrays or neither");
     if (lambda != 0.0 && ma != nb) return fail(KRR_ERR_INVALID_ARG, "krr_sample: lambda needs Xa == Xb");
-    if (d > kMaxMixedDim) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_sample: mixed path supports d <= 82");
+    if (d > kMaxMixedDim) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_sample: mixed path supports d <= 1024");
     Ctx *c = &k->c;
     const int kpad = aug_kpad(d);
     const int64_t ldrt = round_up(nb > 0 ? nb : 1, 8);

@@ -38,7 +38,7 @@ namespace krr {
 namespace {
 
 constexpr int kMaxIter = 100;
-constexpr int kMaxD = 64;
+constexpr int kMaxD = 1024;  // feature dimensions the node state holds
 constexpr int kTB = 256;
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {  // b > 0
@@ -405,7 +405,7 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
             std::vector<int32_t> &tp, std::vector<int32_t> &tv, const std::vector<int64_t> *segments) {
     tb.clear(); te.clear(); tl.clear(); tr.clear(); tp.clear(); tv.clear();
     if (n == 0) return KRR_OK;
-    if (d > kMaxD) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_cluster: d > 64");
+    if (d > kMaxD) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_cluster: d > 1024");
     cudaStream_t st = c->stream;
     // segments (one, the whole set, unless given)
     std::vector<int64_t> seg = segments ? *segments : std::vector<int64_t>{0, n};

@@ -2224,7 +2224,7 @@ int hss_compress(krr_ctx *k, const float *X, int64_t n, int32_t d, const krr_opt
         o->p < 0 || o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64))
         return fail(KRR_ERR_INVALID_ARG, "hss_compress: bad options");
     if (o->precision == KRR_MIXED && d > kMaxMixedDim)
-        return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress: mixed path supports d <= 82");
+        return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress: mixed path supports d <= 1024");
     if (n > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "hss_compress: n too large");
     krr_hss *H = new (std::nothrow) krr_hss();
     if (!H) return fail(KRR_ERR_OOM, "hss_compress: host allocation failed");
@@ -2246,7 +2246,7 @@ int hss_compress_batched(krr_ctx *k, const float *X, int64_t n, int32_t d, int32
         o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64))
         return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: bad options");
     if (o->precision == KRR_MIXED && d > kMaxMixedDim)
-        return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress_batched: mixed path supports d <= 82");
+        return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress_batched: mixed path supports d <= 1024");
     if (n > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: n too large");
     std::vector<int64_t> off(offsets, offsets + nprob + 1);
     std::vector<double> hw(h, h + nprob);

@@ -25,7 +25,8 @@ inline int aug_used(int d) { return 3 * d + 6; }
 inline int aug_kmma(int d) { return int(cdiv(aug_used(d), 16)); }
 inline int aug_chunks(int d) { return int(cdiv(aug_used(d), 64)); }
 inline int aug_kpad(int d) { return 64 * aug_chunks(d); }
-constexpr int kMaxMixedDim = 82;  // 3d + 6 <= 256: at most four 64-element chunks
+constexpr int kMaxResidentDim = 82;  // 3d + 6 <= 256: rows resident in shared memory (four chunks)
+constexpr int kMaxMixedDim = 1024;   // above kMaxResidentDim the rows stream chunk by chunk
 
 // A block-diagonal product: many independent problems whose rows are
 // contiguous ranges of A and of B; a pair (i, j) is kept only when
@@ -48,6 +49,9 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
                      const int32_t *leaf_b, float *S, int64_t lds, bool split_k = false,
                      const BlockDiag *bd = nullptr);
+int launch_sample_tc_wide(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
+                          const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
+                          const int32_t *leaf_b, float *S, int64_t lds, bool split_k, const BlockDiag *bd);
 int launch_sample_f64(Ctx *c, const double *Xa, int64_t ma, const double *Xb, int64_t nb, int d, double h,
                       const double *R, int r, int64_t ldr, const int32_t *leaf_a, const int32_t *leaf_b, double *S,
                       int64_t lds, const BlockDiag *bd = nullptr);

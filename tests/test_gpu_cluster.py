@@ -35,11 +35,18 @@ def _check(K, ctx, X32, leaf, seed):
 @pytest.mark.parametrize("n,d,comp,leaf,seed", [(1000, 8, 4, 64, 1),       # the small plain workload
                                                 (5000, 3, 7, 16, 5),
                                                 (3333, 54, 7, 100, 9),
-                                                (20000, 8, 16, 128, 2)])
+                                                (20000, 8, 16, 128, 2),
+                                                (1500, 128, 5, 64, 3)])
 def test_mixture_bit_exact(K, ctx, n, d, comp, leaf, seed):
     X, *_ = synth.mixture(n, d, comp, 0.7, seed)
     Z, *_ = prep.standardize(X)
     _check(K, ctx, Z.astype(np.float32), leaf, seed)
+
+
+def test_image_like_d784_bit_exact(K, ctx):
+    """MNIST-shaped rows: d = 784, most coordinates exactly zero."""
+    X = synth.image_like(1000, 3)[0].astype(np.float32)
+    _check(K, ctx, X, 128, 4)
 
 
 def test_full_size_bit_exact(K, ctx):

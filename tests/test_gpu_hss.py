@@ -161,6 +161,25 @@ def test_mixed_full_size(K, ctx):
     H.close()
 
 
+def test_image_like_d784_mixed(K, ctx):
+    """MNIST-shaped workload at n = 4096 (d = 784 raw pixels in [0, 1],
+    one-vs-all class 5, h = 4, lambda = 10, leaf 256, eps = 1e-3): residual
+    <= 10 eps against the oracle's operator and accuracy within 0.5 points
+    of the dense solve."""
+    X, y, Xt, yt = synth.image_like(4096, 3, m_test=500)
+    X32, Xt32 = X.astype(np.float32), Xt.astype(np.float32)
+    eps = 1e-3
+    H, A, res = _fit(K, ctx, X32, y[:, None], 4.0, 10.0, 0.05, 256, K.KRR_MIXED, eps)
+    Xo = X32.astype(np.float64)
+    rho = solve.residual(Xo, 4.0, 10.0, A, y[:, None])
+    assert rho.max() <= 10 * eps
+    dec = H.predict(torch.from_numpy(Xt32).cuda(), torch.from_numpy(A.copy()).cuda()).cpu().numpy()[:, 0]
+    wd = solve.krr_dense(Xo, y, 4.0, 10.0)
+    acc_d = solve.accuracy(solve.sign_pm1(solve.predict(Xt32.astype(np.float64), Xo, wd, 4.0)), yt)
+    assert abs(solve.accuracy(solve.sign_pm1(dec), yt) - acc_d) <= 0.005
+    H.close()
+
+
 def test_truncate_at_budget_still_preconditions(K, ctx):
     """KRR_TRUNCATE_AT_RMAX: with a sample budget far below the ranks the
     compression keeps truncated decompositions instead of failing, and the

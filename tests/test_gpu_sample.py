@@ -78,7 +78,10 @@ def test_mixed_masked_and_lambda(K, ctx):
 @pytest.mark.parametrize("n,d,r,masked", [(4096, 40, 128, True),    # two chunks, two stages
                                            (4096, 54, 64, True),     # three chunks, two row-tile buffers
                                            (4096, 54, 128, False),   # three chunks, one row-tile buffer
-                                           (3000, 80, 64, True)])    # four chunks
+                                           (3000, 80, 64, True),     # four chunks
+                                           (3000, 100, 64, False),   # five chunks: rows streamed
+                                           (4096, 128, 128, True),   # seven chunks, streamed
+                                           (1500, 200, 200, True)])  # ten chunks, two column launches
 def test_mixed_wide_rows_many_tiles_per_cta(K, ctx, n, d, r, masked):
     """Every CTA walks several tiles, so the stage / distance-buffer rings
     wrap; wide feature rows leave room for only two stages."""
@@ -107,6 +110,21 @@ def test_mixed_full_size_sampled_rows(K, ctx):
     ctx.sync()
     rows = np.concatenate([[0, 1, 127, 128, n - 1], np.random.default_rng(0).choice(n, 187, replace=False)])
     ref, ref_abs = kernel.kernel_product(X, X, h, R, rows=rows, want_abs=True)
+    err = np.abs(S.cpu().numpy()[rows] - ref)
+    assert np.all(err <= _mixed_tol(ref_abs, R))
+
+
+def test_mixed_image_like_d784(K, ctx):
+    """MNIST-shaped rows (d = 784, about 80 % exact zeros, values in [0, 1],
+    h = 4): 37 streamed feature chunks, masked by leaves."""
+    n, r, h = 2048, 64, 4.0
+    X = synth.image_like(n, 3)[0].astype(np.float32)
+    R = synth.gaussian_block(n, r, 9).astype(np.float32)
+    leaf = (np.arange(n) // 200).astype(np.int32)
+    S = K.krr_sample(ctx, _cuda(X), _cuda(X), h, 0.0, _cuda(R), _cuda(leaf), _cuda(leaf))
+    ctx.sync()
+    rows = np.concatenate([np.arange(0, 130), np.arange(n - 130, n)])
+    ref, ref_abs = kernel.kernel_product(X, X, h, R, leaf, leaf, rows=rows, want_abs=True)
     err = np.abs(S.cpu().numpy()[rows] - ref)
     assert np.all(err <= _mixed_tol(ref_abs, R))
 
