@@ -190,17 +190,25 @@ __global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const 
 }
 
 // Assign each point of a still-running node to its nearer centre and
-// accumulate the new groups' sums and counts.
+// accumulate the new groups' sums and counts.  When a block's points all
+// belong to one node, the sums are gathered per coordinate in shared
+// memory (int64 atomics, exact and order-free) and added to the node once
+// per coordinate; dynamic shared memory: 2 d int64.
 __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t *node_of, NodeState *ns,
                               int8_t *label) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    extern __shared__ unsigned long long s_sum[];  // [2][d]
     __shared__ int s_uniform;
     __shared__ int32_t s_node;
+    __shared__ int8_t s_lab[kTB];
+    __shared__ int s_cnt1;
+    const int64_t i0 = int64_t(blockIdx.x) * blockDim.x;
+    const int64_t i = i0 + threadIdx.x;
     const int32_t v = i < n ? node_of[i] : -1;
     if (threadIdx.x == 0) {
-        const int64_t last = min(int64_t(blockIdx.x) * blockDim.x + blockDim.x - 1, n - 1);
+        const int64_t last = min(i0 + blockDim.x - 1, n - 1);
         s_node = v;
         s_uniform = (v >= 0 && node_of[last] == v) ? 1 : 0;
+        s_cnt1 = 0;
     }
     __syncthreads();
     const bool uniform = s_uniform != 0;
@@ -220,33 +228,24 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
         label[i] = int8_t(lab);
     }
     if (uniform) {
-        // all points of this block belong to one node: reduce, then one atomic per value
-        if (ns[s_node].done) return;
-        __shared__ long long red[kTB / 32];
-        for (int k = -1; k < 2 * d; ++k) {
-            long long val;
-            if (k < 0)
-                val = lab;
-            else if (k < d)
-                val = (active && lab == 0) ? q[i * d + k] : 0;
-            else
-                val = (active && lab == 1) ? q[i * d + (k - d)] : 0;
-            for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                long long t = 0;
-                for (int w = 0; w < kTB / 32; ++w) t += red[w];
-                NodeState &S = ns[s_node];
-                if (k < 0)
-                    atomicAdd(&S.cnt1, (unsigned long long)t);
-                else if (k < d)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&S.sum0[k]), (unsigned long long)t);
-                else
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&S.sum1[k - d]), (unsigned long long)t);
-            }
-            __syncthreads();
+        if (ns[s_node].done) return;  // the whole block agrees: no thread reaches a barrier below
+        s_lab[threadIdx.x] = int8_t(active ? lab : -1);
+        for (int k = threadIdx.x; k < 2 * d; k += blockDim.x) s_sum[k] = 0ull;
+        if (active && lab == 1) atomicAdd(&s_cnt1, 1);
+        __syncthreads();
+        const int np = int(min(int64_t(blockDim.x), n - i0));
+        for (int e = threadIdx.x; e < np * d; e += blockDim.x) {
+            const int pnt = e / d, k = e - pnt * d;
+            const int lb = s_lab[pnt];
+            if (lb >= 0) atomicAdd(&s_sum[lb * d + k], (unsigned long long)q[(i0 + pnt) * d + k]);
         }
+        __syncthreads();
+        NodeState &S = ns[s_node];
+        for (int k = threadIdx.x; k < d; k += blockDim.x) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&S.sum0[k]), s_sum[k]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&S.sum1[k]), s_sum[d + k]);
+        }
+        if (threadIdx.x == 0) atomicAdd(&S.cnt1, (unsigned long long)s_cnt1);
     } else if (active) {
         NodeState &S = ns[v];
         if (lab) atomicAdd(&S.cnt1, 1ull);
@@ -512,7 +511,7 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         KRR_CUDA(cudaGetLastError());
         for (int iter = 0; iter <= kMaxIter; ++iter) {
             KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
-            { assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(qc, d, n, node_of.get(), dns.get(), label.get()); ::krr::count_launch(); }
+            { assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get()); ::krr::count_launch(); }
             { update_kernel<<<unsigned(cdiv(nn, 128)), 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             int hrun = 0;
