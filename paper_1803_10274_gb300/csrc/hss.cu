@@ -199,16 +199,16 @@ __global__ void __launch_bounds__(cta::kNT) id_prep_kernel(const NodeDesc *nd, c
         for (int a = threadIdx.x; a < m; a += blockDim.x) I[N.rows + a] = N.leaf_begin + a;
 }
 
-// Row ID from the Gram matrix (one CTA of NT threads per node).  With
-// G = S S^T over the sample columns that enter the decomposition (rows of
-// S_loc, G in F + drr), a left-looking Cholesky of G with diagonal
-// pivoting picks at each step the row with the largest remaining squared
-// norm, exactly the row a column-pivoted QR of S^T would pick, and its
-// factor L is R^T of that QR (P G P^T = L L^T = R^T R).  So the rank rule
-// (|R_jj| > eps |R_11| and > eps_abs), T = R11^{-1} R12 and the in-sample
-// error sqrt(remaining diagonal / trace G) are those of the QR, from
-// O(m^2) data instead of O(m r).  L (position x step) goes to the w
-// workspace with row stride r, the remaining diagonal to norm.
+// Row ID from the Gram matrix.  With G = S S^T over the sample columns
+// that enter the decomposition (rows of S_loc; G in the node's drr slot), a
+// Cholesky factorization of G with diagonal pivoting picks at each step the
+// row with the largest remaining squared norm, exactly the row a
+// column-pivoted QR of S^T would pick, and its factor L is R^T of that QR
+// (P G P^T = L L^T = R^T R).  So the rank rule (|R_jj| > eps |R_11| and
+// > eps_abs), T = R11^{-1} R12 and the in-sample error
+// sqrt(remaining diagonal / trace G) are those of the QR, from O(m^2) data
+// instead of O(m r).  The kernels below run it blocked; these are their
+// CTA-wide reductions for NT threads.
 template <class T, int NT>
 __device__ void argmax_nt(T &val, int &idx) {
     __shared__ T sv[NT / 32];
