@@ -10,8 +10,11 @@
 //     of W), stopped at the numerical rank: the row interpolative
 //     decomposition of the node samples.
 #pragma once
+#include <algorithm>
+#include <vector>
 #include "common.cuh"
 #include "dense.cuh"
+#include "grouped.cuh"
 
 namespace krr {
 namespace big {
@@ -112,6 +115,149 @@ int gj_inverse_batched(Ctx *c, const std::vector<InvItem> &items, T *F, int32_t 
     for (int j = 0; j < nmax; ++j) {
         { gj_pivot_kernel<T><<<ni, 256, 0, c->stream>>>(d.get(), F, I, j, c->status); ::krr::count_launch(); }
         { gj_elim_kernel<T><<<eg, 256, 0, c->stream>>>(d.get(), F, j); ::krr::count_launch(); }
+    }
+    { gj_unswap_kernel<T><<<ni, 256, 0, c->stream>>>(d.get(), F, I); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
+// ------------------------------------------- blocked Gauss-Jordan inverse
+// The same in-place elimination, kGjPanel pivots at a time.  Within a panel
+// (one CTA per matrix) rows are interchanged over their full width but the
+// eliminations touch only the panel's columns; those columns then hold the
+// composite transform M of the panel's steps (in-place Gauss-Jordan leaves
+// the transform's columns where the eliminated columns were).  Every other
+// column c is then updated at once: A(:, c) <- M A(:, c), i.e. with the
+// panel rows J, A(J, c) copied out and zeroed, A(:, c) += A(:, J-columns)
+// A_old(J, c) -- one grouped GEMM per panel over all matrices.
+constexpr int kGjPanel = 32;
+
+template <class T>
+__global__ void __launch_bounds__(1024) gjb_panel_kernel(const InvItem *items, T *F, int32_t *I, int j0,
+                                                        DevStatus *st) {
+    const InvItem it = items[blockIdx.x];
+    const int n = it.n;
+    if (j0 >= n) return;
+    T *A = F + it.off;
+    const int jend = min(j0 + kGjPanel, n);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __shared__ T sv[32];
+    __shared__ int si[32];
+    for (int j = j0; j < jend; ++j) {
+        // pivot: largest |A(i, j)| over i >= j, ties to the lowest row
+        T best = T(-1);
+        int bi = 0x7fffffff;
+        for (int i = j + threadIdx.x; i < n; i += 1024) {
+            const T v = cta::tabs(A[int64_t(i) * n + j]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (l == 0) { sv[w] = best; si[w] = bi; }
+        __syncthreads();
+        if (w == 0) {
+            best = sv[l];
+            bi = si[l];
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (l == 0) { sv[0] = best; si[0] = bi; }
+        }
+        __syncthreads();
+        const int p = si[0];
+        __syncthreads();
+        if (p != j)
+            for (int c = threadIdx.x; c < n; c += 1024) {
+                const T t = A[int64_t(j) * n + c];
+                A[int64_t(j) * n + c] = A[int64_t(p) * n + c];
+                A[int64_t(p) * n + c] = t;
+            }
+        if (threadIdx.x == 0) I[it.ipiv + j] = p;
+        __syncthreads();
+        const T piv = A[int64_t(j) * n + j];
+        if (piv == T(0)) {
+            if (threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 203);
+            return;  // every thread read the same pivot
+        }
+        const T inv = T(1) / piv;
+        __syncthreads();
+        for (int c = j0 + threadIdx.x; c < jend; c += 1024) {
+            const T v = c == j ? T(1) : A[int64_t(j) * n + c];
+            A[int64_t(j) * n + c] = v * inv;
+        }
+        __syncthreads();
+        // other rows, panel columns only: lane c - j0 of a warp owns column c
+        const T rj = (j0 + l < jend) ? A[int64_t(j) * n + j0 + l] : T(0);
+        for (int i = w; i < n; i += 32) {
+            if (i == j) continue;
+            T *ri = A + int64_t(i) * n;
+            const T f = ri[j];
+            __syncwarp();
+            if (j0 + l < jend) {
+                const int c = j0 + l;
+                ri[c] = (c == j ? T(0) : ri[c]) - f * rj;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Rows [j0, jend) outside the panel's columns: copied to Tt (kGjPanel rows
+// of n - (jend - j0), in column order with the panel removed) and zeroed.
+template <class T>
+__global__ void gjb_copyout_kernel(const InvItem *items, T *F, T *Tt, int64_t tstride, int j0) {
+    const InvItem it = items[blockIdx.y];
+    const int n = it.n;
+    if (j0 >= n) return;
+    const int jend = min(j0 + kGjPanel, n);
+    const int b = jend - j0, nr = n - b;
+    T *A = F + it.off;
+    T *Tp = Tt + int64_t(blockIdx.y) * tstride;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < int64_t(b) * nr;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int t = int(e / nr), cc = int(e % nr);
+        const int c = cc < j0 ? cc : cc + b;
+        T *a = A + int64_t(j0 + t) * n + c;
+        Tp[e] = *a;
+        *a = T(0);
+    }
+}
+
+template <class T>
+int gj_inverse_blocked(Ctx *c, const std::vector<InvItem> &items, T *F, int32_t *I) {
+    if (items.empty()) return KRR_OK;
+    int nmax = 0;
+    for (const InvItem &it : items) nmax = it.n > nmax ? it.n : nmax;
+    if (nmax == 0) return KRR_OK;
+    const int ni = int(items.size());
+    DBuf<InvItem> d(c, ni);
+    const int64_t tstride = int64_t(kGjPanel) * nmax;
+    DBuf<T> Tt(c, size_t(ni) * tstride);
+    if (!d.get() || !Tt.get()) return fail(KRR_ERR_OOM, "inverse: out of memory");
+    KRR_CUDA(cudaMemcpyAsync(d.get(), items.data(), ni * sizeof(InvItem), cudaMemcpyHostToDevice, c->stream));
+    for (int j0 = 0; j0 < nmax; j0 += kGjPanel) {
+        { gjb_panel_kernel<T><<<ni, 1024, 0, c->stream>>>(d.get(), F, I, j0, c->status); ::krr::count_launch(); }
+        const dim3 cg(unsigned(std::min<int64_t>(cdiv(int64_t(kGjPanel) * nmax, 256), 64)), unsigned(ni));
+        { gjb_copyout_kernel<T><<<cg, 256, 0, c->stream>>>(d.get(), F, Tt.get(), tstride, j0); ::krr::count_launch(); }
+        KRR_CUDA(cudaGetLastError());
+        // every column outside the panel: A(:, c) += A(:, panel) Tt
+        GemmBatch<T> gb;
+        for (int a = 0; a < ni; ++a) {
+            const InvItem &it = items[a];
+            const int n = it.n;
+            if (j0 >= n) continue;
+            const int jend = std::min(j0 + kGjPanel, n), b = jend - j0, nr = n - b;
+            T *A = F + it.off;
+            const T *Tp = Tt.get() + int64_t(a) * tstride;
+            gb.add(n, j0, b, T(1), A + j0, n, false, Tp, nr, false, T(1), A, n);
+            gb.add(n, n - jend, b, T(1), A + j0, n, false, Tp + j0, nr, false, T(1), A + jend, n);
+        }
+        KRR_TRY(gb.launch(c));
     }
     { gj_unswap_kernel<T><<<ni, 256, 0, c->stream>>>(d.get(), F, I); ::krr::count_launch(); }
     KRR_CUDA(cudaGetLastError());
