@@ -40,6 +40,7 @@ namespace {
 constexpr int kMaxIter = 100;
 constexpr int kMaxD = 1024;  // feature dimensions the node state holds
 constexpr int kTB = 256;
+constexpr int kWarpDim = 64;  // from this dimension on, a warp computes one point's distances
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {  // b > 0
     return a >= 0 ? a / b : -((-a + b - 1) / b);
@@ -214,7 +215,30 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
     const bool uniform = s_uniform != 0;
     bool active = v >= 0 && !ns[v].done;
     int lab = 0;
-    if (active) {
+    if (d >= kWarpDim) {
+        // wide rows: the warp computes its 32 points' distances one point
+        // at a time, lanes striding over the coordinates (coalesced)
+        const int lane = threadIdx.x & 31;
+        const int64_t wbase = i0 + (threadIdx.x & ~31);
+        for (int pl = 0; pl < 32; ++pl) {
+            const int64_t ip = wbase + pl;
+            const int32_t vp = ip < n ? node_of[ip] : -1;  // the same for every lane
+            if (vp < 0 || ns[vp].done) continue;
+            const NodeState &S = ns[vp];
+            long long d0 = 0, d1 = 0;
+            for (int k = lane; k < d; k += 32) {
+                const int64_t x = q[ip * d + k];
+                const int64_t a = x - S.c0[k], bb = x - S.c1[k];
+                d0 += a * a;
+                d1 += bb * bb;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+            }
+            if (lane == pl) lab = d0 > d1 ? 1 : 0;
+        }
+    } else if (active) {
         const NodeState &S = ns[v];
         int64_t d0 = 0, d1 = 0;
         for (int k = 0; k < d; ++k) {
@@ -224,7 +248,9 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
             d1 += bb * bb;
         }
         lab = d0 > d1 ? 1 : 0;
-        if (S.first || label[i] != lab) ns[v].changed = 1;
+    }
+    if (active) {
+        if (ns[v].first || label[i] != lab) ns[v].changed = 1;
         label[i] = int8_t(lab);
     }
     if (uniform) {
