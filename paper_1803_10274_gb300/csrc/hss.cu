@@ -1448,6 +1448,7 @@ int build_solve_plan(HssImpl *H, int nrhs) {
         if (!P.dl.reset(c, nn)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
         KRR_CUDA(cudaMemcpyAsync(P.dl.get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
         GemmBatch<T, 16> g1, g2, g3, g4, d1, d2;
+        g1.split_ok = g2.split_ok = g3.split_ok = g4.split_ok = d1.split_ok = d2.split_ok = true;
         if (h == H->H) {
             for (const NodeDesc &N : ld)
                 g1.add(N.m, nrhs, N.m, T(1), F + N.drr, N.m, false, F + N.zvec, nrhs, false, T(0), F + N.xloc, nrhs);
