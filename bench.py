@@ -137,6 +137,18 @@ def _flush_l2(buf):
     buf.add_(1.0)
 
 
+def max_over_ranks(value):
+    """Largest value over the ranks of the initialized process group (the
+    slowest replica sets the step time).  The tensor lives where the
+    backend wants it: on the GPU for NCCL, on the host for gloo."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     import paper_1803_10274_gb300 as K
@@ -201,10 +213,7 @@ def run_ours(args):
     launches = (_lib.lib().krr_launch_count() - l0) // max(args.steps, 1)
     t_step = sum(times) / len(times)
     if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+        t_step = max_over_ranks(t_step)
     a, dec, res, st = last
     acc = float(np.mean(np.where(dec.cpu().numpy()[:, 0] >= 0, 1.0, -1.0) == yt))
 
