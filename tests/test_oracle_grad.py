@@ -51,3 +51,28 @@ def test_grad_zero_at_perfect_fit_direction():
     yt = kernel.kernel_product(Xt, X, 1.0, alpha)[:, 0]
     L, dh, dlam, dX = grad.loss_and_grad(X, Xt, y, yt, 1.0, 1.0)
     assert L < 1e-20 and abs(dh) < 1e-9 and abs(dlam) < 1e-9 and np.abs(dX).max() < 1e-9
+
+
+def test_grad_single_training_point_closed_form():
+    """n = 1: K = [1], alpha = y / (1 + lambda), prediction k' alpha with
+    k'_k = exp(-|x'_k - x|^2 / (2 h^2)); the loss and its three derivatives
+    written out by hand."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((1, 4))
+    Xt = rng.standard_normal((5, 4))
+    y = np.array([0.7])
+    yt = rng.standard_normal(5)
+    h, lam = 1.3, 0.4
+    L, dh, dlam, dX = grad.loss_and_grad(x, Xt, y, yt, h, lam)
+    D = ((Xt - x) ** 2).sum(1)
+    k = np.exp(-D / (2 * h * h))
+    a = y[0] / (1 + lam)
+    g = k * a - yt
+    assert abs(L - 0.5 * (g @ g)) <= 1e-14
+    # dL/dlambda = sum_k g_k k_k d(alpha)/dlambda, d(alpha)/dlambda = -y / (1 + lambda)^2
+    assert abs(dlam - (g @ k) * (-y[0] / (1 + lam) ** 2)) <= 1e-13
+    # dL/dh = sum_k g_k alpha dk_k/dh, dk/dh = k D / h^3
+    assert abs(dh - (g * a * k * D / h ** 3).sum()) <= 1e-13
+    # dL/dx = sum_k g_k alpha dk_k/dx, dk/dx = k (x'_k - x) / h^2
+    ref = ((g * a * k)[:, None] * (Xt - x)).sum(0) / h ** 2
+    assert np.abs(dX[0] - ref).max() <= 1e-13
