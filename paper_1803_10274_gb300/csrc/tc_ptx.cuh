@@ -77,7 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
     return true;
 }
-// mbar_wait for a whole warp: every lane gets the same verdict, so the
+// mbar_wait for a whole warp: every lane gets the same result, so the
 // warp's control flow stays converged even if a wait times out.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           long long budget, DevStatus *st, int where) {
