@@ -550,27 +550,34 @@ def bench_million(K, ctx, n=1 << 20, r=256, reps=2):
             "algorithmic_flops": "2 n^2 (d + r)"}
 
 
-def sample_only(n, r):
+def sample_only(n, r, image=False):
     """Five launches of the fused sampling product on the benchmark's data
-    distribution (d=8, standardized), for kernel profiling."""
+    distribution (d=8, standardized), or with image=True on MNIST-shaped
+    rows (d=784, h=4: the streamed wide-row kernel), for kernel profiling."""
     import torch
     import paper_1803_10274_gb300 as K
     import synth
     torch.cuda.set_device(0)
     ctx = K.Context()
-    X = synth.mixture(n, WL["d"], WL["comps"], WL["sigma"], WL["seed"])[0]
-    X = ((X - X.mean(0)) / X.std(0)).astype(np.float32)
+    if image:
+        X = synth.image_like(n, IMAGE_WL["seed"])[0].astype(np.float32)
+        h = IMAGE_WL["h"]
+    else:
+        X = synth.mixture(n, WL["d"], WL["comps"], WL["sigma"], WL["seed"])[0]
+        X = ((X - X.mean(0)) / X.std(0)).astype(np.float32)
+        h = WL["h"]
+    d = X.shape[1]
     Xd = torch.from_numpy(X).cuda()
     R = torch.from_numpy(np.random.default_rng(7).standard_normal((n, r)).astype(np.float16).astype(np.float32)).cuda()
     S = torch.empty(n, r, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx.stream)
     for _ in range(5):
-        K.krr_sample(ctx, Xd, Xd, WL["h"], 0.0, R, S=S)
+        K.krr_sample(ctx, Xd, Xd, h, 0.0, R, S=S)
     e1.record(ctx.stream)
     ctx.sync()
     ms = e0.elapsed_time(e1) / 5
-    print(json.dumps({"n": n, "r": r, "ms": ms, "tflops": 2.0 * n * n * (WL["d"] + r) / ms / 1e9}), flush=True)
+    print(json.dumps({"n": n, "d": d, "r": r, "ms": ms, "tflops": 2.0 * n * n * (d + r) / ms / 1e9}), flush=True)
 
 
 def cpu_baseline(X):
@@ -625,12 +632,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the gradient workload and the million-point product")
+    ap.add_argument("--image", action="store_true", help="with --sample-only: MNIST-shaped rows (d=784)")
     ap.add_argument("--batch-only", action="store_true", help="only run the MNIST-shaped and batched-problems workloads")
     ap.add_argument("--sample-only", nargs=2, type=int, metavar=("N", "R"),
                     help="only run the fused sampling product at n=N, r=R (5 launches; for profilers)")
     args = ap.parse_args()
     if args.sample_only:
-        sample_only(*args.sample_only)
+        sample_only(*args.sample_only, image=args.image)
     elif args.batch_only:
         import torch
         import paper_1803_10274_gb300 as K
