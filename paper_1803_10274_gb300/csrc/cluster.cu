@@ -1,7 +1,10 @@
 // Recursive two-means ordering (paper Sections 4.2-4.3, Algorithm 1 step 0)
 // on the GPU, level by level: every node of a tree level is split at once.
 //
-// Arithmetic is exact so that any schedule reaches the same permutation:
+// Arithmetic is exact so that any schedule reaches the same permutation
+// (when every segment has n d >= 3 the bound below keeps |q| <= 2^29, so a
+// coordinate minus a centre fits in 32 bits and each square is one
+// 32 x 32 -> 64-bit product; otherwise the squares are taken in 64 bits):
 // coordinates are quantized once to 64-bit integers q = rint(x 2^k) with k
 // the largest exponent for which every squared distance inside the data
 // hull, summed over all n points, stays below 2^63; distances, sums and
@@ -100,6 +103,16 @@ __global__ void quantize_seg_kernel(const float *X, int d, const int64_t *seg, c
         q[k] = __double2ll_rn(double(X[k]) * scale);
 }
 
+// (x - c)^2 exactly: in 32-bit differences when `narrow` (see above)
+__device__ __forceinline__ long long sq_diff(int64_t x, int64_t c, bool narrow) {
+    if (narrow) {
+        const int32_t a = int32_t(x - c);
+        return (long long)a * a;
+    }
+    const int64_t a = x - c;
+    return a * a;
+}
+
 struct NodeState {
     int64_t c0[kMaxD], c1[kMaxD];
     int64_t sum0[kMaxD], sum1[kMaxD];
@@ -109,7 +122,7 @@ struct NodeState {
 
 // One block per node: seeds and initial state.
 __global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const int64_t *nsize, const int64_t *nbase,
-                            NodeState *ns, uint64_t seed) {
+                            NodeState *ns, uint64_t seed, bool narrow) {
     const int v = blockIdx.x;
     const int64_t b = nbeg[v], m = nsize[v];
     NodeState &S = ns[v];
@@ -122,8 +135,7 @@ __global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const 
     auto dist0 = [&](int64_t i) -> unsigned long long {
         int64_t s = 0;
         for (int k = 0; k < d; ++k) {
-            const int64_t t = q[i * d + k] - c0[k];
-            s += t * t;
+            s += sq_diff(q[i * d + k], c0[k], narrow);
         }
         return (unsigned long long)s;
     };
@@ -196,7 +208,7 @@ __global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const 
 // memory (int64 atomics, exact and order-free) and added to the node once
 // per coordinate; dynamic shared memory: 2 d int64.
 __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t *node_of, NodeState *ns,
-                              int8_t *label) {
+                              int8_t *label, bool narrow) {
     extern __shared__ unsigned long long s_sum[];  // [2][d]
     __shared__ int s_uniform;
     __shared__ int32_t s_node;
@@ -228,9 +240,8 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
             long long d0 = 0, d1 = 0;
             for (int k = lane; k < d; k += 32) {
                 const int64_t x = q[ip * d + k];
-                const int64_t a = x - S.c0[k], bb = x - S.c1[k];
-                d0 += a * a;
-                d1 += bb * bb;
+                d0 += sq_diff(x, S.c0[k], narrow);
+                d1 += sq_diff(x, S.c1[k], narrow);
             }
             for (int o = 16; o > 0; o >>= 1) {
                 d0 += __shfl_xor_sync(0xffffffffu, d0, o);
@@ -243,9 +254,8 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
         int64_t d0 = 0, d1 = 0;
         for (int k = 0; k < d; ++k) {
             const int64_t x = q[i * d + k];
-            const int64_t a = x - S.c0[k], bb = x - S.c1[k];
-            d0 += a * a;
-            d1 += bb * bb;
+            d0 += sq_diff(x, S.c0[k], narrow);
+            d1 += sq_diff(x, S.c1[k], narrow);
         }
         lab = d0 > d1 ? 1 : 0;
     }
@@ -458,6 +468,8 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
     KRR_CUDA(cudaStreamSynchronize(st));
     if (hbad) return fail(KRR_ERR_NONFINITE_INPUT, "krr_cluster: NaN or Inf in X");
     std::vector<int> hk(nseg);
+    bool narrow = true;  // every segment has n d >= 3: differences fit in 32 bits
+    for (int p = 0; p < nseg; ++p) narrow = narrow && (seg[p + 1] - seg[p]) * int64_t(d) >= 3;
     for (int p = 0; p < nseg; ++p) {
         float maxabs;
         std::memcpy(&maxabs, &hmx[p], 4);
@@ -533,11 +545,11 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         KRR_CUDA(cudaMemcpyAsync(dbase.get(), hbase.data(), nn * 8, cudaMemcpyHostToDevice, st));
         KRR_CUDA(cudaMemsetAsync(node_of.get(), 0xFF, n * 4, st));
         { mark_nodes_kernel<<<nn, kTB, 0, st>>>(nn, db.get(), ds.get(), node_of.get()); ::krr::count_launch(); }
-        { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed); ::krr::count_launch(); }
+        { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed, narrow); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         for (int iter = 0; iter <= kMaxIter; ++iter) {
             KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
-            { assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get()); ::krr::count_launch(); }
+            { assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get(), narrow); ::krr::count_launch(); }
             { update_kernel<<<unsigned(cdiv(nn, 128)), 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             int hrun = 0;
