@@ -345,14 +345,13 @@ def bench_gradient(K, ctx, l2, reps=3):
     solves to 1e-6 and the augmented fused products)."""
     import torch
     import synth
-    from oracle import prep
     W = GRAD_WL
     X, _, Xt, _, c, ct = synth.mixture(W["n"], W["d"], W["comps"], 0.7, W["seed"], W["m_test"])
     y, yt = synth.labels_one_vs_rest(c, W["cls"]), synth.labels_one_vs_rest(ct, W["cls"])
-    # standardizing the inputs is data preparation, not part of the timed step
-    Z, Zt, _, _ = prep.standardize(X, Xt)
-    Xd = torch.from_numpy(Z.astype(np.float32)).cuda()
-    Xtd = torch.from_numpy(Zt.astype(np.float32)).cuda()
+    # standardizing the inputs (krr_standardize) is data preparation, not part of the timed step
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    Xtd = torch.from_numpy(Xt.astype(np.float32)).cuda()
+    K.krr_standardize(ctx, Xd, Xtd)
     yd, ytd = torch.from_numpy(y).cuda(), torch.from_numpy(yt).cuda()
     o = K.default_options(h=W["h"], lambda_=W["lam"], eps_c=W["eps_c"], leaf=W["leaf"], precision=K.KRR_MIXED)
 
@@ -385,12 +384,13 @@ BATCH_WL = dict(nprob=256, n_lo=512, n_hi=8192, dims=(8, 32, 128), hs=(0.5, 1.0,
                 eps_c=0.05, eps_abs=1e-2, r_max=1024, tol=1e-4, max_refine=600, seed=5)
 
 
-def batch_groups(W):
+def batch_groups(W, K, ctx):
     """The batched workload's data: one group per feature dimension, each a
-    list of (X, Y, h) systems; the 256 problems' sizes and dimensions are
-    drawn from the workload seed."""
+    list of (X, Y, h) systems (X on the device, standardized per problem by
+    krr_standardize); the 256 problems' sizes and dimensions are drawn from
+    the workload seed."""
+    import torch
     import synth
-    from oracle import prep
     rng = np.random.default_rng(W["seed"])
     sizes = rng.integers(W["n_lo"], W["n_hi"] + 1, size=W["nprob"])
     dims = rng.choice(W["dims"], size=W["nprob"])
@@ -399,7 +399,8 @@ def batch_groups(W):
         systems = []
         for p in np.nonzero(dims == d)[0]:
             X, y, *_ = synth.mixture(int(sizes[p]), int(d), 4, 0.7, 1000 + int(p))
-            Z = prep.standardize(X)[0].astype(np.float32)
+            Z = torch.from_numpy(X.astype(np.float32)).cuda()
+            K.krr_standardize(ctx, Z)
             Y = np.concatenate([y[:, None], rng.standard_normal((len(y), W["nrhs"] - 1))], 1)
             for h in W["hs"]:
                 systems.append((Z, Y, h))
@@ -418,11 +419,11 @@ def bench_batch(K, ctx, l2, reps=2):
     import torch
     W = BATCH_WL
     groups = []
-    for d, systems in batch_groups(W).items():
+    for d, systems in batch_groups(W, K, ctx).items():
         for h in W["hs"]:
             sel = [(x, y) for x, y, hh in systems if hh == h]
-            off = np.concatenate([[0], np.cumsum([len(x) for x, _ in sel])]).astype(np.int64)
-            groups.append((d, h, torch.from_numpy(np.concatenate([x for x, _ in sel])).cuda(),
+            off = np.concatenate([[0], np.cumsum([x.shape[0] for x, _ in sel])]).astype(np.int64)
+            groups.append((d, h, torch.cat([x for x, _ in sel]).contiguous(),
                            torch.from_numpy(np.ascontiguousarray(np.concatenate([y for _, y in sel]))).cuda(), off))
 
     def step():

@@ -86,6 +86,18 @@ long long krr_launch_count(void);
  * error.  Synchronizes. */
 int krr_sync(krr_ctx *ctx);
 
+/* Limit, in SM clock cycles, of each hand-off wait inside the pipelined
+ * tensor-core kernels (the fused products) that this context launches from
+ * now on; cycles <= 0 restores the default (4e9 cycles, about two seconds).
+ * When a wait runs past the limit the kernel stops its pipeline, lets the
+ * copies and tensor-core operations it already issued finish, frees its
+ * tensor memory and returns; the context latches KRR_ERR_TIMEOUT, which the
+ * next synchronizing call (krr_sync, a compression, a solve) returns and
+ * clears.  The outputs of that launch are then undefined; the context stays
+ * usable.  Failure detection (the paper has no counterpart): a stalled
+ * pipeline ends with an error status instead of a hung GPU. */
+int krr_set_wait_limit(krr_ctx *ctx, int64_t cycles);
+
 /* ---------------------------------------------------------------------
  * Feature standardization (Section 5.2: zero mean, unit standard
  * deviation per column; test data use the training statistics; a column
@@ -160,9 +172,10 @@ int krr_sample(krr_ctx *ctx, const float *Xa, int64_t ma, const float *Xb,
                const int32_t *leaf_b, float *S, int64_t lds);
 
 /* krr_sample without device-memory allocation, for callers that cannot
- * allocate at the point of the call (for example while a CUDA graph is
- * being captured, or under a fixed memory budget with no allocator at
- * hand).  The paper has no counterpart: this is an interface convenience.
+ * allocate at the point of the call: a process that runs under a fixed
+ * device-memory budget, one that has no allocator to hand to the library,
+ * or a latency-critical loop that must not enter an allocator.  The paper
+ * has no counterpart: this is an interface convenience.
  * Same arguments, result and precision as krr_sample (KRR_MIXED).  Its
  * scratch lives in one fixed device array inside the library (about
  * 12.6 MB, reserved on every GPU that loads the library until the process

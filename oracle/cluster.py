@@ -77,24 +77,42 @@ def _centre(qs: np.ndarray) -> np.ndarray:
     return (2 * s + cnt) // (2 * cnt)
 
 
+def pick_by_weight(weights, target: int) -> int:
+    """Index of the first entry whose inclusive prefix sum of the
+    non-negative integer weights exceeds target (0 <= target < total), so
+    entry j is picked for exactly weights[j] of the total target values."""
+    prefix = np.cumsum(np.asarray(weights, dtype=np.uint64), dtype=np.uint64)
+    return int(np.searchsorted(prefix, np.uint64(target), side="right"))
+
+
+def seed_pair(q: np.ndarray, seed: int, begin: int):
+    """The two starting representatives of the node with rows q (m x d)
+    that starts at row ``begin``: (first, second, total).  The first is
+    uniform over the rows; the second is drawn with probability
+    proportional to the squared distance to the first (reading 3 above);
+    second is None when every row coincides with the first (total 0)."""
+    m = q.shape[0]
+    w0, w1 = cluster_words(seed, begin, m)
+    first = mulhi64(w0, m)
+    dist = ((q - q[first]) ** 2).sum(axis=1)
+    du = dist.astype(np.uint64)
+    total = int(du.sum(dtype=np.uint64))
+    if total == 0:
+        return first, None, 0
+    return first, pick_by_weight(du, mulhi64(w1, total)), total
+
+
 def split_node(q: np.ndarray, seed: int, begin: int):
     """Two-means labels (0/1, int8) of the m rows q (m x d) of one node.
 
     Returns (labels, n_centre_updates, halved).
     """
     m = q.shape[0]
-    w0, w1 = cluster_words(seed, begin, m)
-    first = mulhi64(w0, m)
-    c0 = q[first].copy()
-    dist = ((q - c0) ** 2).sum(axis=1)
-    du = dist.astype(np.uint64)
-    total = int(du.sum(dtype=np.uint64))
+    first, second, total = seed_pair(q, seed, begin)
     halves = (np.arange(m) >= m // 2).astype(np.int8)
     if total == 0:
         return halves, 0, True
-    target = mulhi64(w1, total)
-    prefix = np.cumsum(du, dtype=np.uint64)
-    second = int(np.searchsorted(prefix, np.uint64(target), side="right"))
+    c0 = q[first].copy()
     c1 = q[second].copy()
 
     labels = None

@@ -73,6 +73,11 @@ class Context:
     def sync(self):
         check(lib().krr_sync(self.h))
 
+    def set_wait_limit(self, cycles=0):
+        """Limit of each device-side hand-off wait of the pipelined kernels
+        launched from now on, in SM clock cycles (0: the default)."""
+        check(lib().krr_set_wait_limit(self.h, int(cycles)))
+
     def close(self):
         if getattr(self, "h", None):
             if not _shutting_down[0]:
@@ -130,15 +135,52 @@ def krr_cluster_batched(ctx, X, offsets, leaf, seed):
     return perm, {k: v[:nn.value].copy() for k, v in arrs.items()}
 
 
-def krr_sample(ctx, Xa, Xb, h, lam, R, leaf_a=None, leaf_b=None, S=None):
-    _need(Xa, torch.float32, "Xa")
-    _need(Xb, torch.float32, "Xb")
-    _need(R, torch.float32, "R")
+def check_sample_args(Xa, Xb, R, S, leaf_a, leaf_b, dtype, cuda=True):
+    """Shapes, dtypes and layouts the C entry points of the fused product
+    rely on (they see only pointers, sizes and row strides): Xa (ma x d) and
+    Xb (nb x d) packed row-major, R (nb x r) and S (at least ma x r)
+    row-major, leaf arrays both given or both absent, int32 of length ma and
+    nb.  Raises ValueError; with cuda=False the device is not checked (the
+    rules themselves are tested on the host)."""
+    for t, name in ((Xa, "Xa"), (Xb, "Xb"), (R, "R"), (S, "S")):
+        if not torch.is_tensor(t) or t.dtype != dtype or t.dim() != 2:
+            raise ValueError("%s must be a 2-D %s tensor" % (name, dtype))
+        if cuda and not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
     ma, d = Xa.shape
     nb, r = R.shape
-    if S is None:
-        S = torch.empty(ma, r, dtype=torch.float32, device=Xa.device)
-    _need(S, torch.float32, "S")
+    if d < 1 or r < 1:
+        raise ValueError("d and r must be positive")
+    if tuple(Xb.shape) != (nb, d):
+        raise ValueError("Xb must be %d x %d (rows of R x columns of Xa), got %s" % (nb, d, tuple(Xb.shape)))
+    for t, name in ((Xa, "Xa"), (Xb, "Xb")):
+        if t.shape[0] > 1 and t.stride(0) != d or d > 1 and t.stride(1) != 1:
+            raise ValueError("%s must be packed row-major (row stride %d)" % (name, d))
+    if S.shape[0] < ma or S.shape[1] < r:
+        raise ValueError("S must hold at least %d x %d, got %s" % (ma, r, tuple(S.shape)))
+    for t, name in ((R, "R"), (S, "S")):
+        if t.shape[1] > 1 and t.stride(1) != 1:
+            raise ValueError("%s must be row-major (unit column stride)" % name)
+        if t.shape[0] > 1 and t.stride(0) < r:
+            raise ValueError("%s row stride must be at least r = %d" % (name, r))
+    if (leaf_a is None) != (leaf_b is None):
+        raise ValueError("give both leaf arrays or neither")
+    if leaf_a is not None:
+        for t, name, ln in ((leaf_a, "leaf_a", ma), (leaf_b, "leaf_b", nb)):
+            if not torch.is_tensor(t) or t.dtype != torch.int32 or t.dim() != 1 or t.shape[0] != ln:
+                raise ValueError("%s must be a 1-D int32 tensor of length %d" % (name, ln))
+            if ln > 1 and t.stride(0) != 1:
+                raise ValueError("%s must be contiguous" % name)
+            if cuda and not t.is_cuda:
+                raise ValueError("%s must be a CUDA tensor" % name)
+
+
+def krr_sample(ctx, Xa, Xb, h, lam, R, leaf_a=None, leaf_b=None, S=None):
+    if S is None and torch.is_tensor(Xa) and torch.is_tensor(R) and Xa.dim() == 2 and R.dim() == 2:
+        S = torch.empty(Xa.shape[0], R.shape[1], dtype=torch.float32, device=Xa.device)
+    check_sample_args(Xa, Xb, R, S, leaf_a, leaf_b, torch.float32)
+    ma, d = Xa.shape
+    nb, r = R.shape
     check(lib().krr_sample(ctx.h, _ptr(Xa), ma, _ptr(Xb), nb, d, h, lam, _ptr(R), r, R.stride(0),
                            _ptr(leaf_a), _ptr(leaf_b), _ptr(S), S.stride(0)))
     return S
@@ -147,10 +189,7 @@ def krr_sample(ctx, Xa, Xb, h, lam, R, leaf_a=None, leaf_b=None, S=None):
 def krr_sample_noalloc(ctx, Xa, Xb, h, lam, R, S, leaf_a=None, leaf_b=None):
     """krr_sample into a caller-provided S, with no device allocation in
     the library (fixed internal scratch; see include/krrhss.h for limits)."""
-    _need(Xa, torch.float32, "Xa")
-    _need(Xb, torch.float32, "Xb")
-    _need(R, torch.float32, "R")
-    _need(S, torch.float32, "S")
+    check_sample_args(Xa, Xb, R, S, leaf_a, leaf_b, torch.float32)
     ma, d = Xa.shape
     nb, r = R.shape
     check(lib().krr_sample_noalloc(ctx.h, _ptr(Xa), ma, _ptr(Xb), nb, d, h, lam, _ptr(R), r, R.stride(0),
@@ -159,14 +198,11 @@ def krr_sample_noalloc(ctx, Xa, Xb, h, lam, R, S, leaf_a=None, leaf_b=None):
 
 
 def krr_sample_f64(ctx, Xa, Xb, h, lam, R, leaf_a=None, leaf_b=None, S=None):
-    _need(Xa, torch.float64, "Xa")
-    _need(Xb, torch.float64, "Xb")
-    _need(R, torch.float64, "R")
+    if S is None and torch.is_tensor(Xa) and torch.is_tensor(R) and Xa.dim() == 2 and R.dim() == 2:
+        S = torch.empty(Xa.shape[0], R.shape[1], dtype=torch.float64, device=Xa.device)
+    check_sample_args(Xa, Xb, R, S, leaf_a, leaf_b, torch.float64)
     ma, d = Xa.shape
     nb, r = R.shape
-    if S is None:
-        S = torch.empty(ma, r, dtype=torch.float64, device=Xa.device)
-    _need(S, torch.float64, "S")
     check(lib().krr_sample_f64(ctx.h, _ptr(Xa), ma, _ptr(Xb), nb, d, h, lam, _ptr(R), r, R.stride(0),
                                _ptr(leaf_a), _ptr(leaf_b), _ptr(S), S.stride(0)))
     return S

@@ -115,6 +115,12 @@ void krr_destroy(krr_ctx *k) {
     delete k;
 }
 
+int krr_set_wait_limit(krr_ctx *k, int64_t cycles) {
+    if (!k) return fail(KRR_ERR_INVALID_ARG, "krr_set_wait_limit: ctx is NULL");
+    k->c.wait_cycles = cycles > 0 ? (long long)cycles : kDefaultWaitCycles;
+    return KRR_OK;
+}
+
 int krr_sync(krr_ctx *k) {
     if (!k) return fail(KRR_ERR_INVALID_ARG, "krr_sync: ctx is NULL");
     KRR_CUDA(cudaStreamSynchronize(k->c.stream));

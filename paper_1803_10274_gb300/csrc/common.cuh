@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,10 @@ struct DevStatus {
 };
 
 // ---------------------------------------------------------------- context
+// Default limit of one device-side wait of the pipelined kernels (about two
+// seconds of SM clock); krr_set_wait_limit changes it per context.
+constexpr long long kDefaultWaitCycles = 4000000000ll;
+
 struct Ctx {
     krr_allocator alloc{};
     bool has_alloc = false;
@@ -44,7 +49,24 @@ struct Ctx {
     int device = 0;
     int num_sms = 0;
     DevStatus *status = nullptr;  // device
+    long long wait_cycles = kDefaultWaitCycles;
 };
+
+// A kernel's dynamic shared-memory limit is an attribute of the device's
+// context, so it is raised once per device (and again if a larger size is
+// asked for).  Threads may race here; the call is idempotent.
+constexpr int kMaxDevices = 64;
+struct SmemLimitOnce {
+    std::atomic<int> bytes[kMaxDevices];
+};
+template <class F>
+inline cudaError_t raise_smem_limit(SmemLimitOnce &once, int device, F *kernel, int bytes) {
+    const bool cached = device >= 0 && device < kMaxDevices;
+    if (cached && once.bytes[device].load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && cached) once.bytes[device].store(bytes, std::memory_order_release);
+    return e;
+}
 
 void *dalloc(Ctx *c, size_t bytes);
 void dfree(Ctx *c, void *p);

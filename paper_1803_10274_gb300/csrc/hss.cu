@@ -1227,11 +1227,8 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             KRR_CUDA(cudaGetLastError());
         } else if (mmax < kBigNode && nn >= c->num_sms) {
             const size_t smem = size_t(r) * sizeof(T);
-            static bool attr = false;
-            if (!attr) {
-                KRR_CUDA(cudaFuncSetAttribute(id_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-                attr = true;
-            }
+            static SmemLimitOnce smem_limit;
+            KRR_CUDA(raise_smem_limit(smem_limit, c->device, id_kernel<T>, 96 * 1024));
             { id_kernel<T><<<nn, cta::kNT, smem, c->stream>>>(dl.get(), H->ddesc.get(), S, R, H->r_cap, r, F,
                                                               H->IA.get(), T(H->opt.eps_c), T(H->opt.eps_abs), kmax,
                                                               dranks.get(), derr.get(), c->status,

@@ -3,10 +3,10 @@
 //
 // krr_sample stages three scratch operands (the augmented FP16 rows of Xa
 // and Xb and the FP16 transpose of R) in memory it allocates per call.
-// Some callers cannot allocate device memory at that point: code being
-// captured into a CUDA graph (allocation calls are not capturable), code
-// running under a fixed memory budget or without access to the framework's
-// allocator, or real-time loops that must not touch the allocator.  This
+// Some callers cannot allocate device memory at that point: code running
+// under a fixed device-memory budget, code without access to an allocator
+// it could hand to the library, or latency-critical loops that must not
+// enter an allocator.  This
 // variant keeps the scratch in one file-scope device array of fixed size
 // instead, so a call only launches kernels and clears S.
 //
@@ -28,6 +28,7 @@ namespace {
 constexpr int64_t kNoAllocMaxRows = 16384;
 constexpr int kNoAllocMaxCols = 256;
 constexpr int kNoAllocKpad = 64;
+constexpr int kNoAllocMaxDim = 19;  // 3 * 19 + 6 = 63 augmented elements: one chunk
 constexpr size_t kXaOff = 0;
 constexpr size_t kXbOff = size_t(kNoAllocMaxRows) * kNoAllocKpad;
 constexpr size_t kRtOff = 2 * size_t(kNoAllocMaxRows) * kNoAllocKpad;
@@ -68,7 +69,9 @@ extern "C" int krr_sample_noalloc(krr_ctx *k, const float *Xa, int64_t ma, const
     if ((leaf_a == nullptr) != (leaf_b == nullptr))
         return fail(KRR_ERR_INVALID_ARG, "krr_sample_noalloc: give both leaf arrays or neither");
     if (lambda != 0.0 && ma != nb) return fail(KRR_ERR_INVALID_ARG, "krr_sample_noalloc: lambda needs Xa == Xb");
-    if (ma > kNoAllocMaxRows || nb > kNoAllocMaxRows || r > kNoAllocMaxCols || aug_kpad(d) > kNoAllocKpad)
+    // d is tested before aug_kpad(d) (3d + 6 must not overflow): 3d + 6 <= 64
+    if (ma > kNoAllocMaxRows || nb > kNoAllocMaxRows || r > kNoAllocMaxCols || d > kNoAllocMaxDim ||
+        aug_kpad(d) > kNoAllocKpad)
         return fail(KRR_ERR_INVALID_ARG,
                     "krr_sample_noalloc: size beyond the fixed scratch (rows <= 16384, r <= 256, d <= 19)");
     Ctx *c = &k->c;

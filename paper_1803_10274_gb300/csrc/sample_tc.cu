@@ -41,7 +41,7 @@ constexpr int kBN = 128;             // K columns of a tile
 constexpr int kChunk = 64;           // FP16 elements per 128-byte swizzled row
 constexpr int kChunkBytes = 128 * 128;
 constexpr int kMaxStages = 6;
-constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
+constexpr long long kWaitBudget = kDefaultWaitCycles;  // drain waits at kernel exit
 
 static_assert(kBM == kTcTile && kBN == kTcTile, "tile lists assume square 128-row tiles");
 
@@ -71,6 +71,7 @@ struct Params {
     float *S;
     int64_t lds;
     DevStatus *status;
+    long long wait;  // limit of one hand-off wait, SM clock cycles
 };
 
 // Barrier slots (uint64 each) after off_bar.
@@ -166,7 +167,7 @@ __device__ __forceinline__ void flush_s(const Params &P, uint64_t *bars, volatil
     const int lane = threadIdx.x & 31;
     const int sb = P.s_bufs == 2 ? int(seg & 1) : 0;
     const uint32_t par = P.s_bufs == 2 ? uint32_t((seg >> 1) & 1) : uint32_t(seg & 1);
-    if (!warp_wait(&bars[BAR_SFULL + sb], par, abort_flag, kWaitBudget, P.status, 8)) return;
+    if (!warp_wait(&bars[BAR_SFULL + sb], par, abort_flag, P.wait, P.status, 8)) return;
     tc_fence_after();
     for (int cc = 0; cc < rh; cc += 32) {
         uint32_t sv[32];
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int seg = c.seg++;
                 const int ab = P.a_bufs == 2 ? (seg & 1) : 0;
                 const int au = P.a_bufs == 2 ? (seg >> 1) : seg;  // use count of that buffer
-                if (!mbar_wait(&bars[BAR_AEMPTY + ab], uint32_t(au & 1) ^ 1u, abort_flag, kWaitBudget,
+                if (!mbar_wait(&bars[BAR_AEMPTY + ab], uint32_t(au & 1) ^ 1u, abort_flag, P.wait,
                                P.status, 1))
                     break;
                 mbar_expect_tx(&bars[BAR_AFULL + ab], a_bytes);
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 ch * kChunk, c.rt * kBM);
                 a_issued = seg;
             }
-            if (!mbar_wait(&bars[BAR_EMPTY + c.stage], c.sphase ^ 1u, abort_flag, kWaitBudget, P.status, 2)) break;
+            if (!mbar_wait(&bars[BAR_EMPTY + c.stage], c.sphase ^ 1u, abort_flag, P.wait, P.status, 2)) break;
             uint8_t *st = smem + P.off_stage + c.stage * P.stage_bytes;
             mbar_expect_tx(&bars[BAR_FULL + c.stage], P.stage_bytes);
             for (int ch = 0; ch < P.nchunk; ++ch)
@@ -327,9 +328,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int u = issued - 1 - k;
             mbar_wait_bounded(&bars[BAR_FULL + (u % NS)], uint32_t((u / NS) & 1), kWaitBudget);
         }
-        if (a_issued >= 0)
-            mbar_wait_bounded(&bars[BAR_AFULL + (P.a_bufs == 2 ? (a_issued & 1) : 0)],
-                              uint32_t((P.a_bufs == 2 ? (a_issued >> 1) : a_issued) & 1), kWaitBudget);
+        // Row-tile loads: only the last a_bufs can still be in flight (an
+        // earlier one into the same buffer was consumed before its reuse).
+        for (int sg = a_issued; sg >= 0 && sg > a_issued - P.a_bufs; --sg)
+            mbar_wait_bounded(&bars[BAR_AFULL + (P.a_bufs == 2 ? (sg & 1) : 0)],
+                              uint32_t((P.a_bufs == 2 ? (sg >> 1) : sg) & 1), kWaitBudget);
     } else if (warp == 1 && lane == 0 && nloc > 0) {
         // ------------------------------------------------ MMA issuer
         // The distance GEMM of tile loc + ND - 1 is issued before waiting for
@@ -350,10 +353,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int sg = cd.seg - 1;
                 if (!mbar_wait(&bars[BAR_AFULL + (P.a_bufs == 2 ? (sg & 1) : 0)],
                                uint32_t((P.a_bufs == 2 ? (sg >> 1) : sg) & 1), abort_flag,
-                               kWaitBudget, P.status, 3))
+                               P.wait, P.status, 3))
                     return false;
             }
-            if (!mbar_wait(&bars[BAR_FULL + cd.stage], cd.sphase, abort_flag, kWaitBudget, P.status, 4)) return false;
+            if (!mbar_wait(&bars[BAR_FULL + cd.stage], cd.sphase, abort_flag, P.wait, P.status, 4)) return false;
             tc_fence_after();
             const int abuf = P.a_bufs == 2 ? ((cd.seg - 1) & 1) : 0;
             const uint32_t a_base = smem_u32(smem + P.off_a + abuf * a_bytes);
@@ -376,11 +379,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int seg = cp.seg++;
                 const uint32_t par = P.s_bufs == 2 ? uint32_t((seg >> 1) & 1) : uint32_t(seg & 1);
                 if (!mbar_wait(&bars[BAR_SEMPTY + (P.s_bufs == 2 ? (seg & 1) : 0)], par ^ 1u, abort_flag,
-                               kWaitBudget, P.status, 5))
+                               P.wait, P.status, 5))
                     break;
             }
             const int sb = P.s_bufs == 2 ? ((cp.seg - 1) & 1) : 0;
-            if (!mbar_wait(&bars[BAR_PFULL + cp.db], cp.dphase, abort_flag, kWaitBudget, P.status, 6)) break;
+            if (!mbar_wait(&bars[BAR_PFULL + cp.db], cp.dphase, abort_flag, P.wait, P.status, 6)) break;
             tc_fence_after();
             const uint32_t r_base = smem_u32(smem + P.off_stage + cp.stage * P.stage_bytes + a_bytes);
             const uint32_t s_tmem = tmem + uint32_t(sb * P.r);
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         Cursor c;
         c.init(P, t0, nct);
         uint32_t va[32], vb[32];
-        bool ok = warp_wait(&bars[BAR_DFULL + 0], 0u, abort_flag, kWaitBudget, P.status, 7);
+        bool ok = warp_wait(&bars[BAR_DFULL + 0], 0u, abort_flag, P.wait, P.status, 7);
         if (ok) {
             tc_fence_after();
             tmem_ld32(tmem + lane_off + uint32_t(P.dist_col0 + 64 * g), va);
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (c.loc + 1 < nloc) {
                 const int nd = c.db + 1 == ND ? 0 : c.db + 1;
                 const uint32_t np = c.db + 1 == ND ? (c.dphase ^ 1u) : c.dphase;
-                if (!warp_wait(&bars[BAR_DFULL + nd], np, abort_flag, kWaitBudget, P.status, 7))
+                if (!warp_wait(&bars[BAR_DFULL + nd], np, abort_flag, P.wait, P.status, 7))
                     ok = false;
                 else {
                     tc_fence_after();
@@ -593,13 +596,10 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     P.S = S;
     P.lds = lds;
     P.status = c->status;
+    P.wait = c->wait_cycles;
 
-    static bool attr_set = false;
-    if (!attr_set) {
-        KRR_CUDA(cudaFuncSetAttribute(tc::sample_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      227 * 1024));
-        attr_set = true;
-    }
+    static SmemLimitOnce smem_limit;
+    KRR_CUDA(raise_smem_limit(smem_limit, c->device, tc::sample_tc_kernel, 227 * 1024));
     const int64_t T = P.n_tiles;
     if (T <= 0) return KRR_OK;
     const int grid = int(T < c->num_sms ? T : c->num_sms);

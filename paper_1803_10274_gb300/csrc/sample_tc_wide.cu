@@ -32,7 +32,7 @@ constexpr int kBN = 128;             // K columns of a tile
 constexpr int kChunk = 64;           // FP16 elements per 128-byte swizzled row
 constexpr int kChunkBytes = 128 * 128;
 constexpr int kMaxStages = 6;
-constexpr long long kWaitBudget = 4000000000ll;  // ~2 s of SM clock per wait
+constexpr long long kWaitBudget = kDefaultWaitCycles;  // drain waits at kernel exit
 
 static_assert(kBM == kTcTile && kBN == kTcTile, "tile lists assume square 128-row tiles");
 constexpr int kStageBytes = 2 * kChunkBytes;  // one 64-element chunk of the A and the B tile
@@ -63,6 +63,7 @@ struct Params {
     float *S;
     int64_t lds;
     DevStatus *status;
+    long long wait;  // limit of one hand-off wait, SM clock cycles
 };
 
 // Barrier slots (uint64 each) after off_bar.
@@ -158,7 +159,7 @@ __device__ __forceinline__ void flush_s(const Params &P, uint64_t *bars, volatil
     const int lane = threadIdx.x & 31;
     const int sb = P.s_bufs == 2 ? int(seg & 1) : 0;
     const uint32_t par = P.s_bufs == 2 ? uint32_t((seg >> 1) & 1) : uint32_t(seg & 1);
-    if (!warp_wait(&bars[BAR_SFULL + sb], par, abort_flag, kWaitBudget, P.status, 8)) return;
+    if (!warp_wait(&bars[BAR_SFULL + sb], par, abort_flag, P.wait, P.status, 8)) return;
     tc_fence_after();
     for (int cc = 0; cc < rh; cc += 32) {
         uint32_t sv[32];
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (; ok && c.loc < nloc; c.next(P, nloc, 1, 1)) {
             for (int ch = 0; ch < P.nchunk; ++ch) {
-                if (!mbar_wait(&bars[BAR_EMPTY + st], sph ^ 1u, abort_flag, kWaitBudget, P.status, 1)) {
+                if (!mbar_wait(&bars[BAR_EMPTY + st], sph ^ 1u, abort_flag, P.wait, P.status, 1)) {
                     ok = false;
                     break;
                 }
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok) break;
-            if (!mbar_wait(&bars[BAR_REMPTY + rb], rph ^ 1u, abort_flag, kWaitBudget, P.status, 2)) break;
+            if (!mbar_wait(&bars[BAR_REMPTY + rb], rph ^ 1u, abort_flag, P.wait, P.status, 2)) break;
             uint8_t *rp = smem + P.off_r + rb * P.r_bytes;
             mbar_expect_tx(&bars[BAR_RFULL + rb], P.r_bytes);
             tma_load_2d(rp, &tmR, &bars[BAR_RFULL + rb], c.ct * kBN, 0);
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             cd.flags(nloc);
             const uint32_t d_tmem = tmem + uint32_t(P.dist_col0 + cd.db * kBN);
             for (int ch = 0; ch < P.nchunk; ++ch) {
-                if (!mbar_wait(&bars[BAR_FULL + st], sph, abort_flag, kWaitBudget, P.status, 4)) return false;
+                if (!mbar_wait(&bars[BAR_FULL + st], sph, abort_flag, P.wait, P.status, 4)) return false;
                 tc_fence_after();
                 const uint32_t a_base = smem_u32(smem + P.off_stage + st * kStageBytes);
                 const uint32_t b_base = a_base + kChunkBytes;
@@ -376,12 +377,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int seg = cp.seg++;
                 const uint32_t par = P.s_bufs == 2 ? uint32_t((seg >> 1) & 1) : uint32_t(seg & 1);
                 if (!mbar_wait(&bars[BAR_SEMPTY + (P.s_bufs == 2 ? (seg & 1) : 0)], par ^ 1u, abort_flag,
-                               kWaitBudget, P.status, 5))
+                               P.wait, P.status, 5))
                     break;
             }
             const int sb = P.s_bufs == 2 ? ((cp.seg - 1) & 1) : 0;
-            if (!mbar_wait(&bars[BAR_PFULL + cp.db], cp.dphase, abort_flag, kWaitBudget, P.status, 6)) break;
-            if (!mbar_wait(&bars[BAR_RFULL + rb], rph, abort_flag, kWaitBudget, P.status, 9)) break;
+            if (!mbar_wait(&bars[BAR_PFULL + cp.db], cp.dphase, abort_flag, P.wait, P.status, 6)) break;
+            if (!mbar_wait(&bars[BAR_RFULL + rb], rph, abort_flag, P.wait, P.status, 9)) break;
             tc_fence_after();
             const uint32_t r_base = smem_u32(smem + P.off_r + rb * P.r_bytes);
             const uint32_t s_tmem = tmem + uint32_t(sb * P.r);
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         Cursor c;
         c.init(P, t0, nct);
         uint32_t va[32], vb[32];
-        bool ok = warp_wait(&bars[BAR_DFULL + 0], 0u, abort_flag, kWaitBudget, P.status, 7);
+        bool ok = warp_wait(&bars[BAR_DFULL + 0], 0u, abort_flag, P.wait, P.status, 7);
         if (ok) {
             tc_fence_after();
             tmem_ld32(tmem + lane_off + uint32_t(P.dist_col0 + 64 * g), va);
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (c.loc + 1 < nloc) {
                 const int nd = c.db + 1 == ND ? 0 : c.db + 1;
                 const uint32_t np = c.db + 1 == ND ? (c.dphase ^ 1u) : c.dphase;
-                if (!warp_wait(&bars[BAR_DFULL + nd], np, abort_flag, kWaitBudget, P.status, 7))
+                if (!warp_wait(&bars[BAR_DFULL + nd], np, abort_flag, P.wait, P.status, 7))
                     ok = false;
                 else {
                     tc_fence_after();
@@ -588,13 +589,10 @@ int launch_sample_tc_wide(Ctx *c, const __half *XA, int64_t ma, const __half *XB
     P.S = S;
     P.lds = lds;
     P.status = c->status;
+    P.wait = c->wait_cycles;
 
-    static bool attr_set = false;
-    if (!attr_set) {
-        KRR_CUDA(cudaFuncSetAttribute(tcw::sample_tc_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      227 * 1024));
-        attr_set = true;
-    }
+    static SmemLimitOnce smem_limit;
+    KRR_CUDA(raise_smem_limit(smem_limit, c->device, tcw::sample_tc_wide_kernel, 227 * 1024));
     const int64_t T = P.n_tiles;
     if (T <= 0) return KRR_OK;
     const int grid = int(T < c->num_sms ? T : c->num_sms);

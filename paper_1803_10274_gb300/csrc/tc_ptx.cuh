@@ -66,7 +66,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     const long long t0 = clock64();
     uint32_t k = 0;
     while (!mbar_test_wait(bar, parity)) {
-        if ((++k & 255u) == 0u) {
+        if ((k++ & 255u) == 0u) {  // first failed probe, then every 256th
             if (*abort_flag) return false;
             if (clock64() - t0 > budget) {
                 *abort_flag = 1;

@@ -1,0 +1,109 @@
+"""The binding's argument rules for the fused-product entry points
+(krr_sample, krr_sample_noalloc, krr_sample_f64).  The C calls see only
+pointers, sizes and row strides, so every shape, dtype and layout mistake
+must be caught before the call; each rule is exercised here on host
+tensors (no GPU needed)."""
+import pytest
+import torch
+
+from paper_1803_10274_gb300.binding import check_sample_args
+
+
+def _ok(ma=5, nb=7, d=3, r=4, dt=torch.float32, leaves=False):
+    Xa = torch.zeros(ma, d, dtype=dt)
+    Xb = torch.zeros(nb, d, dtype=dt)
+    R = torch.zeros(nb, r, dtype=dt)
+    S = torch.zeros(ma, r, dtype=dt)
+    la = torch.zeros(ma, dtype=torch.int32) if leaves else None
+    lb = torch.zeros(nb, dtype=torch.int32) if leaves else None
+    return dict(Xa=Xa, Xb=Xb, R=R, S=S, leaf_a=la, leaf_b=lb)
+
+
+def _check(a, dt=torch.float32):
+    check_sample_args(a["Xa"], a["Xb"], a["R"], a["S"], a["leaf_a"], a["leaf_b"], dt, cuda=False)
+
+
+def test_valid_arguments_pass():
+    _check(_ok())
+    _check(_ok(leaves=True))
+    _check(_ok(dt=torch.float64), torch.float64)
+    a = _ok()
+    a["S"] = torch.zeros(9, 6)             # a larger S is allowed
+    _check(a)
+    a = _ok()
+    a["R"] = torch.zeros(7, 10)[:, :4]     # R with a row stride above r
+    _check(a)
+
+
+def test_xb_shape_must_match_r_rows_and_xa_columns():
+    a = _ok()
+    a["Xb"] = torch.zeros(6, 3)            # fewer rows than R
+    with pytest.raises(ValueError, match="Xb"):
+        _check(a)
+    a = _ok()
+    a["Xb"] = torch.zeros(7, 4)            # other feature count
+    with pytest.raises(ValueError, match="Xb"):
+        _check(a)
+
+
+def test_s_must_hold_the_output():
+    a = _ok()
+    a["S"] = torch.zeros(4, 4)             # fewer rows than Xa
+    with pytest.raises(ValueError, match="S must hold"):
+        _check(a)
+    a = _ok()
+    a["S"] = torch.zeros(5, 3)             # fewer columns than R
+    with pytest.raises(ValueError, match="S must hold"):
+        _check(a)
+
+
+def test_feature_rows_must_be_packed():
+    a = _ok()
+    a["Xa"] = torch.zeros(5, 8)[:, :3]     # column slice: row stride 8, not d
+    with pytest.raises(ValueError, match="packed"):
+        _check(a)
+    a = _ok()
+    a["Xb"] = torch.zeros(3, 7).t()        # transposed view
+    with pytest.raises(ValueError, match="packed"):
+        _check(a)
+
+
+def test_r_and_s_row_major():
+    a = _ok()
+    a["R"] = torch.zeros(4, 7).t()
+    with pytest.raises(ValueError, match="row-major"):
+        _check(a)
+
+
+def test_dtypes():
+    a = _ok()
+    a["R"] = torch.zeros(7, 4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="R must be"):
+        _check(a)
+    with pytest.raises(ValueError, match="Xa must be"):
+        _check(_ok(), torch.float64)
+
+
+def test_leaf_arrays():
+    a = _ok(leaves=True)
+    a["leaf_b"] = None                     # one without the other
+    with pytest.raises(ValueError, match="both leaf arrays"):
+        _check(a)
+    a = _ok(leaves=True)
+    a["leaf_a"] = torch.zeros(4, dtype=torch.int32)    # wrong length
+    with pytest.raises(ValueError, match="leaf_a"):
+        _check(a)
+    a = _ok(leaves=True)
+    a["leaf_b"] = torch.zeros(7, dtype=torch.int64)    # wrong dtype
+    with pytest.raises(ValueError, match="leaf_b"):
+        _check(a)
+    a = _ok(leaves=True)
+    a["leaf_a"] = torch.zeros(10, dtype=torch.int32)[::2]  # strided
+    with pytest.raises(ValueError, match="contiguous"):
+        _check(a)
+
+
+def test_device_checked_by_default():
+    a = _ok()
+    with pytest.raises(ValueError, match="CUDA"):
+        check_sample_args(a["Xa"], a["Xb"], a["R"], a["S"], None, None, torch.float32)

@@ -117,3 +117,40 @@ def test_nonfinite_rejected():
     X[3, 1] = np.nan
     with pytest.raises(ValueError):
         cluster.two_means_tree(X, 4, 0)
+
+
+def test_second_seed_boundary_rule_worked_example():
+    """The second representative is the first row whose inclusive prefix sum
+    of squared distances exceeds the target.  Hand-worked: weights
+    [0, 4, 1, 9] have prefix sums [0, 4, 5, 14]; targets 0..3 land in row 1,
+    target 4 (exactly on the boundary) in row 2, targets 5..13 in row 3.
+    The zero-weight row (the first representative itself) is never drawn."""
+    w = np.array([0, 4, 1, 9], dtype=np.uint64)
+    got = [cluster.pick_by_weight(w, t) for t in range(14)]
+    assert got == [1, 1, 1, 1, 2] + [3] * 9
+    # a zero weight in the middle is skipped as well
+    assert [cluster.pick_by_weight(np.array([2, 0, 3], np.uint64), t) for t in range(5)] == [0, 0, 2, 2, 2]
+
+
+def test_second_seed_frequencies_follow_squared_distance():
+    """Section 4.3 draws the second point with probability growing with its
+    distance from the first; the oracle reads this as the squared distance
+    (k-means++ weight).  Over 20000 seeds the draws on five 1-D points must
+    follow D^2 / sum D^2 given the first point (chi-square, p > 1e-3); the
+    plain-distance weights are rejected by the same test."""
+    from scipy.stats import chisquare
+    q = np.array([[0], [1], [3], [6], [10]], dtype=np.int64)
+    counts = np.zeros((5, 5), dtype=np.int64)
+    for seed in range(20000):
+        f, s, total = cluster.seed_pair(q, seed, 0)
+        assert s is not None and s != f
+        counts[f, s] += 1
+    for f in range(5):
+        n_f = counts[f].sum()
+        assert n_f > 3000                          # the first point is uniform
+        others = [j for j in range(5) if j != f]
+        d2 = np.array([float((q[j, 0] - q[f, 0]) ** 2) for j in others])
+        p = chisquare(counts[f, others], n_f * d2 / d2.sum()).pvalue
+        assert p > 1e-3, (f, counts[f], p)
+        d1 = np.sqrt(d2)
+        assert chisquare(counts[f, others], n_f * d1 / d1.sum()).pvalue < 1e-6
