@@ -82,6 +82,15 @@ const char *krr_last_error(void);
  * (a diagnostic for profiling and benchmarks). */
 long long krr_launch_count(void);
 
+/* Measured throughput of one arithmetic pipe of the context's GPU (a
+ * diagnostic: the denominators of the fused product's secondary bounds and
+ * of the FP64 comparator).  which: 0 = FP32 FMA (flop/s, 2 per FMA),
+ * 1 = FP64 FMA (flop/s), 2 = ex2.approx.ftz.f32 on the SFU (results/s),
+ * 3 = cvt.rn.f16x2.f32 (converted values/s, 2 per instruction).  Runs
+ * independent chains in a full grid, best of three timed launches after a
+ * warm-up.  Synchronizes. */
+int krr_probe_rate(krr_ctx *ctx, int32_t which, double *ops_per_second);
+
 /* Wait for the context's stream and return (and clear) any latched device
  * error.  Synchronizes. */
 int krr_sync(krr_ctx *ctx);
@@ -299,12 +308,52 @@ int hss_solve(krr_hss *H, const double *y, int32_t nrhs, int64_t ldy,
               double *alpha, int64_t lda, double tol, int32_t max_refine,
               double *resid);
 
+/* y = H x for the HSS matrix H that the compression built (Section 3.1:
+ * leaf blocks D = K(I, I) + lambda I, nested interpolative bases U and
+ * sibling blocks B = K(J_a, J_b)), applied from those generators in FP64.
+ *   x, y   device double, n x nrhs (row strides ldx, ldy >= nrhs), original
+ *          row order; 1 <= nrhs <= 64
+ * The ULV factorization eliminates exactly this matrix, so hss_solve with
+ * tol <= 0 applied to H x returns x up to rounding, and
+ * (H - (K + lambda I)) x measures the compression error.  Works before or
+ * after hss_factor.  Single-problem handles only (batched handles return
+ * KRR_ERR_NOT_IMPLEMENTED).  Synchronizes. */
+int hss_matvec(krr_hss *H, const double *x, int32_t nrhs, int64_t ldx,
+               double *y, int64_t ldy);
+
 /* Decision values out = K(Xt, X) alpha (Algorithm 1 steps 3-4; the label
  * is sign(out) with sign(0) = +1).  Xt device float m x d (standardized
  * like X), alpha device double n x nrhs (original order), out device
  * double m x nrhs. */
 int krr_predict(krr_hss *H, const float *Xt, int64_t m, const double *alpha,
                 int32_t nrhs, int64_t lda, double *out, int64_t ldo);
+
+/* ---------------------------------------------------------------------
+ * Multi-class prediction by one-vs-all (Section 2, after Algorithm 1): one
+ * binary classifier per class, all c solved as right-hand sides of one
+ * hss_solve, and the class of a test point is the argmax of its c
+ * confidences.  The paper prints the confidence as |w(c)^T K'(i)|; read
+ * literally, a point far on the "not c" side would count as confident in
+ * c, so the default takes the signed value w(c)^T K'(i) (absolute = 0) and
+ * absolute = 1 gives the printed form.
+ * ------------------------------------------------------------------- */
+/* Right-hand sides of the c binary problems: Y(i, k) = +1 if cls[i] == k,
+ * else -1 (a class outside [0, c) gives -1 in every column).
+ *   cls  device int32[n];  Y  device double n x c (row stride ldy >= c)
+ * c >= 2. */
+int krr_one_vs_all(krr_ctx *ctx, const int32_t *cls, int64_t n, int32_t c,
+                   double *Y, int64_t ldy);
+
+/* Decision values dec = K(Xt, X) alpha (m x c, as krr_predict) and
+ * labels[i] = argmax_k score(i, k), the lowest k on ties, with score the
+ * decision value (absolute = 0) or its magnitude (absolute = 1).
+ *   alpha   device double n x c (row stride lda), 2 <= c <= 64
+ *   dec     device double m x c (row stride ldd >= c) output, or NULL
+ *   labels  device int32[m] output */
+int krr_predict_classes(krr_hss *H, const float *Xt, int64_t m,
+                        const double *alpha, int32_t c, int64_t lda,
+                        int32_t absolute, double *dec, int64_t ldd,
+                        int32_t *labels);
 
 /* ---------------------------------------------------------------------
  * Held-out squared-error loss and its gradient in h, lambda and the

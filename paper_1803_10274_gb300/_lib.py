@@ -56,6 +56,7 @@ SIGNATURES = {
     "krr_launch_count": (ctypes.c_longlong, []),
     "krr_sync": (i32, [P]),
     "krr_set_wait_limit": (i32, [P, i64]),
+    "krr_probe_rate": (i32, [P, i32, ctypes.POINTER(f64)]),
     "krr_standardize": (i32, [P, P, i64, i32, P, i64, P, P]),
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),
     "krr_cluster_batched": (i32, [P, P, i64, i32, i32, P, i32, u64, P, i32, krr_tree_arrays,
@@ -72,6 +73,9 @@ SIGNATURES = {
     "hss_factor": (i32, [P]),
     "hss_solve": (i32, [P, P, i32, i64, P, i64, f64, i32, ctypes.POINTER(f64)]),
     "krr_predict": (i32, [P, P, i64, P, i32, i64, P, i64]),
+    "hss_matvec": (i32, [P, P, i32, i64, P, i64]),
+    "krr_one_vs_all": (i32, [P, P, i64, i32, P, i64]),
+    "krr_predict_classes": (i32, [P, P, i64, P, i32, i64, i32, P, i64, P]),
     "krr_heldout_grad": (i32, [P, P, i64, P, P, f64, i32, ctypes.POINTER(f64), ctypes.POINTER(f64),
                                ctypes.POINTER(f64), P, i64, P, ctypes.POINTER(f64)]),
     "hss_stats": (i32, [P, ctypes.POINTER(krr_hss_stats)]),

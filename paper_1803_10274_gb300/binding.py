@@ -14,7 +14,7 @@ from . import _lib
 from ._lib import KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_TRUNCATE_AT_RMAX, KRRError, check, lib
 
 __all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "krr_standardize", "krr_cluster", "krr_sample",
-           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "HSS", "hss_compress", "default_options",
+           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "krr_one_vs_all", "HSS", "hss_compress", "default_options",
            "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]
 
 
@@ -72,6 +72,13 @@ class Context:
 
     def sync(self):
         check(lib().krr_sync(self.h))
+
+    def probe_rate(self, which):
+        """krr_probe_rate: 0 FP32 FMA flop/s, 1 FP64 FMA flop/s, 2 ex2/s,
+        3 FP32->FP16 conversions/s."""
+        v = ctypes.c_double()
+        check(lib().krr_probe_rate(self.h, int(which), ctypes.byref(v)))
+        return v.value
 
     def set_wait_limit(self, cycles=0):
         """Limit of each device-side hand-off wait of the pipelined kernels
@@ -215,6 +222,15 @@ def krr_random_block(ctx, n, r, col0, seed, precision=KRR_MIXED, device=None):
     return out
 
 
+def krr_one_vs_all(ctx, cls, c):
+    """n x c float64 right-hand sides of the c one-vs-all problems."""
+    _need(cls, torch.int32, "cls", dims=1)
+    cls = cls.contiguous()
+    Y = torch.empty(cls.shape[0], c, dtype=torch.float64, device=cls.device)
+    check(lib().krr_one_vs_all(ctx.h, _ptr(cls), cls.shape[0], c, _ptr(Y), c))
+    return Y
+
+
 def default_options(**kw):
     o = _lib.krr_options()
     lib().krr_default_options(ctypes.byref(o))
@@ -248,6 +264,29 @@ class HSS:
         if code != _lib.KRR_ERR_NO_CONVERGENCE or raise_on_no_convergence:
             check(code)
         return alpha, res.value
+
+    def predict_classes(self, Xt, alpha, absolute=False):
+        """One-vs-all classes (argmax of the c decision values) and the
+        decision values: (labels int32 [m], dec float64 m x c)."""
+        _need(Xt, torch.float32, "Xt")
+        _need(alpha, torch.float64, "alpha")
+        m, c = Xt.shape[0], alpha.shape[1]
+        dec = torch.empty(m, c, dtype=torch.float64, device=Xt.device)
+        lab = torch.empty(m, dtype=torch.int32, device=Xt.device)
+        check(lib().krr_predict_classes(self.h, _ptr(Xt.contiguous()), m, _ptr(alpha), c, alpha.stride(0),
+                                        1 if absolute else 0, _ptr(dec), c, _ptr(lab)))
+        return lab, dec
+
+    def matvec(self, x):
+        """y = H x with the compressed HSS matrix H (x: n x nrhs float64,
+        original order)."""
+        _need(x, torch.float64, "x")
+        if x.shape[0] != self.n:
+            raise ValueError("x must have n = %d rows" % self.n)
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        check(lib().hss_matvec(self.h, _ptr(x), x.shape[1], x.shape[1], _ptr(y), y.shape[1]))
+        return y
 
     def predict(self, Xt, alpha):
         _need(Xt, torch.float32, "Xt")

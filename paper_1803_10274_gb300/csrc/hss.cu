@@ -1962,6 +1962,204 @@ int hss_predict_batched_impl(HssImpl *H, const float *Xt, int64_t m, const std::
     return KRR_OK;
 }
 
+// ------------------------------------------------------------ multi-class
+// One-vs-all classification (Section 2, after Algorithm 1): c binary
+// right-hand sides solved at once, the class of a test point the argmax of
+// its c decision values.
+namespace {
+
+__global__ void one_vs_all_kernel(const int32_t *cls, int64_t n, int c, double *Y, int64_t ldy) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * c) return;
+    const int64_t i = e / c;
+    const int k = int(e % c);
+    Y[i * ldy + k] = cls[i] == k ? 1.0 : -1.0;
+}
+
+// Lowest class index on ties; score = decision value, or its magnitude.
+__global__ void class_argmax_kernel(const double *dec, int64_t m, int c, int64_t ldd, int absolute,
+                                    int32_t *labels) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const double *row = dec + i * ldd;
+    double best = absolute ? fabs(row[0]) : row[0];
+    int arg = 0;
+    for (int k = 1; k < c; ++k) {
+        const double v = absolute ? fabs(row[k]) : row[k];
+        if (v > best) {
+            best = v;
+            arg = k;
+        }
+    }
+    labels[i] = arg;
+}
+
+}  // namespace
+
+int one_vs_all_impl(Ctx *c, const int32_t *cls, int64_t n, int nc, double *Y, int64_t ldy) {
+    { one_vs_all_kernel<<<unsigned(cdiv(n * nc, 256)), 256, 0, c->stream>>>(cls, n, nc, Y, ldy); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
+int predict_classes_impl(HssImpl *H, const float *Xt, int64_t m, const double *alpha, int nc, int64_t lda,
+                         int absolute, double *dec, int64_t ldd, int32_t *labels) {
+    Ctx *c = H->c;
+    DBuf<double> own;
+    if (!dec) {
+        if (!own.reset(c, size_t(m) * nc)) return fail(KRR_ERR_OOM, "krr_predict_classes: out of memory");
+        dec = own.get();
+        ldd = nc;
+    }
+    KRR_TRY(hss_predict_impl(H, Xt, m, alpha, nc, lda, dec, ldd));
+    { class_argmax_kernel<<<unsigned(cdiv(m, 256)), 256, 0, c->stream>>>(dec, m, nc, ldd, absolute, labels); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
+// ------------------------------------------------------------ matvec
+// y = H x for the HSS matrix H the compression built (Section 3.1: leaf
+// blocks D = K(I, I) + lambda I, nested bases U = Pi [I; T^T] from the
+// interpolative decompositions, sibling blocks B_ab = K(J_a, J_b)):
+//   up:    xhat_tau = U_tau^T [x_tau (leaf) | xhat_a; xhat_b (parent)]
+//   down:  u = U_tau yhat_tau (0 at the root);
+//          yhat_a = u_a + B_ab xhat_b,  yhat_b = u_b + B_ab^T xhat_a
+//   leaf:  y_tau = D_tau x_tau + U_tau yhat_tau
+// The ULV factorization eliminates exactly this matrix, so solving H x
+// returns x to rounding; products of H with random x against (K + lambda I)x
+// measure the compression error.  Sums in FP64 over the stored generators.
+namespace {
+
+// W: per node v, xhat at W + off[v] (k x nrhs), yhat at W + off[v] + m * nrhs
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) mv_up_kernel(const int *ids, const NodeDesc *all, const double *xp,
+                                                         int nrhs, const int64_t *off, double *W, const T *F,
+                                                         const int32_t *I) {
+    const int v = ids[blockIdx.x];
+    const NodeDesc &N = all[v];
+    const int m = N.m, k = N.k, nr = m - k;
+    const int32_t *piv = I + N.piv;
+    const T *Tm = F + N.tmat;
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    auto local = [&](int a, int c) -> double {
+        if (N.is_leaf) return xp[(N.leaf_begin + int64_t(a)) * nrhs + c];
+        if (a < A->k) return W[off[N.child_a] + int64_t(a) * nrhs + c];
+        return W[off[N.child_b] + int64_t(a - A->k) * nrhs + c];
+    };
+    double *xh = W + off[v];
+    for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
+        const int j = e / nrhs, c = e % nrhs;
+        double s = local(piv[j], c);
+        for (int i = 0; i < nr; ++i) s += double(Tm[int64_t(j) * nr + i]) * local(piv[k + i], c);
+        xh[e] = s;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) mv_down_kernel(const int *ids, const NodeDesc *all, const double *xp,
+                                                           const T *X, int d, T inv2h2, double lambda, int nrhs,
+                                                           const int64_t *off, double *W, const T *F,
+                                                           const int32_t *I, double *yp, int is_root) {
+    const int v = ids[blockIdx.x];
+    const NodeDesc &N = all[v];
+    const int m = N.m, k = is_root ? 0 : N.k, nr = m - k;
+    const int32_t *piv = I + N.piv;
+    const T *Tm = F + N.tmat;
+    const double *yh = W + off[v] + int64_t(m) * nrhs;
+    for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
+        const int p = e / nrhs, c = e % nrhs;
+        // (U yhat) at local row a: the skeleton rows take yhat, the redundant
+        // ones T^T yhat (local rows in pivot order; a root has no basis)
+        const int a = is_root ? p : piv[p];
+        double u = 0.0;
+        if (p < k) u = yh[int64_t(p) * nrhs + c];
+        else if (k > 0)
+            for (int j = 0; j < k; ++j) u += double(Tm[int64_t(j) * nr + (p - k)]) * yh[int64_t(j) * nrhs + c];
+        if (N.is_leaf) {
+            const T *xa = X + (N.leaf_begin + int64_t(a)) * d;
+            double s = 0.0;
+            for (int b = 0; b < m; ++b) {
+                const double dab = a == b ? 1.0 + lambda : double(kern(xa, X + (N.leaf_begin + int64_t(b)) * d, d, inv2h2));
+                s += dab * xp[(N.leaf_begin + int64_t(b)) * nrhs + c];
+            }
+            yp[(N.leaf_begin + int64_t(a)) * nrhs + c] = s + u;
+            continue;
+        }
+        const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
+        const int ka = A.k, kb = B.k;
+        const T *Bm = F + N.bmat;  // ka x kb
+        if (a < ka) {
+            const double *xb = W + off[N.child_b];
+            for (int j = 0; j < kb; ++j) u += double(Bm[int64_t(a) * kb + j]) * xb[int64_t(j) * nrhs + c];
+            W[off[N.child_a] + int64_t(A.m) * nrhs + int64_t(a) * nrhs + c] = u;
+        } else {
+            const double *xa = W + off[N.child_a];
+            for (int i = 0; i < ka; ++i) u += double(Bm[int64_t(i) * kb + (a - ka)]) * xa[int64_t(i) * nrhs + c];
+            W[off[N.child_b] + int64_t(B.m) * nrhs + int64_t(a - ka) * nrhs + c] = u;
+        }
+    }
+}
+
+template <class T>
+int matvec_t(HssImpl *H, const double *xp, int nrhs, double *yp) {
+    Ctx *c = H->c;
+    const int nn = int(H->desc.size());
+    std::vector<int64_t> off(nn);
+    int64_t tot = 0;
+    for (int v = 0; v < nn; ++v) {
+        off[v] = tot;
+        tot += 2 * int64_t(H->desc[v].m) * nrhs;
+    }
+    DBuf<double> W(c, size_t(tot));
+    DBuf<int64_t> doff(c, nn);
+    DBuf<int> ids(c, nn);
+    if (!W.get() || !doff.get() || !ids.get()) return fail(KRR_ERR_OOM, "hss_matvec: out of memory");
+    std::vector<int> order;
+    std::vector<int> lvl_start(H->H + 2, 0);
+    for (int h = 0; h <= H->H; ++h) {
+        lvl_start[h] = int(order.size());
+        for (int v : H->by_height[h]) order.push_back(v);
+    }
+    lvl_start[H->H + 1] = int(order.size());
+    KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
+    KRR_CUDA(cudaMemcpyAsync(doff.get(), off.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    KRR_CUDA(cudaMemcpyAsync(ids.get(), order.data(), nn * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    const T *F = farena<T>(H);
+    const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
+    const T inv2h2 = T(1.0 / (2.0 * H->opt.h * H->opt.h));
+    for (int h = 0; h < H->H; ++h) {
+        const int cnt = lvl_start[h + 1] - lvl_start[h];
+        if (!cnt) continue;
+        { mv_up_kernel<T><<<cnt, cta::kNT, 0, c->stream>>>(ids.get() + lvl_start[h], H->ddesc.get(), xp, nrhs,
+                                                            doff.get(), W.get(), F, H->IA.get()); ::krr::count_launch(); }
+        KRR_CUDA(cudaGetLastError());
+    }
+    for (int h = H->H; h >= 0; --h) {
+        const int cnt = lvl_start[h + 1] - lvl_start[h];
+        if (!cnt) continue;
+        { mv_down_kernel<T><<<cnt, cta::kNT, 0, c->stream>>>(ids.get() + lvl_start[h], H->ddesc.get(), xp, X, H->d,
+                                                              inv2h2, H->lambda, nrhs, doff.get(), W.get(), F,
+                                                              H->IA.get(), yp, h == H->H ? 1 : 0); ::krr::count_launch(); }
+        KRR_CUDA(cudaGetLastError());
+    }
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
+}  // namespace
+
+int hss_matvec_impl(HssImpl *H, const double *x, int nrhs, int64_t ldx, double *y, int64_t ldy) {
+    Ctx *c = H->c;
+    const int64_t n = H->n;
+    DBuf<double> xp(c, size_t(n) * nrhs), yp(c, size_t(n) * nrhs);
+    if (!xp.get() || !yp.get()) return fail(KRR_ERR_OOM, "hss_matvec: out of memory");
+    KRR_TRY((gather_rows<double, double>(c, x, ldx, H->perm.get(), n, nrhs, xp.get(), nrhs)));
+    if (H->mixed()) KRR_TRY(matvec_t<float>(H, xp.get(), nrhs, yp.get()));
+    else KRR_TRY(matvec_t<double>(H, xp.get(), nrhs, yp.get()));
+    KRR_TRY((scatter_rows<double, double>(c, yp.get(), nrhs, H->perm.get(), n, nrhs, y, ldy)));
+    return take_status(c, "hss_matvec");
+}
+
 // ------------------------------------------------------------ gradient
 // Held-out loss L = 1/2 ||K(Xt, X) alpha - yt||^2 with alpha =
 // (K + lambda I)^{-1} y and its adjoint gradient in h, lambda and X (the
@@ -2300,6 +2498,29 @@ int hss_solve(krr_hss *H, const double *y, int32_t nrhs, int64_t ldy, double *al
     if (!H || !y || !alpha || nrhs < 1 || ldy < nrhs || lda < nrhs || max_refine < 0)
         return fail(KRR_ERR_INVALID_ARG, "hss_solve: bad arguments");
     return hss_solve_impl(&H->h, y, nrhs, ldy, alpha, lda, tol, max_refine, resid);
+}
+
+int krr_one_vs_all(krr_ctx *k, const int32_t *cls, int64_t n, int32_t c, double *Y, int64_t ldy) {
+    if (!k || !cls || !Y || n < 0 || c < 2 || ldy < c) return fail(KRR_ERR_INVALID_ARG, "krr_one_vs_all: bad arguments");
+    if (n == 0) return KRR_OK;
+    return one_vs_all_impl(&k->c, cls, n, c, Y, ldy);
+}
+
+int krr_predict_classes(krr_hss *H, const float *Xt, int64_t m, const double *alpha, int32_t c, int64_t lda,
+                        int32_t absolute, double *dec, int64_t ldd, int32_t *labels) {
+    if (!H || !Xt || !alpha || !labels || m < 0 || c < 2 || c > 64 || lda < c || (dec && ldd < c) ||
+        (absolute != 0 && absolute != 1))
+        return fail(KRR_ERR_INVALID_ARG, "krr_predict_classes: bad arguments");
+    if (H->h.nprob > 0) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_predict_classes: batched handle");
+    if (m == 0) return KRR_OK;
+    return predict_classes_impl(&H->h, Xt, m, alpha, c, lda, absolute, dec, ldd, labels);
+}
+
+int hss_matvec(krr_hss *H, const double *x, int32_t nrhs, int64_t ldx, double *y, int64_t ldy) {
+    if (!H || !x || !y || nrhs < 1 || nrhs > 64 || ldx < nrhs || ldy < nrhs)
+        return fail(KRR_ERR_INVALID_ARG, "hss_matvec: bad arguments");
+    if (H->h.nprob > 0) return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_matvec: batched handle");
+    return hss_matvec_impl(&H->h, x, nrhs, ldx, y, ldy);
 }
 
 int krr_predict(krr_hss *H, const float *Xt, int64_t m, const double *alpha, int32_t nrhs, int64_t lda, double *out,

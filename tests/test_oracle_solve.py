@@ -45,3 +45,41 @@ def test_standardize():
     np.testing.assert_allclose(Z[:, [0, 1, 3]].std(0), 1, rtol=1e-12)
     assert np.all(Z[:, 2] == 0)
     np.testing.assert_allclose(Zt, Z[:5])
+
+
+def test_dense_large_route_equals_hand_cholesky():
+    """The in-place 64-bit LAPACK route used for the 65536-point golden
+    solve gives the hand-written Cholesky's solution (n below LAPACK_ABOVE)."""
+    import synth
+    X, y, *_ = synth.mixture(900, 8, 4, 0.7, 7)
+    a = solve.krr_dense(X, y, 1.0, 1.0)
+    b = solve.krr_dense_large(X, y, 1.0, 1.0)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_one_vs_all_targets_and_argmax_worked_example():
+    """One-vs-all (Section 2 after Algorithm 1): one +1 per row; argmax with
+    the lowest class on ties; the literal |.| confidence differs from the
+    signed one on a point that is strongly "not class 0"."""
+    Y = solve.one_vs_all_targets([2, 0, 1, 2], 3)
+    assert Y.tolist() == [[-1, -1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]]
+    dec = np.array([[0.2, 0.9, -0.1],
+                    [0.5, 0.5, 0.1],      # tie: lowest index
+                    [-3.0, 0.4, 0.2],     # signed -> 1, absolute -> 0
+                    [-0.1, -0.2, -0.3]])
+    assert solve.predict_classes(dec).tolist() == [1, 0, 1, 0]
+    assert solve.predict_classes(dec, absolute=True).tolist() == [1, 0, 0, 2]
+
+
+def test_two_classes_reduce_to_the_sign_rule():
+    """With c = 2 the one-vs-all targets are y and -y, so w(1) = -w(0) and
+    the signed argmax is the binary rule sign(w^T K'(i)) with sign(0) = +1
+    (class 0 <-> label +1) of Algorithm 1 step 4."""
+    import synth
+    X, y, Xt, yt, comp, comp_t = synth.mixture(300, 4, 2, 0.7, 11, 120)
+    cls = (comp % 2).astype(np.int32)          # class 0 <-> label +1
+    W = solve.krr_dense(X, solve.one_vs_all_targets(cls, 2), 1.0, 1.0)
+    dec = solve.predict(Xt, X, W, 1.0)
+    w = solve.krr_dense(X, np.where(cls == 0, 1.0, -1.0), 1.0, 1.0)
+    lab = solve.sign_pm1(solve.predict(Xt, X, w, 1.0)[:, 0])
+    assert np.array_equal(solve.predict_classes(dec), np.where(lab > 0, 0, 1))
