@@ -24,7 +24,10 @@ int random_block(Ctx *c, int64_t n, int r, int col0, uint64_t seed, int precisio
 inline int aug_used(int d) { return 3 * d + 6; }
 inline int aug_kmma(int d) { return int(cdiv(aug_used(d), 16)); }
 inline int aug_chunks(int d) { return int(cdiv(aug_used(d), 64)); }
-inline int aug_kpad(int d) { return 64 * aug_chunks(d); }
+// d <= 8 (3d + 6 <= 32): one 32-element chunk of 64-byte rows (64-byte
+// swizzle), half the shared-memory bytes of a 64-element chunk
+inline bool aug_narrow(int d) { return aug_used(d) <= 32; }
+inline int aug_kpad(int d) { return aug_narrow(d) ? 32 : 64 * aug_chunks(d); }
 constexpr int kMaxResidentDim = 82;  // 3d + 6 <= 256: rows resident in shared memory (four chunks)
 constexpr int kMaxMixedDim = 1024;   // above kMaxResidentDim the rows stream chunk by chunk
 

@@ -57,7 +57,9 @@ struct Params {
     int ndist;    // distance / K buffers in tensor memory (2 or 3)
     int dist_col0;
     int split_k;  // 1: K = K_hi + K_lo (two FP16 parts, two product MMAs)
-    int a_bufs;   // row-tile (A) buffers in shared memory: 2, or 1 for wide feature rows
+    int a_bufs;   // row-tile (A) buffers in shared memory: 2, or 1 when that buys a stage
+    uint32_t chunk_bytes;  // 128 rows x 128 B (64-element chunks), or x 64 B (one 32-element chunk)
+    uint32_t ab_hi;        // descriptor high word of the A / B chunks (128- or 64-byte swizzle)
     uint32_t off_a, off_stage, stage_bytes, off_bar;
     const int32_t *leaf_a, *leaf_b;
     // block-diagonal products (many independent problems in one launch):
@@ -242,6 +244,14 @@ struct Cursor {
     }
 };
 
+// PAIR = true: clusters of two CTAs walk the same column tiles for two
+// adjacent row tiles (CTA rank q takes row tile 2 u + q of row unit u).
+// Each column tile's B rows and R tile are read from L2 once: each CTA
+// loads half of them (its half of the B rows, its 64 columns of R^T) and
+// multicasts it into both CTAs' stage; a stage is free again once both
+// CTAs' MMAs have released it.  P.n_row_tiles then counts row units and
+// the tile list (if any) is over row units.
+template <bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     sample_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmR, const Params P) {
@@ -255,14 +265,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int nct = int(P.n_col_tiles);
     const int64_t T = P.n_tiles;
-    const int64_t t0 = T * blockIdx.x / gridDim.x;
-    const int nloc = int(T * (blockIdx.x + 1) / gridDim.x - t0);
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const int64_t unit = PAIR ? blockIdx.x / 2 : blockIdx.x, nunits = PAIR ? gridDim.x / 2 : gridDim.x;
+    const int64_t t0 = T * unit / nunits;
+    const int nloc = int(T * (unit + 1) / nunits - t0);
     const int NS = P.nstage, ND = P.ndist;
+    // this CTA's row tile within row unit u
+    auto row_tile = [&](int u) -> int { return PAIR ? 2 * u + int(rank) : u; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&bars[BAR_FULL + s], 1);
-            mbar_init(&bars[BAR_EMPTY + s], 1);
+            mbar_init(&bars[BAR_EMPTY + s], PAIR ? 2 : 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bars[BAR_AFULL + b], 1);
@@ -289,9 +303,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();  // the peer's barriers are initialized
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t a_bytes = P.nchunk * kChunkBytes;
+    const uint32_t a_bytes = P.nchunk * P.chunk_bytes;
 
     if (warp == 0 && lane == 0 && nloc > 0) {
         // ------------------------------------------------ TMA producer
@@ -309,19 +324,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 mbar_expect_tx(&bars[BAR_AFULL + ab], a_bytes);
                 for (int ch = 0; ch < P.nchunk; ++ch)
-                    tma_load_2d(smem + P.off_a + ab * a_bytes + ch * kChunkBytes, &tmA, &bars[BAR_AFULL + ab],
-                                ch * kChunk, c.rt * kBM);
+                    tma_load_2d(smem + P.off_a + ab * a_bytes + ch * P.chunk_bytes, &tmA, &bars[BAR_AFULL + ab],
+                                ch * kChunk, row_tile(c.rt) * kBM);
                 a_issued = seg;
             }
+            // PAIR: the wait also covers the peer's MMAs, so both CTAs'
+            // copies of this stage are free before either half is sent
             if (!mbar_wait(&bars[BAR_EMPTY + c.stage], c.sphase ^ 1u, abort_flag, P.wait, P.status, 2)) break;
             uint8_t *st = smem + P.off_stage + c.stage * P.stage_bytes;
             mbar_expect_tx(&bars[BAR_FULL + c.stage], P.stage_bytes);
-            for (int ch = 0; ch < P.nchunk; ++ch)
-                tma_load_2d(st + ch * kChunkBytes, &tmB, &bars[BAR_FULL + c.stage], ch * kChunk, c.ct * kBN);
-            tma_load_2d(st + a_bytes, &tmR, &bars[BAR_FULL + c.stage], c.ct * kBN, 0);
-            tma_load_2d(st + a_bytes + P.r * 128, &tmR, &bars[BAR_FULL + c.stage], c.ct * kBN + 64, 0);
+            if (PAIR) {
+                // rank q: B rows [64 q, 64 q + 64) of the tile (a 64-row box at
+                // byte 8192 q keeps the 128-byte swizzle of the full tile) and
+                // R^T columns [64 q, 64 q + 64), both to both CTAs
+                const int q = int(rank);
+                for (int ch = 0; ch < P.nchunk; ++ch)
+                    tma_load_2d_mc(st + ch * P.chunk_bytes + q * (P.chunk_bytes / 2), &tmB, &bars[BAR_FULL + c.stage],
+                                   ch * kChunk, c.ct * kBN + 64 * q, uint16_t(3));
+                tma_load_2d_mc(st + a_bytes + q * P.r * 128, &tmR, &bars[BAR_FULL + c.stage], c.ct * kBN + 64 * q,
+                               0, uint16_t(3));
+            } else {
+                for (int ch = 0; ch < P.nchunk; ++ch)
+                    tma_load_2d(st + ch * P.chunk_bytes, &tmB, &bars[BAR_FULL + c.stage], ch * kChunk, c.ct * kBN);
+                tma_load_2d(st + a_bytes, &tmR, &bars[BAR_FULL + c.stage], c.ct * kBN, 0);
+                tma_load_2d(st + a_bytes + P.r * 128, &tmR, &bars[BAR_FULL + c.stage], c.ct * kBN + 64, 0);
+            }
             ++issued;
         }
+        const bool aborted = *abort_flag != 0;
         // Drain: wait (bounded) until every load issued has landed, so no
         // TMA write is in flight when the CTA exits.
         for (int k = 0; k < (issued < NS ? issued : NS); ++k) {
@@ -333,6 +363,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int sg = a_issued; sg >= 0 && sg > a_issued - P.a_bufs; --sg)
             mbar_wait_bounded(&bars[BAR_AFULL + (P.a_bufs == 2 ? (sg & 1) : 0)],
                               uint32_t((P.a_bufs == 2 ? (sg >> 1) : sg) & 1), kWaitBudget);
+        if (PAIR) {
+            // The peer's MMAs release this CTA's stages by remote commits:
+            // wait until the last use of every stage has both releases, so
+            // no arrival is still on its way when the CTA exits.  After an
+            // abort the peer may have stopped early (short bound), and its
+            // multicast halves of steps this CTA never armed get a grace
+            // period to land.
+            const long long lim = aborted ? 200000ll : kWaitBudget;
+            for (int k = 0; k < (issued < NS ? issued : NS); ++k) {
+                const int u = issued - 1 - k;
+                mbar_wait_bounded(&bars[BAR_EMPTY + (u % NS)], uint32_t((u / NS) & 1), lim);
+            }
+            if (aborted) {
+                const long long tg = clock64();
+                while (clock64() - tg < 200000ll) {
+                }
+            }
+        }
     } else if (warp == 1 && lane == 0 && nloc > 0) {
         // ------------------------------------------------ MMA issuer
         // The distance GEMM of tile loc + ND - 1 is issued before waiting for
@@ -342,6 +390,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // read its K values.
         const uint32_t idesc_d = idesc_f16_f32(kBM, kBN);
         const uint32_t idesc_p = idesc_f16_f32(kBM, P.r);
+        // descriptor low words of buffer 0 / stage 0 and the strides between
+        // buffers (16-byte units): each MMA then costs one 32-bit add
+        const uint32_t a_lo0 = sdesc_lo_sw128(smem_u32(smem + P.off_a));
+        const uint32_t b_lo0 = sdesc_lo_sw128(smem_u32(smem + P.off_stage));
+        const uint32_t r_lo0 = sdesc_lo_sw128(smem_u32(smem + P.off_stage + a_bytes));
+        const uint32_t a_units = a_bytes >> 4, stage_units = P.stage_bytes >> 4;
+        const uint32_t rbox_units = uint32_t(P.r * 128) >> 4;  // second 64-row box of the R tile
         Cursor cd, cp;  // distance-side and product-side positions
         cd.init(P, t0, nct);
         cp.init(P, t0, nct);
@@ -359,12 +414,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(&bars[BAR_FULL + cd.stage], cd.sphase, abort_flag, P.wait, P.status, 4)) return false;
             tc_fence_after();
             const int abuf = P.a_bufs == 2 ? ((cd.seg - 1) & 1) : 0;
-            const uint32_t a_base = smem_u32(smem + P.off_a + abuf * a_bytes);
-            const uint32_t b_base = smem_u32(smem + P.off_stage + cd.stage * P.stage_bytes);
+            const uint32_t a_lo = a_lo0 + uint32_t(abuf) * a_units;
+            const uint32_t b_lo = b_lo0 + uint32_t(cd.stage) * stage_units;
             const uint32_t d_tmem = tmem + uint32_t(P.dist_col0 + cd.db * kBN);
-            for (int k = 0; k < P.kmma; ++k) {
-                const uint32_t off = (k >> 2) * kChunkBytes + (k & 3) * 32;
-                mma_ss(d_tmem, sdesc_k_sw128(a_base + off), sdesc_k_sw128(b_base + off), idesc_d, k > 0);
+            mma_ss_w(d_tmem, a_lo, b_lo, P.ab_hi, idesc_d, 0u);
+#pragma unroll 1
+            for (int k = 1; k < P.kmma; ++k) {
+                // 32 bytes per 16-element K step inside a chunk (a 32-element
+                // chunk has at most two steps, so k >> 2 is 0 there)
+                const uint32_t off = uint32_t(k >> 2) * (P.chunk_bytes >> 4) + uint32_t((k & 3) * 2);
+                mma_ss_w(d_tmem, a_lo + off, b_lo + off, P.ab_hi, idesc_d, 1u);
             }
             tc_commit(&bars[BAR_DFULL + cd.db]);
             if (cd.last) tc_commit(&bars[BAR_AEMPTY + abuf]);
@@ -385,26 +444,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int sb = P.s_bufs == 2 ? ((cp.seg - 1) & 1) : 0;
             if (!mbar_wait(&bars[BAR_PFULL + cp.db], cp.dphase, abort_flag, P.wait, P.status, 6)) break;
             tc_fence_after();
-            const uint32_t r_base = smem_u32(smem + P.off_stage + cp.stage * P.stage_bytes + a_bytes);
+            const uint32_t r_lo = r_lo0 + uint32_t(cp.stage) * stage_units;
             const uint32_t s_tmem = tmem + uint32_t(sb * P.r);
             const uint32_t p_tmem = tmem + uint32_t(P.dist_col0 + cp.db * kBN);
+            // K of warpgroup k/4 sits in its first 32 columns, 8 columns per 16 K;
+            // R rows of K step k: box k/4, 32 bytes per step inside the box
+            mma_ts_w(s_tmem, p_tmem, r_lo, kSdescHiSw128, idesc_p, cp.first ? 0u : 1u);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                // K of warpgroup k/4 sits in its first 32 columns, 8 columns per 16 K
-                const uint32_t a_t = p_tmem + uint32_t((k >> 2) * 64 + (k & 3) * 8);
-                const uint32_t roff = uint32_t((k >> 2) * P.r * 128 + (k & 3) * 32);
-                mma_ts(s_tmem, a_t, sdesc_k_sw128(r_base + roff), idesc_p, (cp.first && k == 0) ? 0u : 1u);
-            }
+            for (int k = 1; k < 8; ++k)
+                mma_ts_w(s_tmem, p_tmem + uint32_t((k >> 2) * 64 + (k & 3) * 8),
+                         r_lo + uint32_t(k >> 2) * rbox_units + uint32_t((k & 3) * 2), kSdescHiSw128, idesc_p, 1u);
             if (P.split_k) {
                 // K_lo sits 32 columns after K_hi
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t a_t = p_tmem + uint32_t((k >> 2) * 64 + 32 + (k & 3) * 8);
-                    const uint32_t roff = uint32_t((k >> 2) * P.r * 128 + (k & 3) * 32);
-                    mma_ts(s_tmem, a_t, sdesc_k_sw128(r_base + roff), idesc_p, 1u);
-                }
+                for (int k = 0; k < 8; ++k)
+                    mma_ts_w(s_tmem, p_tmem + uint32_t((k >> 2) * 64 + 32 + (k & 3) * 8),
+                             r_lo + uint32_t(k >> 2) * rbox_units + uint32_t((k & 3) * 2), kSdescHiSw128, idesc_p,
+                             1u);
             }
-            tc_commit(&bars[BAR_EMPTY + cp.stage]);
+            if (PAIR) tc_commit_mc(&bars[BAR_EMPTY + cp.stage], uint16_t(3));
+            else tc_commit(&bars[BAR_EMPTY + cp.stage]);
             if (cp.last) tc_commit(&bars[BAR_SFULL + sb]);
         }
         // Drain: every MMA issued has completed before tensor memory is freed.
@@ -434,9 +493,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             c.flags(nloc);
             if (c.first) ++c.seg;
             const uint32_t base = tmem + lane_off + uint32_t(P.dist_col0 + c.db * kBN + 64 * g);
-            const int64_t i = int64_t(c.rt) * kBM + 32 * q + lane;
+            const int rt = row_tile(c.rt);
+            const int64_t i = int64_t(rt) * kBM + 32 * q + lane;
             uint32_t mlo = 0, mhi = 0;
-            if (P.leaf_a != nullptr || P.grp_a != nullptr) tile_mask(P, c.rt, c.ct, g, i, mlo, mhi);
+            if ((P.leaf_a != nullptr || P.grp_a != nullptr) && int64_t(rt) * kBM < P.ma)
+                tile_mask(P, rt, c.ct, g, i, mlo, mhi);
             tmem_wait_ld_regs(va);                 // chunk 0 of this tile
             tmem_ld32(base + 32, vb);              // chunk 1 in flight
             uint32_t pk[16];
@@ -486,6 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 2) tmem_dealloc(tmem, 512);
+    if (PAIR) cluster_sync();  // neither CTA exits while the other may still signal it
 }
 
 }  // namespace tc
@@ -511,9 +573,10 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D FP16 tensor map: `cols` contiguous elements per row (row stride
-// ld_elems), box of box_cols x box_rows with the 128-byte swizzle.
+// ld_elems), box of box_cols x box_rows with the 128-byte swizzle (or the
+// 64-byte one for 32-element boxes).
 int make_map(CUtensorMap *m, const void *base, int64_t cols, int64_t rows, int64_t ld_elems, int box_cols,
-             int box_rows) {
+             int box_rows, bool swizzle64 = false) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(KRR_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
@@ -521,7 +584,8 @@ int make_map(CUtensorMap *m, const void *base, int64_t cols, int64_t rows, int64
     cuuint32_t box[2] = {cuuint32_t(box_cols), cuuint32_t(box_rows)};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(KRR_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(int(r)) + ")");
     return KRR_OK;
@@ -531,7 +595,8 @@ int make_map(CUtensorMap *m, const void *base, int64_t cols, int64_t rows, int64
 
 // S (+)= W o K(XA rows, XB rows) RT^T, accumulated atomically into S
 // (which the caller zeroes).  XA, XB: augmented FP16 rows (Kpad = 64 *
-// nchunk elements each); RT: FP16, rpad x ldrt (row c = column c of R).
+// nchunk elements each, or 32 when nchunk = 1 and kmma <= 2: the rows of
+// d <= 8); RT: FP16, rpad x ldrt (row c = column c of R).
 int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
                      const int32_t *leaf_b, float *S, int64_t lds, bool split_k, const BlockDiag *bd) {
@@ -540,9 +605,10 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     if (ma <= 0 || nb <= 0) return KRR_OK;
     if (ldrt % 8 != 0) return fail(KRR_ERR_INVALID_ARG, "sample_tc: ldrt must be a multiple of 8");
     CUtensorMap mA, mB, mR;
-    const int kpad = 64 * nchunk;
-    KRR_TRY(make_map(&mA, XA, kpad, ma, kpad, 64, tc::kBM));
-    KRR_TRY(make_map(&mB, XB, kpad, nb, kpad, 64, tc::kBN));
+    const bool narrow = nchunk == 1 && kmma <= 2;
+    const int kpad = narrow ? 32 : 64 * nchunk, box_k = narrow ? 32 : 64;
+    KRR_TRY(make_map(&mA, XA, kpad, ma, kpad, box_k, tc::kBM, narrow));
+    KRR_TRY(make_map(&mB, XB, kpad, nb, kpad, box_k, tc::kBN, narrow));
     KRR_TRY(make_map(&mR, RT, nb, rpad, ldrt, 64, rpad));
 
     tc::Params P{};
@@ -562,11 +628,16 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     if (P.dist_col0 < 128) P.dist_col0 = 128;
     P.ndist = (512 - P.dist_col0) / 128;
     if (P.ndist > 3) P.ndist = 3;
-    const uint32_t a_bytes = nchunk * tc::kChunkBytes;
+    P.chunk_bytes = narrow ? tc::kChunkBytes / 2 : tc::kChunkBytes;
+    P.ab_hi = narrow ? ptx::kSdescHiSw64 : ptx::kSdescHiSw128;
+    const uint32_t a_bytes = nchunk * P.chunk_bytes;
     P.stage_bytes = a_bytes + 2 * rpad * 128;
     const int budget = 227 * 1024 - 1024 - 256;  // alignment slack + barriers
-    // two row-tile buffers when they fit beside two stages, else one
-    P.a_bufs = (2 * a_bytes + 2 * P.stage_bytes <= uint32_t(budget)) ? 2 : 1;
+    // two row-tile buffers (the next row tile loads while the current one
+    // is in use), unless a single buffer makes room for a third stage
+    const int ns2 = int((budget - 2 * int(a_bytes)) / int(P.stage_bytes));
+    const int ns1 = int((budget - int(a_bytes)) / int(P.stage_bytes));
+    P.a_bufs = (ns2 >= 3 || (ns2 >= 2 && ns1 == ns2)) ? 2 : 1;
     P.off_a = 0;
     P.off_stage = P.a_bufs * a_bytes;
     int ns = int((budget - int(P.off_stage)) / int(P.stage_bytes));
@@ -598,13 +669,51 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     P.status = c->status;
     P.wait = c->wait_cycles;
 
-    static SmemLimitOnce smem_limit;
-    KRR_CUDA(raise_smem_limit(smem_limit, c->device, tc::sample_tc_kernel, 227 * 1024));
-    const int64_t T = P.n_tiles;
-    if (T <= 0) return KRR_OK;
-    const int grid = int(T < c->num_sms ? T : c->num_sms);
-    { tc::sample_tc_kernel<<<grid, tc::kThreads, smem, c->stream>>>(mA, mB, mR, P); ::krr::count_launch(); }
-    KRR_CUDA(cudaGetLastError());
+    static SmemLimitOnce smem_single, smem_pair;
+    if (P.n_tiles <= 0) return KRR_OK;
+    // Pairs of row tiles share every column tile's loads (clusters of two
+    // CTAs, multicast); block-diagonal tile lists keep one row tile per CTA.
+#ifndef KRR_PAIR_OFF
+    const bool pair = bd == nullptr && P.n_row_tiles >= 2;
+#else
+    const bool pair = false;
+#endif
+    if (!pair) {
+        KRR_CUDA(raise_smem_limit(smem_single, c->device, tc::sample_tc_kernel<false>, 227 * 1024));
+        const int64_t T = P.n_tiles;
+        const int grid = int(T < c->num_sms ? T : c->num_sms);
+        { tc::sample_tc_kernel<false><<<grid, tc::kThreads, smem, c->stream>>>(mA, mB, mR, P); ::krr::count_launch(); }
+        KRR_CUDA(cudaGetLastError());
+        return KRR_OK;
+    }
+    KRR_CUDA(raise_smem_limit(smem_pair, c->device, tc::sample_tc_kernel<true>, 227 * 1024));
+    KRR_TRY(make_map(&mB, XB, kpad, nb, kpad, box_k, tc::kBN / 2, narrow));  // half-tile boxes
+    P.n_row_tiles = cdiv(P.n_row_tiles, 2);  // row units of two row tiles
+    P.n_tiles = P.n_row_tiles * P.n_col_tiles;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(tc::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // clusters that can be resident at once (one CTA per SM), per device
+    static std::atomic<int> max_clusters[kMaxDevices];
+    int mc = (c->device >= 0 && c->device < kMaxDevices) ? max_clusters[c->device].load() : 0;
+    if (mc <= 0) {
+        cfg.gridDim = dim3(2 * (c->num_sms / 2));
+        KRR_CUDA(cudaOccupancyMaxActiveClusters(&mc, tc::sample_tc_kernel<true>, &cfg));
+        if (mc <= 0) return fail(KRR_ERR_CUDA, "sample_tc: no cluster of two CTAs fits on the device");
+        if (c->device >= 0 && c->device < kMaxDevices) max_clusters[c->device].store(mc);
+    }
+    const int64_t units = P.n_tiles < mc ? P.n_tiles : mc;
+    cfg.gridDim = dim3(unsigned(2 * units));
+    KRR_CUDA(cudaLaunchKernelEx(&cfg, tc::sample_tc_kernel<true>, mA, mB, mR, P));
+    ::krr::count_launch();
     return KRR_OK;
 }
 
