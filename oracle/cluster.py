@@ -207,6 +207,150 @@ def two_means_tree(X32: np.ndarray, leaf: int, seed: int):
     return perm.astype(np.int32), tree, {"centre_updates": iters, "quant_exp": k}
 
 
+def _build_tree(q, leaf, split):
+    """Recursive divisive ordering shared by the KD and PCA readings:
+    split(q_rows) -> int8 labels (0 = first child); a split with an empty
+    side becomes halves.  Stable partition, postorder numbering."""
+    n = q.shape[0]
+    q = q.copy()
+    perm = np.arange(n, dtype=np.int64)
+    tree = Tree()
+
+    def build(b, e, lev):
+        m = e - b
+        if m <= leaf:
+            return tree.add(b, e, -1, -1, lev)
+        labels = split(q[b:e])
+        c1 = int(labels.sum())
+        if c1 == 0 or c1 == m:
+            labels = (np.arange(m) >= m // 2).astype(np.int8)
+        order = np.concatenate([np.nonzero(labels == 0)[0], np.nonzero(labels == 1)[0]])
+        q[b:e] = q[b:e][order]
+        perm[b:e] = perm[b:e][order]
+        c0 = int(np.count_nonzero(labels == 0))
+        l = build(b, b + c0, lev + 1)
+        r = build(b + c0, e, lev + 1)
+        return tree.add(b, e, l, r, lev)
+
+    old = sys.getrecursionlimit()
+    sys.setrecursionlimit(max(old, 4 * n // max(leaf, 1) + 1000))
+    try:
+        if n > 0:
+            build(0, n, 0)
+    finally:
+        sys.setrecursionlimit(old)
+    return perm.astype(np.int32), tree
+
+
+KD_UNBALANCED = 100  # mean split rejected when 100 * |smaller side| < |larger side|
+
+
+def kd_split(q: np.ndarray) -> np.ndarray:
+    """k-d tree split of one node (Section 4.3, "K-d tree"): the coordinate
+    of maximum spread (read as max - min of the quantized coordinates;
+    lowest index on ties), split at its mean (a point goes to the first
+    child iff its value is <= the mean, i.e. q * m <= sum q, exact in
+    integers); if 100 * |smaller side| < |larger side| the split moves to
+    the median: the floor(m / 2) smallest values go first, ties by row
+    order.  All points identical: halves."""
+    m = q.shape[0]
+    spread = q.max(axis=0) - q.min(axis=0)
+    k = int(np.argmax(spread))                  # first maximum
+    if spread[k] == 0:
+        return (np.arange(m) >= m // 2).astype(np.int8)
+    col = q[:, k]
+    tot = int(col.sum())
+    labels = np.array([0 if int(v) * m <= tot else 1 for v in col], dtype=np.int8)
+    c1 = int(labels.sum())
+    c0 = m - c1
+    if KD_UNBALANCED * min(c0, c1) < max(c0, c1):
+        rank = np.lexsort((np.arange(m), col))   # by value, then row order
+        labels = np.ones(m, dtype=np.int8)
+        labels[rank[: m // 2]] = 0
+    return labels
+
+
+PCA_POWER_ITERS = 64
+
+
+def pca_direction(q: np.ndarray):
+    """First principal direction of the node's quantized points (Section
+    4.3, "Principal component analysis"), as a fixed sequence of IEEE FP64
+    operations (no fused multiply-add), so every implementation that follows
+    it gets the same bits:
+      mu_a  = double(sum_i q_ia) / m
+      C_ab  = double(sum_i q_ia q_ib) / m - mu_a * mu_b   (sums exact in int64)
+      v     = e_0 ... then PCA_POWER_ITERS times w = C v (sum over b in
+              order), v = w / sqrt(sum_a w_a^2); stop early if w = 0;
+      sign: the entry of largest magnitude (lowest index on ties) positive.
+    Returns (mu, v); v is None when C is zero (all points identical)."""
+    m, d = q.shape
+    s = [int(q[:, a].sum()) for a in range(d)]
+    mu = [float(s[a]) / float(m) for a in range(d)]
+    C = [[0.0] * d for _ in range(d)]
+    zero = True
+    for a in range(d):
+        for b in range(d):
+            sab = int(np.dot(q[:, a], q[:, b]))           # exact: |sum| < 2^63 by the quantization
+            C[a][b] = float(sab) / float(m) - mu[a] * mu[b]
+            zero = zero and C[a][b] == 0.0
+    if zero:
+        return mu, None
+    v = [1.0] + [0.0] * (d - 1)
+    for _ in range(PCA_POWER_ITERS):
+        w = [0.0] * d
+        for a in range(d):
+            acc = 0.0
+            for b in range(d):
+                acc = acc + C[a][b] * v[b]
+            w[a] = acc
+        nrm = 0.0
+        for a in range(d):
+            nrm = nrm + w[a] * w[a]
+        if nrm == 0.0:
+            break
+        nrm = math.sqrt(nrm)
+        v = [w[a] / nrm for a in range(d)]
+    big = 0
+    for a in range(1, d):
+        if abs(v[a]) > abs(v[big]):
+            big = a
+    if v[big] < 0:
+        v = [-x for x in v]
+    return mu, v
+
+
+def pca_split(q: np.ndarray) -> np.ndarray:
+    """PCA split of one node: a point goes to the first child iff its
+    projection onto the principal direction, relative to the mean, is
+    <= 0: p_i = sum_a (double(q_ia) - mu_a) * v_a, summed over a in order."""
+    m, d = q.shape
+    mu, v = pca_direction(q)
+    if v is None:
+        return (np.arange(m) >= m // 2).astype(np.int8)
+    p = np.zeros(m)
+    for a in range(d):
+        p = p + (q[:, a].astype(np.float64) - mu[a]) * v[a]
+    return (p > 0).astype(np.int8)
+
+
+def kd_tree(X32: np.ndarray, leaf: int):
+    """Recursive k-d tree ordering (KD, Section 4.3).  Returns (perm, tree)."""
+    if leaf < 1:
+        raise ValueError("leaf must be >= 1")
+    q, _ = quantize(X32)
+    return _build_tree(q, leaf, kd_split)
+
+
+def pca_tree(X32: np.ndarray, leaf: int):
+    """Recursive principal-direction ordering (PCA, Section 4.3).  Returns
+    (perm, tree)."""
+    if leaf < 1:
+        raise ValueError("leaf must be >= 1")
+    q, _ = quantize(X32)
+    return _build_tree(q, leaf, pca_split)
+
+
 def natural_tree(n: int, leaf: int):
     """No preprocessing (NP, Section 4.3): natural order, halves (+-1)."""
     tree = Tree()

@@ -154,3 +154,62 @@ def test_second_seed_frequencies_follow_squared_distance():
         assert p > 1e-3, (f, counts[f], p)
         d1 = np.sqrt(d2)
         assert chisquare(counts[f, others], n_f * d1 / d1.sum()).pvalue < 1e-6
+
+
+def test_kd_split_worked_examples():
+    """k-d split (Section 4.3): coordinate of maximum spread, split at its
+    mean; 100 x smaller side < larger side falls back to the median."""
+    # spread x = 10 > spread y = 5: split x at its mean 4.4 -> {0, 1, 2} | {9, 10}
+    P = np.array([[0, 0], [1, 5], [2, 1], [9, 2], [10, 3]], np.float32)
+    perm, tree = cluster.kd_tree(P, 3)
+    a = tree.arrays()
+    assert tree.n_nodes == 3 and sorted(perm[a["begin"][0]:a["end"][0]].tolist()) == [0, 1, 2]
+    # equal spreads: the lower coordinate; a point exactly at the mean goes first
+    Q = np.array([[0, 4], [2, 0], [4, 2]], np.float32)   # x: 0,2,4 (mean 2), y: 4,0,2 (mean 2)
+    assert cluster.kd_split(cluster.quantize(Q)[0]).tolist() == [0, 0, 1]
+    # 200 zeros and one outlier: the mean split is 200 | 1 (100 * 1 < 200), so the
+    # median split puts the first floor(201 / 2) = 100 rows of the tie first
+    R = np.zeros((201, 1), np.float32)
+    R[150, 0] = 1000.0
+    lab = cluster.kd_split(cluster.quantize(R)[0])
+    assert lab[:100].tolist() == [0] * 100 and lab[100:].sum() == 101
+    # all points identical: halves
+    assert cluster.kd_split(np.zeros((5, 3), np.int64)).tolist() == [0, 0, 1, 1, 1]
+
+
+def test_pca_direction_matches_lapack_eigenvector():
+    """The power iteration of pca_direction reaches the top eigenvector of
+    the node's covariance (numpy.linalg.eigh, a library routine) when the
+    spectrum has a clear gap; the split separates the points by the sign of
+    their projection relative to the mean."""
+    rng = np.random.default_rng(5)
+    for d in (2, 5, 8):
+        X = (rng.standard_normal((400, d)) * np.r_[3.0, np.linspace(1.2, 0.5, d - 1)]).astype(np.float32)
+        q, _ = cluster.quantize(X)
+        mu, v = cluster.pca_direction(q)
+        qf = q.astype(np.float64)
+        C = np.cov(qf.T, bias=True)
+        w, U = np.linalg.eigh(C)
+        u = U[:, -1] * np.sign(U[np.argmax(np.abs(U[:, -1])), -1])
+        assert np.allclose(v, u, atol=1e-9), (d, v, u)
+        lab = cluster.pca_split(q)
+        p = (qf - qf.mean(0)) @ u
+        assert np.array_equal(lab, (p > 0).astype(np.int8)) or np.min(np.abs(p)) < 1e-6 * np.abs(p).max()
+    # identical points: no direction, halves
+    assert cluster.pca_direction(np.ones((4, 3), np.int64))[1] is None
+    assert cluster.pca_split(np.ones((4, 3), np.int64)).tolist() == [0, 0, 1, 1]
+
+
+@pytest.mark.parametrize("name", ["kd_tree", "pca_tree"])
+def test_kd_and_pca_tree_invariants(name):
+    X = synth.mixture(3000, 6, 8, 0.7, 9)[0].astype(np.float32)
+    perm, tree = getattr(cluster, name)(X, 64)
+    _tree_ok(perm, tree, 3000, 64)
+
+
+def test_natural_order_halves():
+    perm, tree = cluster.natural_tree(1000, 64)
+    _tree_ok(perm, tree, 1000, 64)
+    a = tree.arrays()
+    sizes = (a["end"] - a["begin"])[a["left"] < 0]
+    assert sizes.max() - sizes.min() <= 1 and np.array_equal(perm, np.arange(1000))
