@@ -143,6 +143,33 @@ int krr_cluster(krr_ctx *ctx, const float *X, int64_t n, int32_t d,
                 int32_t leaf, uint64_t seed, int32_t *perm,
                 int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes);
 
+/* The orderings Section 4.3 compares (same outputs and conventions as
+ * krr_cluster, which is ordering KRR_ORDER_TWO_MEANS):
+ *   KRR_ORDER_NATURAL  no preprocessing (NP): the input order, every node
+ *                      split into halves (first floor(m/2) rows first);
+ *   KRR_ORDER_KD       k-d tree: split along the coordinate of maximum
+ *                      spread (max - min of the quantized coordinates,
+ *                      lowest coordinate on ties) at its mean (a row goes
+ *                      first iff its value <= the mean, exact in integers);
+ *                      when 100 x the smaller side < the larger side, at
+ *                      the median (the floor(m/2) smallest values first,
+ *                      ties in row order);
+ *   KRR_ORDER_PCA      principal direction: split at the mean of the
+ *                      projections onto the node's first principal
+ *                      direction (covariance from exact integer sums, 64
+ *                      power iterations from e_0, fixed round-to-nearest FP64
+ *                      operation order, largest entry made positive; a row
+ *                      goes first iff its projection <= 0); d <= 64.
+ * A split that leaves one side empty becomes halves; seed is used by
+ * two-means only.  Synchronizes. */
+#define KRR_ORDER_TWO_MEANS 0
+#define KRR_ORDER_NATURAL 1
+#define KRR_ORDER_KD 2
+#define KRR_ORDER_PCA 3
+int krr_order(krr_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t leaf,
+              int32_t ordering, uint64_t seed, int32_t *perm,
+              int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes);
+
 /* Batched form: the rows of X split into nprob contiguous problems
  * (offsets: host int64[nprob + 1], offsets[0] = 0, offsets[nprob] = n, every
  * problem non-empty).  The top of the tree is a balanced binary tree over
@@ -232,6 +259,8 @@ typedef struct {
     uint64_t seed;     /* seeds clustering and the random block             */
     int32_t precision; /* krr_precision                                     */
     int32_t flags;     /* KRR_TRUNCATE_AT_RMAX | KRR_LAMBDA_TOL, or 0       */
+    int32_t ordering;  /* KRR_ORDER_* (default two-means, Section 4.3)      */
+    int32_t pad;
 } krr_options;
 
 /* krr_options.flags: when the ranks are not revealed within r_max samples,
@@ -249,7 +278,8 @@ typedef struct {
 #define KRR_LAMBDA_TOL 2
 
 /* Fill opts with defaults: eps_c 0.03, eps_abs 0, leaf 128, r0 64, p 10,
- * r_max 2048, seed 1, KRR_MIXED, flags 0; h and lambda set to 1. */
+ * r_max 2048, seed 1, KRR_MIXED, flags 0, two-means ordering; h and lambda
+ * set to 1. */
 void krr_default_options(krr_options *opts);
 
 /* Cluster X (device float n x d, original order, already standardized if

@@ -22,6 +22,7 @@ STATUS = {0: "KRR_OK", 1: "KRR_ERR_INVALID_ARG", 2: "KRR_ERR_NONFINITE_INPUT", 3
 KRR_TRUNCATE_AT_RMAX = 1
 KRR_LAMBDA_TOL = 2
 KRR_MIXED, KRR_FP64 = 0, 1
+KRR_ORDER_TWO_MEANS, KRR_ORDER_NATURAL, KRR_ORDER_KD, KRR_ORDER_PCA = 0, 1, 2, 3
 
 P = ctypes.c_void_p
 i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
@@ -39,7 +40,8 @@ class krr_tree_arrays(ctypes.Structure):
 
 class krr_options(ctypes.Structure):
     _fields_ = [("h", f64), ("lam", f64), ("eps_c", f64), ("eps_abs", f64), ("leaf", i32), ("r0", i32),
-                ("p", i32), ("r_max", i32), ("seed", u64), ("precision", i32), ("flags", i32)]
+                ("p", i32), ("r_max", i32), ("seed", u64), ("precision", i32), ("flags", i32), ("ordering", i32),
+                ("pad", i32)]
 
 
 class krr_hss_stats(ctypes.Structure):
@@ -59,6 +61,7 @@ SIGNATURES = {
     "krr_probe_rate": (i32, [P, i32, ctypes.POINTER(f64)]),
     "krr_standardize": (i32, [P, P, i64, i32, P, i64, P, P]),
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),
+    "krr_order": (i32, [P, P, i64, i32, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),
     "krr_cluster_batched": (i32, [P, P, i64, i32, i32, P, i32, u64, P, i32, krr_tree_arrays,
                                   ctypes.POINTER(i32)]),
     "krr_sample": (i32, [P, P, i64, P, i64, i32, f64, f64, P, i32, i64, P, P, P, i64]),

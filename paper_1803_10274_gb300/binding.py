@@ -11,9 +11,11 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_TRUNCATE_AT_RMAX, KRRError, check, lib
+from ._lib import (KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_ORDER_KD, KRR_ORDER_NATURAL, KRR_ORDER_PCA,
+                   KRR_ORDER_TWO_MEANS, KRR_TRUNCATE_AT_RMAX, KRRError, check, lib)
 
-__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "krr_standardize", "krr_cluster", "krr_sample",
+__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "KRR_ORDER_TWO_MEANS",
+           "KRR_ORDER_NATURAL", "KRR_ORDER_KD", "KRR_ORDER_PCA", "krr_order", "krr_standardize", "krr_cluster", "krr_sample",
            "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "krr_one_vs_all", "HSS", "hss_compress", "default_options",
            "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]
 
@@ -117,6 +119,20 @@ def krr_cluster(ctx, X, leaf, seed):
     ta = _lib.krr_tree_arrays(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for k, v in arrs.items()})
     nn = ctypes.c_int32()
     check(lib().krr_cluster(ctx.h, _ptr(X), n, d, leaf, seed, _ptr(perm), cap, ta, ctypes.byref(nn)))
+    return perm, {k: v[:nn.value].copy() for k, v in arrs.items()}
+
+
+def krr_order(ctx, X, leaf, ordering, seed=1):
+    """Ordering of Section 4.3 (KRR_ORDER_*): (perm, tree dict) as krr_cluster."""
+    import numpy as np
+    _need(X, torch.float32, "X")
+    n, d = X.shape
+    perm = torch.empty(n, dtype=torch.int32, device=X.device)
+    cap = max(2 * n, 1)
+    arrs = {k: np.zeros(cap, np.int32) for k in ("begin", "end", "left", "right", "parent", "level")}
+    ta = _lib.krr_tree_arrays(**{k: v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for k, v in arrs.items()})
+    nn = ctypes.c_int32()
+    check(lib().krr_order(ctx.h, _ptr(X), n, d, leaf, ordering, seed, _ptr(perm), cap, ta, ctypes.byref(nn)))
     return perm, {k: v[:nn.value].copy() for k, v in arrs.items()}
 
 

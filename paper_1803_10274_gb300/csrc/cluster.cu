@@ -420,6 +420,259 @@ __global__ void mark_nodes_kernel(int nn, const int64_t *nbeg, const int64_t *ns
     for (int64_t i = nbeg[v] + threadIdx.x; i < nbeg[v] + nsize[v]; i += blockDim.x) node_of[i] = v;
 }
 
+// ------------------------------------------------ other orderings
+// Section 4.3 compares two-means with no preprocessing (NP: halves in the
+// natural order), a k-d tree (split along the coordinate of maximum spread
+// at its mean, the median when that leaves one side 100 times larger) and
+// the principal direction (split at the mean of the projections).  All
+// three run on the same quantized coordinates and level loop as two-means.
+// k-d: spread = max - min of the integer coordinates (lowest coordinate on
+// ties), a point goes first iff q m <= sum q (exact).  PCA: a fixed
+// sequence of round-to-nearest FP64 operations (no contraction into FMA),
+// so the decision is the same in any implementation that follows it.
+
+// Generic labels -> "goes first" flags; halves where flagged.
+__global__ void finalize_generic_kernel(int64_t n, const int32_t *node_of, const int64_t *nbeg, const int64_t *nsize,
+                                        const int *halved, int8_t *label, int32_t *zero_flag) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    if (v < 0) {
+        zero_flag[i] = 0;
+        return;
+    }
+    int lab = label[i];
+    if (halved[v]) {
+        lab = (i - nbeg[v]) >= nsize[v] / 2 ? 1 : 0;
+        label[i] = int8_t(lab);
+    }
+    zero_flag[i] = lab == 0 ? 1 : 0;
+}
+
+__global__ void count_second_kernel(int64_t n, const int32_t *node_of, const int8_t *label, int *c1) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    if (v >= 0 && label[i]) atomicAdd(&c1[v], 1);
+}
+
+// A split that leaves one side empty becomes halves.
+__global__ void empty_side_kernel(int nn, const int64_t *nsize, const int *c1, int *halved) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    if (c1[v] == 0 || c1[v] == nsize[v]) halved[v] = 1;
+}
+
+__global__ void kd_stats_kernel(const int64_t *q, int d, int64_t n, const int32_t *node_of, long long *nmin,
+                                long long *nmax, unsigned long long *nsum) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * d) return;
+    const int64_t i = e / d;
+    const int a = int(e % d);
+    const int32_t v = node_of[i];
+    if (v < 0) return;
+    const long long x = q[e];
+    atomicMin(&nmin[int64_t(v) * d + a], x);
+    atomicMax(&nmax[int64_t(v) * d + a], x);
+    atomicAdd(&nsum[int64_t(v) * d + a], static_cast<unsigned long long>(x));
+}
+
+__global__ void kd_choose_kernel(int nn, int d, const long long *nmin, const long long *nmax,
+                                 const unsigned long long *nsum, int *kdim, long long *ksum, int *halved,
+                                 long long *lo, long long *hi) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    long long best = -1;
+    int bk = 0;
+    for (int a = 0; a < d; ++a) {
+        const long long sp = nmax[int64_t(v) * d + a] - nmin[int64_t(v) * d + a];
+        if (sp > best) {
+            best = sp;
+            bk = a;
+        }
+    }
+    kdim[v] = bk;
+    ksum[v] = static_cast<long long>(nsum[int64_t(v) * d + bk]);
+    halved[v] = best == 0 ? 1 : 0;
+    lo[v] = nmin[int64_t(v) * d + bk];
+    hi[v] = nmax[int64_t(v) * d + bk];
+}
+
+__global__ void kd_label_kernel(int64_t n, int d, const int64_t *q, const int32_t *node_of, const int64_t *nsize,
+                                const int *kdim, const long long *ksum, int8_t *label, int *c1) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    if (v < 0) return;
+    const long long x = q[i * d + kdim[v]];
+    const int lab = x * nsize[v] <= ksum[v] ? 0 : 1;
+    label[i] = int8_t(lab);
+    if (lab) atomicAdd(&c1[v], 1);
+}
+
+// 100 x the smaller side below the larger one: the median split is needed.
+__global__ void kd_balance_kernel(int nn, const int64_t *nsize, const int *c1, const int *halved, int *need,
+                                  int *any) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    const int64_t c0 = nsize[v] - c1[v];
+    const int64_t small = c0 < c1[v] ? c0 : c1[v], large = c0 < c1[v] ? c1[v] : c0;
+    need[v] = (!halved[v] && 100 * small < large) ? 1 : 0;
+    if (need[v]) atomicAdd(any, 1);
+}
+
+// Bisection for the smallest value v* with count(x <= v*) >= floor(m / 2)
+// in the nodes that need the median (exact, order-free counts).
+__global__ void kd_med_count_kernel(int64_t n, int d, const int64_t *q, const int32_t *node_of, const int *kdim,
+                                    const int *need, const long long *lo, const long long *hi, int *cnt,
+                                    int strict) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    if (v < 0 || !need[v]) return;
+    const long long x = q[i * d + kdim[v]];
+    // strict = 0: count x <= mid (mid = lo + (hi - lo) / 2); strict = 1: count x < lo
+    const long long mid = lo[v] + ((hi[v] - lo[v]) >> 1);
+    if (strict ? x < lo[v] : x <= mid) atomicAdd(&cnt[v], 1);
+}
+__global__ void kd_med_step_kernel(int nn, const int64_t *nsize, const int *need, long long *lo, long long *hi,
+                                   int *cnt) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nn) return;
+    if (need[v] && lo[v] < hi[v]) {
+        const long long mid = lo[v] + ((hi[v] - lo[v]) >> 1);
+        if (cnt[v] >= nsize[v] / 2) hi[v] = mid;
+        else lo[v] = mid + 1;
+    }
+    cnt[v] = 0;
+}
+// flags of the rows equal to v* (ranked by a scan), then the median labels:
+// x < v* first, and the first floor(m / 2) - count(x < v*) rows equal to v*
+__global__ void kd_med_eq_kernel(int64_t n, int d, const int64_t *q, const int32_t *node_of, const int *kdim,
+                                 const int *need, const long long *lo, int32_t *eq) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    eq[i] = (v >= 0 && need[v] && q[i * d + kdim[v]] == lo[v]) ? 1 : 0;
+}
+__global__ void kd_med_label_kernel(int64_t n, int d, const int64_t *q, const int32_t *node_of, const int64_t *nbeg,
+                                    const int64_t *nsize, const int *kdim, const int *need, const long long *lo,
+                                    const int *cless, const int64_t *eqscan, int8_t *label) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    if (v < 0 || !need[v]) return;
+    const long long x = q[i * d + kdim[v]];
+    const int64_t room = nsize[v] / 2 - cless[v];
+    const int64_t rank = eqscan[i] - eqscan[nbeg[v]];
+    label[i] = int8_t((x < lo[v] || (x == lo[v] && rank < room)) ? 0 : 1);
+}
+
+// Exact integer sums of one node's coordinates and their products: a CTA
+// walks a contiguous range of rows (which may cross node boundaries) and
+// adds its partial sums to the node at each boundary.  Entry p < d*d is
+// the pair (p / d, p % d), entry d*d + a the coordinate a.
+constexpr int kPcaRows = 1024;
+constexpr int kPcaMaxD = 64;
+__global__ void pca_sums_kernel(const int64_t *q, int d, int64_t n, const int32_t *node_of,
+                                unsigned long long *sums) {
+    const int64_t r0 = int64_t(blockIdx.x) * kPcaRows, r1 = min(n, r0 + kPcaRows);
+    const int np = d * d + d;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const int a = p < d * d ? p / d : p - d * d, b = p < d * d ? p % d : -1;
+        long long acc = 0;
+        int32_t cur = -1;
+        for (int64_t i = r0; i < r1; ++i) {
+            const int32_t v = node_of[i];
+            if (v != cur) {
+                if (cur >= 0 && acc) atomicAdd(&sums[int64_t(cur) * np + p], static_cast<unsigned long long>(acc));
+                acc = 0;
+                cur = v;
+            }
+            if (v < 0) continue;
+            const long long x = q[i * d + a];
+            acc += b < 0 ? x : x * q[i * d + b];
+        }
+        if (cur >= 0 && acc) atomicAdd(&sums[int64_t(cur) * np + p], static_cast<unsigned long long>(acc));
+    }
+}
+
+// One CTA per node, thread a <-> coordinate a: mean, covariance and the
+// power iteration in the prescribed order of rounded operations.
+constexpr int kPcaIters = 64;
+__global__ void pca_direction_kernel(int d, const int64_t *nsize, const unsigned long long *sums, double *mu_out,
+                                     double *v_out, int *halved) {
+    __shared__ double C[kPcaMaxD][kPcaMaxD + 1];
+    __shared__ double mu[kPcaMaxD], v[kPcaMaxD], w[kPcaMaxD];
+    __shared__ double nrm;
+    __shared__ int zero;
+    const int node = blockIdx.x, a = threadIdx.x;
+    const int np = d * d + d;
+    const unsigned long long *S = sums + int64_t(node) * np;
+    const double m = double(nsize[node]);
+    if (a == 0) zero = 1;
+    if (a < d) mu[a] = __ddiv_rn(__ll2double_rn(static_cast<long long>(S[d * d + a])), m);
+    __syncthreads();
+    if (a < d) {
+        for (int b = 0; b < d; ++b) {
+            const double c = __dsub_rn(__ddiv_rn(__ll2double_rn(static_cast<long long>(S[a * d + b])), m),
+                                       __dmul_rn(mu[a], mu[b]));
+            C[a][b] = c;
+            if (c != 0.0) zero = 0;
+        }
+        v[a] = a == 0 ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (zero) {
+        if (a == 0) halved[node] = 1;
+        return;
+    }
+    for (int it = 0; it < kPcaIters; ++it) {
+        if (a < d) {
+            double acc = 0.0;
+            for (int b = 0; b < d; ++b) acc = __dadd_rn(acc, __dmul_rn(C[a][b], v[b]));
+            w[a] = acc;
+        }
+        __syncthreads();
+        if (a == 0) {
+            double s2 = 0.0;
+            for (int b = 0; b < d; ++b) s2 = __dadd_rn(s2, __dmul_rn(w[b], w[b]));
+            nrm = s2;
+        }
+        __syncthreads();
+        if (nrm == 0.0) break;  // uniform across the block
+        const double r = __dsqrt_rn(nrm);
+        if (a < d) v[a] = __ddiv_rn(w[a], r);
+        __syncthreads();
+    }
+    if (a == 0) {
+        int big = 0;
+        for (int b = 1; b < d; ++b)
+            if (fabs(v[b]) > fabs(v[big])) big = b;
+        nrm = v[big] < 0.0 ? -1.0 : 1.0;
+    }
+    __syncthreads();
+    if (a < d) {
+        mu_out[int64_t(node) * d + a] = mu[a];
+        v_out[int64_t(node) * d + a] = nrm < 0.0 ? -v[a] : v[a];
+    }
+}
+
+__global__ void pca_label_kernel(int64_t n, int d, const int64_t *q, const int32_t *node_of, const double *mu,
+                                 const double *vdir, const int *halved, int8_t *label, int *c1) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = node_of[i];
+    if (v < 0 || halved[v]) return;
+    double p = 0.0;
+    for (int a = 0; a < d; ++a)
+        p = __dadd_rn(p, __dmul_rn(__dsub_rn(__ll2double_rn(q[i * d + a]), mu[int64_t(v) * d + a]),
+                                   vdir[int64_t(v) * d + a]));
+    const int lab = p > 0.0 ? 1 : 0;
+    label[i] = int8_t(lab);
+    if (lab) atomicAdd(&c1[v], 1);
+}
+
 }  // namespace
 
 // Quantization exponent for m points in d dimensions with max |x| = maxabs:
@@ -437,10 +690,14 @@ static int quant_exponent(float maxabs, int d, int64_t m) {
 
 int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, int32_t *perm_out,
             std::vector<int32_t> &tb, std::vector<int32_t> &te, std::vector<int32_t> &tl, std::vector<int32_t> &tr,
-            std::vector<int32_t> &tp, std::vector<int32_t> &tv, const std::vector<int64_t> *segments) {
+            std::vector<int32_t> &tp, std::vector<int32_t> &tv, const std::vector<int64_t> *segments, int method) {
     tb.clear(); te.clear(); tl.clear(); tr.clear(); tp.clear(); tv.clear();
     if (n == 0) return KRR_OK;
     if (d > kMaxD) return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_cluster: d > 1024");
+    if (method < KRR_ORDER_TWO_MEANS || method > KRR_ORDER_PCA)
+        return fail(KRR_ERR_INVALID_ARG, "krr_cluster: unknown ordering");
+    if (method == KRR_ORDER_PCA && d > kPcaMaxD)
+        return fail(KRR_ERR_NOT_IMPLEMENTED, "krr_cluster: the principal-direction ordering supports d <= 64");
     cudaStream_t st = c->stream;
     // segments (one, the whole set, unless given)
     std::vector<int64_t> seg = segments ? *segments : std::vector<int64_t>{0, n};
@@ -528,6 +785,8 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
     }
     DBuf<int32_t> running(c, 1);
     if (!running.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+    DBuf<int32_t> eqflag;
+    if (method == KRR_ORDER_KD && !eqflag.reset(c, n)) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
     while (!active.empty()) {
         const int nn = int(active.size());
         std::vector<int64_t> hb(nn), hs(nn), hbase(nn);
@@ -545,21 +804,88 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         KRR_CUDA(cudaMemcpyAsync(dbase.get(), hbase.data(), nn * 8, cudaMemcpyHostToDevice, st));
         KRR_CUDA(cudaMemsetAsync(node_of.get(), 0xFF, n * 4, st));
         { mark_nodes_kernel<<<nn, kTB, 0, st>>>(nn, db.get(), ds.get(), node_of.get()); ::krr::count_launch(); }
-        { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed, narrow); ::krr::count_launch(); }
-        KRR_CUDA(cudaGetLastError());
-        for (int iter = 0; iter <= kMaxIter; ++iter) {
-            KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
-            { assign_kernel<<<unsigned(cdiv(n, kTB)), kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get(), narrow); ::krr::count_launch(); }
-            { update_kernel<<<unsigned(cdiv(nn, 128)), 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get()); ::krr::count_launch(); }
-            KRR_CUDA(cudaGetLastError());
-            int hrun = 0;
-            KRR_CUDA(cudaMemcpyAsync(&hrun, running.get(), 4, cudaMemcpyDeviceToHost, st));
-            KRR_CUDA(cudaStreamSynchronize(st));
-            if (hrun == 0) break;
-        }
-        { finalize_labels_kernel<<<unsigned(cdiv(n, kTB)), kTB, 0, st>>>(n, node_of.get(), db.get(), ds.get(),
-                                                                        dns.get(), label.get(), zflag.get()); ::krr::count_launch(); }
         const int64_t nblk = cdiv(n, kTB);
+        const unsigned gn = unsigned(cdiv(n, kTB)), gv = unsigned(cdiv(nn, 128));
+        if (method == KRR_ORDER_TWO_MEANS) {
+            { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed, narrow); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+            for (int iter = 0; iter <= kMaxIter; ++iter) {
+                KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
+                { assign_kernel<<<gn, kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get(), narrow); ::krr::count_launch(); }
+                { update_kernel<<<gv, 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get()); ::krr::count_launch(); }
+                KRR_CUDA(cudaGetLastError());
+                int hrun = 0;
+                KRR_CUDA(cudaMemcpyAsync(&hrun, running.get(), 4, cudaMemcpyDeviceToHost, st));
+                KRR_CUDA(cudaStreamSynchronize(st));
+                if (hrun == 0) break;
+            }
+            { finalize_labels_kernel<<<gn, kTB, 0, st>>>(n, node_of.get(), db.get(), ds.get(), dns.get(), label.get(),
+                                                        zflag.get()); ::krr::count_launch(); }
+        } else {
+            DBuf<int> halved(c, nn), c1(c, nn);
+            if (!halved.get() || !c1.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+            KRR_CUDA(cudaMemsetAsync(c1.get(), 0, nn * 4, st));
+            if (method == KRR_ORDER_NATURAL) {
+                std::vector<int> ones(nn, 1);
+                KRR_CUDA(cudaMemcpyAsync(halved.get(), ones.data(), nn * 4, cudaMemcpyHostToDevice, st));
+            } else if (method == KRR_ORDER_KD) {
+                DBuf<long long> nmin(c, size_t(nn) * d), nmax(c, size_t(nn) * d), ksum(c, nn), lo(c, nn), hi(c, nn);
+                DBuf<unsigned long long> nsum(c, size_t(nn) * d);
+                DBuf<int> kdim(c, nn), need(c, nn), cnt(c, nn), any(c, 1);
+                if (!nmin.get() || !nmax.get() || !ksum.get() || !lo.get() || !hi.get() || !nsum.get() || !kdim.get() ||
+                    !need.get() || !cnt.get() || !any.get())
+                    return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+                std::vector<long long> big(size_t(nn) * d, 0x7FFFFFFFFFFFFFFFll), small(size_t(nn) * d, -0x7FFFFFFFFFFFFFFFll - 1);
+                KRR_CUDA(cudaMemcpyAsync(nmin.get(), big.data(), big.size() * 8, cudaMemcpyHostToDevice, st));
+                KRR_CUDA(cudaMemcpyAsync(nmax.get(), small.data(), small.size() * 8, cudaMemcpyHostToDevice, st));
+                KRR_CUDA(cudaMemsetAsync(nsum.get(), 0, size_t(nn) * d * 8, st));
+                KRR_CUDA(cudaMemsetAsync(any.get(), 0, 4, st));
+                KRR_CUDA(cudaMemsetAsync(cnt.get(), 0, nn * 4, st));
+                { kd_stats_kernel<<<unsigned(cdiv(n * d, kTB)), kTB, 0, st>>>(qc, d, n, node_of.get(), nmin.get(), nmax.get(), nsum.get()); ::krr::count_launch(); }
+                { kd_choose_kernel<<<gv, 128, 0, st>>>(nn, d, nmin.get(), nmax.get(), nsum.get(), kdim.get(), ksum.get(),
+                                                       halved.get(), lo.get(), hi.get()); ::krr::count_launch(); }
+                { kd_label_kernel<<<gn, kTB, 0, st>>>(n, d, qc, node_of.get(), ds.get(), kdim.get(), ksum.get(), label.get(), c1.get()); ::krr::count_launch(); }
+                { kd_balance_kernel<<<gv, 128, 0, st>>>(nn, ds.get(), c1.get(), halved.get(), need.get(), any.get()); ::krr::count_launch(); }
+                KRR_CUDA(cudaGetLastError());
+                int hany = 0;
+                KRR_CUDA(cudaMemcpyAsync(&hany, any.get(), 4, cudaMemcpyDeviceToHost, st));
+                KRR_CUDA(cudaStreamSynchronize(st));
+                if (hany) {
+                    // bisection on the value (64 halvings cover any int64 range)
+                    for (int it = 0; it < 64; ++it) {
+                        { kd_med_count_kernel<<<gn, kTB, 0, st>>>(n, d, qc, node_of.get(), kdim.get(), need.get(), lo.get(), hi.get(), cnt.get(), 0); ::krr::count_launch(); }
+                        { kd_med_step_kernel<<<gv, 128, 0, st>>>(nn, ds.get(), need.get(), lo.get(), hi.get(), cnt.get()); ::krr::count_launch(); }
+                    }
+                    { kd_med_count_kernel<<<gn, kTB, 0, st>>>(n, d, qc, node_of.get(), kdim.get(), need.get(), lo.get(), hi.get(), cnt.get(), 1); ::krr::count_launch(); }
+                    { kd_med_eq_kernel<<<gn, kTB, 0, st>>>(n, d, qc, node_of.get(), kdim.get(), need.get(), lo.get(), eqflag.get()); ::krr::count_launch(); }
+                    { scan_blocks_kernel<<<unsigned(nblk), kTB, 0, st>>>(eqflag.get(), n, zscan.get(), bsum.get()); ::krr::count_launch(); }
+                    { scan_sums_kernel<<<1, kTB, 0, st>>>(bsum.get(), nblk); ::krr::count_launch(); }
+                    { scan_add_kernel<<<unsigned(nblk), kTB, 0, st>>>(zscan.get(), n, bsum.get(), nullptr); ::krr::count_launch(); }
+                    { kd_med_label_kernel<<<gn, kTB, 0, st>>>(n, d, qc, node_of.get(), db.get(), ds.get(), kdim.get(), need.get(), lo.get(), cnt.get(), zscan.get(), label.get()); ::krr::count_launch(); }
+                    KRR_CUDA(cudaGetLastError());
+                    // the median labels replace the mean ones: recount the second side
+                    KRR_CUDA(cudaMemsetAsync(c1.get(), 0, nn * 4, st));
+                    { count_second_kernel<<<gn, kTB, 0, st>>>(n, node_of.get(), label.get(), c1.get()); ::krr::count_launch(); }
+                }
+            } else {  // KRR_ORDER_PCA
+                const int np = d * d + d;
+                DBuf<unsigned long long> sums(c, size_t(nn) * np);
+                DBuf<double> mu(c, size_t(nn) * d), vdir(c, size_t(nn) * d);
+                if (!sums.get() || !mu.get() || !vdir.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+                KRR_CUDA(cudaMemsetAsync(sums.get(), 0, size_t(nn) * np * 8, st));
+                KRR_CUDA(cudaMemsetAsync(halved.get(), 0, nn * 4, st));
+                { pca_sums_kernel<<<unsigned(cdiv(n, kPcaRows)), kTB, 0, st>>>(qc, d, n, node_of.get(), sums.get()); ::krr::count_launch(); }
+                { pca_direction_kernel<<<nn, kPcaMaxD, 0, st>>>(d, ds.get(), sums.get(), mu.get(), vdir.get(), halved.get()); ::krr::count_launch(); }
+                { pca_label_kernel<<<gn, kTB, 0, st>>>(n, d, qc, node_of.get(), mu.get(), vdir.get(), halved.get(), label.get(), c1.get()); ::krr::count_launch(); }
+                KRR_CUDA(cudaGetLastError());
+            }
+            if (method != KRR_ORDER_NATURAL)
+                { empty_side_kernel<<<gv, 128, 0, st>>>(nn, ds.get(), c1.get(), halved.get()); ::krr::count_launch(); }
+            { finalize_generic_kernel<<<gn, kTB, 0, st>>>(n, node_of.get(), db.get(), ds.get(), halved.get(), label.get(),
+                                                         zflag.get()); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+            KRR_CUDA(cudaStreamSynchronize(st));  // the level's scratch is freed at the end of this block
+        }
         { scan_blocks_kernel<<<unsigned(nblk), kTB, 0, st>>>(zflag.get(), n, zscan.get(), bsum.get()); ::krr::count_launch(); }
         { scan_sums_kernel<<<1, kTB, 0, st>>>(bsum.get(), nblk); ::krr::count_launch(); }
         { scan_add_kernel<<<unsigned(nblk), kTB, 0, st>>>(zscan.get(), n, bsum.get(), nullptr); ::krr::count_launch(); }
@@ -627,12 +953,12 @@ using namespace krr;
 
 static int cluster_entry(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t leaf, uint64_t seed,
                          int32_t *perm, int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes,
-                         const std::vector<int64_t> *seg) {
+                         const std::vector<int64_t> *seg, int method = KRR_ORDER_TWO_MEANS) {
     if (!k || (n > 0 && (!X || !perm)) || n < 0 || d <= 0 || leaf < 1 || !n_nodes)
         return fail(KRR_ERR_INVALID_ARG, "krr_cluster: bad arguments");
     if (n > 0x7FFFFFFF) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: n too large");
     std::vector<int32_t> tb, te, tl, tr, tp, tv;
-    KRR_TRY(cluster(&k->c, X, n, d, leaf, seed, perm, tb, te, tl, tr, tp, tv, seg));
+    KRR_TRY(cluster(&k->c, X, n, d, leaf, seed, perm, tb, te, tl, tr, tp, tv, seg, method));
     const int N = int(tb.size());
     *n_nodes = N;
     if (N > max_nodes) return fail(KRR_ERR_INVALID_ARG, "krr_cluster: max_nodes too small");
@@ -660,4 +986,9 @@ extern "C" int krr_cluster_batched(krr_ctx *k, const float *X, int64_t n, int32_
     if (nprob < 1 || !offsets) return fail(KRR_ERR_INVALID_ARG, "krr_cluster_batched: bad arguments");
     std::vector<int64_t> seg(offsets, offsets + nprob + 1);
     return cluster_entry(k, X, n, d, leaf, seed, perm, max_nodes, tree, n_nodes, &seg);
+}
+
+extern "C" int krr_order(krr_ctx *k, const float *X, int64_t n, int32_t d, int32_t leaf, int32_t ordering,
+                         uint64_t seed, int32_t *perm, int32_t max_nodes, krr_tree_arrays tree, int32_t *n_nodes) {
+    return cluster_entry(k, X, n, d, leaf, seed, perm, max_nodes, tree, n_nodes, nullptr, ordering);
 }

@@ -111,6 +111,118 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(const GemmProb<T> *pr
     }
 }
 
+// Skinny products (N <= 16 columns per output tile: right-hand-side blocks
+// of the ULV solve): bound by reading A once, so A is staged through shared
+// memory in wide K chunks with coalesced loads in either layout (rows of A,
+// or columns of A^T), B's K range of the item staged once, and every thread
+// owns one output row: lane = row within a 32-row half, the warp picks the
+// half and one of four K groups; the groups are summed at the end.
+template <class T>
+struct SkinnyCfg {
+    static constexpr int KC = sizeof(T) == 4 ? 128 : 64;  // K chunk of A in shared memory
+    static constexpr int KB = 512;                        // K of B staged at a time
+    static constexpr size_t smem() {
+        return sizeof(T) * (size_t(64) * (KC + 1) + size_t(KB) * 16);
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *probs, int np, int total_tiles) {
+    constexpr int KC = SkinnyCfg<T>::KC, KB = SkinnyCfg<T>::KB;
+    extern __shared__ __align__(16) unsigned char skinny_smem[];
+    T *As = reinterpret_cast<T *>(skinny_smem);  // 64 x (KC + 1), then the group sums
+    T *Bs = As + 64 * (KC + 1);                   // KB x 16
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row = 32 * (warp & 1) + lane, grp = warp >> 1;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        int lo = 0, hi = np - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].tile0 <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const GemmProb<T> &P = probs[lo];
+        const int t = tile - P.tile0;
+        const int i0 = (t / P.tn) * 64, j0 = (t % P.tn) * 16;
+        const int M = P.M, K = P.K, nc = min(16, P.N - j0);
+        T acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = T(0);
+        for (int kb0 = 0; kb0 < K; kb0 += KB) {
+            const int kbn = min(KB, K - kb0);
+            const int kbr = (kbn + KC - 1) / KC * KC;  // rows read by the chunks (zero past kbn)
+            __syncthreads();
+            for (int e = tid; e < kbr * 16; e += 256) {
+                const int k = e >> 4, c = e & 15;
+                T w = T(0);
+                if (c < nc && k < kbn)
+                    w = P.tb ? P.B[int64_t(j0 + c) * P.ldb + kb0 + k] : P.B[int64_t(kb0 + k) * P.ldb + j0 + c];
+                Bs[e] = w;
+            }
+            for (int k0 = 0; k0 < kbn; k0 += KC) {
+                const int kn = min(KC, kbn - k0);
+                __syncthreads();
+                if (!P.ta) {  // A(i, k) = A[i * lda + k]: consecutive threads along k
+                    for (int e = tid; e < 64 * KC; e += 256) {
+                        const int ii = e / KC, kk = e % KC;
+                        const int gi = i0 + ii;
+                        As[ii * (KC + 1) + kk] =
+                            (gi < M && kk < kn) ? P.A[int64_t(gi) * P.lda + kb0 + k0 + kk] : T(0);
+                    }
+                } else {      // A(i, k) = A[k * lda + i]: consecutive threads along i
+                    for (int e = tid; e < 64 * KC; e += 256) {
+                        const int kk = e / 64, ii = e % 64;
+                        const int gi = i0 + ii;
+                        As[ii * (KC + 1) + kk] =
+                            (gi < M && kk < kn) ? P.A[int64_t(kb0 + k0 + kk) * P.lda + gi] : T(0);
+                    }
+                }
+                __syncthreads();
+                const T *ar = As + row * (KC + 1);
+                const T *bk = Bs + (k0 + grp * (KC / 4)) * 16;
+#pragma unroll 4
+                for (int kk = 0; kk < KC / 4; ++kk) {
+                    const T a = ar[grp * (KC / 4) + kk];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) acc[c] += a * bk[kk * 16 + c];
+                }
+            }
+        }
+        // sum the four K groups (the staging buffer is free after the sync)
+        __syncthreads();
+        T *red = As;  // [4][64][16]
+#pragma unroll
+        for (int c = 0; c < 16; ++c) red[(grp * 64 + row) * 16 + c] = acc[c];
+        __syncthreads();
+        for (int e = tid; e < 64 * 16; e += 256) {
+            const int ii = e >> 4, c = e & 15;
+            const int gi = i0 + ii;
+            if (gi >= M || c >= nc) continue;
+            const T v = red[ii * 16 + c] + red[(64 + ii) * 16 + c] + red[(128 + ii) * 16 + c] +
+                        red[(192 + ii) * 16 + c];
+            T *cp = P.C + int64_t(gi) * P.ldc + j0 + c;
+            if (P.atomic) atomicAdd(cp, P.alpha * v);
+            else *cp = P.beta == T(0) ? P.alpha * v : P.alpha * v + P.beta * *cp;
+        }
+    }
+}
+
+template <class T, int TN>
+inline cudaError_t launch_grouped(Ctx *c, const GemmProb<T> *probs, int np, int tiles) {
+    const int grid = tiles < 4 * c->num_sms ? tiles : 4 * c->num_sms;
+    if (TN == 16) {
+        static SmemLimitOnce once;
+        const int bytes = int(SkinnyCfg<T>::smem());
+        const cudaError_t e = raise_smem_limit(once, c->device, skinny_gemm_kernel<T>, bytes);
+        if (e != cudaSuccess) return e;
+        skinny_gemm_kernel<T><<<grid, 256, bytes, c->stream>>>(probs, np, tiles);
+    } else {
+        grouped_gemm_kernel<T, TN><<<grid, 256, 0, c->stream>>>(probs, np, tiles);
+    }
+    ::krr::count_launch();
+    return cudaGetLastError();
+}
+
 // A problem list uploaded once and launched many times.
 template <class T, int TN>
 struct GemmPlan {
@@ -123,9 +235,7 @@ struct GemmPlan {
             { zero_jobs_kernel<T><<<g, 256, 0, c->stream>>>(z.get(), nz); ::krr::count_launch(); }
         }
         if (np == 0) return KRR_OK;
-        const int grid = tiles < 4 * c->num_sms ? tiles : 4 * c->num_sms;
-        { grouped_gemm_kernel<T, TN><<<grid, 256, 0, c->stream>>>(d.get(), np, tiles); ::krr::count_launch(); }
-        KRR_CUDA(cudaGetLastError());
+        KRR_CUDA((launch_grouped<T, TN>(c, d.get(), np, tiles)));
         return KRR_OK;
     }
 };
@@ -218,9 +328,7 @@ struct GemmBatch {
         DBuf<GemmProb<T>> d(c, v.size());
         if (!d.get()) return fail(KRR_ERR_OOM, "grouped gemm: out of memory");
         KRR_CUDA(cudaMemcpyAsync(d.get(), v.data(), v.size() * sizeof(GemmProb<T>), cudaMemcpyHostToDevice, c->stream));
-        const int grid = tiles < 4 * c->num_sms ? tiles : 4 * c->num_sms;
-        { grouped_gemm_kernel<T, TN><<<grid, 256, 0, c->stream>>>(d.get(), int(v.size()), tiles); ::krr::count_launch(); }
-        KRR_CUDA(cudaGetLastError());
+        KRR_CUDA((launch_grouped<T, TN>(c, d.get(), int(v.size()), tiles)));
         v.clear();
         tiles = 0;
         return KRR_OK;

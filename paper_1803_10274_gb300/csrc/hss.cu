@@ -46,7 +46,7 @@ namespace krr {
 
 int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, int32_t *perm_out,
             std::vector<int32_t> &tb, std::vector<int32_t> &te, std::vector<int32_t> &tl, std::vector<int32_t> &tr,
-            std::vector<int32_t> &tp, std::vector<int32_t> &tv, const std::vector<int64_t> *segments);
+            std::vector<int32_t> &tp, std::vector<int32_t> &tv, const std::vector<int64_t> *segments, int method);
 
 namespace {
 
@@ -102,7 +102,8 @@ __global__ void extract_b_kernel(const NodeDesc *nd, const T *X, int d, T inv2h2
     if (N.is_leaf) return;
     const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
     const int ka = A.k, kb = B.k;
-    for (int e = threadIdx.x; e < ka * kb; e += blockDim.x) {
+    // gridDim.y CTAs share a node (the top levels have few, large nodes)
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < ka * kb; e += gridDim.y * blockDim.x) {
         const int a = e / kb, b = e % kb;
         const int ia = I[A.jsk + a], ib = I[B.jsk + b];
         F[N.bmat + e] = kern(X + int64_t(ia) * d, X + int64_t(ib) * d, d, inv2h2);
@@ -119,10 +120,12 @@ __global__ void parent_sloc_kernel(const NodeDesc *nd, const NodeDesc *all, int 
     const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
     const int ka = A.k, kb = B.k;
     T *Sl = F + N.sloc;
-    for (int64_t e = threadIdx.x; e < int64_t(ka) * r; e += blockDim.x) Sl[e] = F[A.skel + e];
-    for (int64_t e = threadIdx.x; e < int64_t(kb) * r; e += blockDim.x) Sl[int64_t(ka) * r + e] = F[B.skel + e];
-    for (int a = threadIdx.x; a < ka; a += blockDim.x) I[N.rows + a] = I[A.jsk + a];
-    for (int a = threadIdx.x; a < kb; a += blockDim.x) I[N.rows + ka + a] = I[B.jsk + a];
+    // gridDim.y CTAs share a node (the top levels have few, large nodes)
+    const int64_t t0 = int64_t(blockIdx.y) * blockDim.x + threadIdx.x, step = int64_t(gridDim.y) * blockDim.x;
+    for (int64_t e = t0; e < int64_t(ka) * r; e += step) Sl[e] = F[A.skel + e];
+    for (int64_t e = t0; e < int64_t(kb) * r; e += step) Sl[int64_t(ka) * r + e] = F[B.skel + e];
+    for (int64_t a = t0; a < ka; a += step) I[N.rows + a] = I[A.jsk + a];
+    for (int64_t a = t0; a < kb; a += step) I[N.rows + ka + a] = I[B.jsk + a];
 }
 
 // Row ID of every node's S_loc (Householder QR with column pivoting of
@@ -1103,9 +1106,12 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
         std::vector<int> lid;
         for (int v : lv)
             if (!H->is_top(v)) lid.push_back(v);
+        // CTAs per node for the per-node copy kernels: about four waves of
+        // the SMs over the level
+        const unsigned per_node = unsigned(std::max(1, std::min(64, 4 * c->num_sms / std::max(nn, 1))));
         if (h > 0) {
-            { extract_b_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), X, H->d, inv2h2, F, H->IA.get(),
-                                                                  H->ddesc.get()); ::krr::count_launch(); }
+            { extract_b_kernel<T><<<dim3(nn, per_node), cta::kNT, 0, c->stream>>>(dl.get(), X, H->d, inv2h2, F,
+                                                                                  H->IA.get(), H->ddesc.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
         }
         int mmax = 0;
@@ -1114,7 +1120,8 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
         if (is_root_level) break;  // the root needs B only
         const int r = H->r;
         if (h > 0) {
-            { parent_sloc_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), r, F, H->IA.get()); ::krr::count_launch(); }
+            { parent_sloc_kernel<T><<<dim3(nn, per_node), cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), r, F,
+                                                                                     H->IA.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             // S_a(J_a) - B_ab Rhat_b ;  S_b(J_b) - B_ab^T Rhat_a
             GemmBatch<T> gb;
@@ -1640,7 +1647,8 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
     const double t0 = now_ms();
     if (!H->perm.reset(c, n) || !H->leaf_of.reset(c, n) || !H->Xp32.reset(c, size_t(n) * d))
         return fail(KRR_ERR_OOM, "hss_compress: out of memory");
-    KRR_TRY(cluster(c, X, n, d, o->leaf, o->seed, H->perm.get(), H->tb, H->te, H->tl, H->tr, H->tp, H->tv, boff));
+    KRR_TRY(cluster(c, X, n, d, o->leaf, o->seed, H->perm.get(), H->tb, H->te, H->tl, H->tr, H->tp, H->tv, boff,
+                    o->ordering));
     H->t_cluster = now_ms() - t0;
     const int nn = int(H->tb.size());
     H->root = nn - 1;
@@ -2418,7 +2426,8 @@ int hss_compress(krr_ctx *k, const float *X, int64_t n, int32_t d, const krr_opt
     if (out) *out = nullptr;
     if (!k || !X || !o || !out || n <= 0 || d <= 0) return fail(KRR_ERR_INVALID_ARG, "hss_compress: bad arguments");
     if (!(o->h > 0) || !(o->lambda > 0) || !(o->eps_c > 0) || o->eps_abs < 0 || o->leaf < 1 || o->r0 < 1 ||
-        o->p < 0 || o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64))
+        o->p < 0 || o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64) ||
+        o->ordering < KRR_ORDER_TWO_MEANS || o->ordering > KRR_ORDER_PCA)
         return fail(KRR_ERR_INVALID_ARG, "hss_compress: bad options");
     if (o->precision == KRR_MIXED && d > kMaxMixedDim)
         return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress: mixed path supports d <= 1024");

@@ -18,6 +18,8 @@ void krr_default_options(krr_options *o) {
     o->seed = 1;
     o->precision = KRR_MIXED;
     o->flags = 0;
+    o->ordering = KRR_ORDER_TWO_MEANS;
+    o->pad = 0;
 }
 
 }  // extern "C"
