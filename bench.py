@@ -278,7 +278,8 @@ def run_ours(args):
     extras = {} if args.no_extras else {"gradient": bench_gradient(K, ctx, l2),
                                         "million_point_product": bench_million(K, ctx),
                                         "batch": bench_batch(K, ctx, l2),
-                                        "image_d784": bench_image(K, ctx, l2)}
+                                        "image_d784": bench_image(K, ctx, l2),
+                                        "orderings": bench_orderings(K, ctx, l2)}
 
     # ---- FP64 plain path, same step (one run: it is slow)
     plain = None
@@ -523,6 +524,58 @@ def bench_image(K, ctx, l2, reps=2):
             "product_r64": {"seconds": tp, "tflops": 2.0 * n * n * (d + r) / tp / 1e12}}
 
 
+ORDER_NAMES = {0: "2MN", 1: "NP", 2: "KD", 3: "PCA"}
+
+
+def bench_orderings(K, ctx, l2):
+    """The comparison of the paper's Section 5.2 table on the synthetic
+    stand-ins: HSS memory (D, U, B generators), largest rank, samples,
+    test accuracy and compress + factor + solve time for each ordering of
+    Section 4.3, on the SUSY-shaped workload (n = 65536, d = 8; all four)
+    and the MNIST-shaped one (n = 32768, d = 784; the principal-direction
+    ordering is limited to d <= 64).  Sample budget 2048 columns; a
+    compression that would need more keeps truncated decompositions and is
+    marked so.  Reported, not gated."""
+    import torch
+    import synth
+    out = {}
+    X, y, Xt, yt, _, _ = synth.mixture(WL["n"], WL["d"], WL["comps"], WL["sigma"], WL["seed"], WL["m_test"])
+    Xs = torch.from_numpy(X.astype(np.float32)).cuda()
+    Xts = torch.from_numpy(Xt.astype(np.float32)).cuda()
+    K.krr_standardize(ctx, Xs, Xts)
+    Xi, yi, Xti, yti = synth.image_like(IMAGE_WL["n"], IMAGE_WL["seed"], m_test=IMAGE_WL["m_test"])
+    cases = [("susy_n65536_d8", Xs, Xts, y, yt, WL["h"], WL["lam"], WL["leaf"], WL["eps_c"], 10 * WL["eps"] / 2,
+              (0, 1, 2, 3)),
+             ("mnist_n32768_d784", torch.from_numpy(Xi.astype(np.float32)).cuda(),
+              torch.from_numpy(Xti.astype(np.float32)).cuda(), yi, yti, IMAGE_WL["h"], IMAGE_WL["lam"],
+              IMAGE_WL["leaf"], IMAGE_WL["eps_c"], IMAGE_WL["eps"], (0, 1, 2))]
+    for name, Xd, Xtd, yv, ytv, h, lam, leaf, eps_c, tol, orders in cases:
+        res = {}
+        yd = torch.from_numpy(np.ascontiguousarray(yv[:, None])).cuda()
+        for od in orders:
+            o = K.default_options(h=h, lambda_=lam, eps_c=eps_c, leaf=leaf, seed=WL["seed"], ordering=od,
+                                  flags=K.KRR_TRUNCATE_AT_RMAX)
+            _flush_l2(l2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            H = K.hss_compress(ctx, Xd, o)
+            H.factor()
+            a, rr = H.solve(yd, tol=tol, max_refine=400, raise_on_no_convergence=False)
+            dec = H.predict(Xtd, a)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            st = H.stats()
+            H.close()
+            acc = float(np.mean(np.where(dec.cpu().numpy()[:, 0] >= 0, 1.0, -1.0) == ytv))
+            res[ORDER_NAMES[od]] = {"hss_memory_MB": st["memory_bytes"] / 1e6, "max_rank": st["max_rank"],
+                                    "samples": st["samples"], "truncated": st["truncated"],
+                                    "gmres_iters": st["refine_steps"], "resid_gpu": rr, "test_accuracy": acc,
+                                    "seconds": e0.elapsed_time(e1) / 1e3}
+        out[name] = res
+    return out
+
+
 def bench_million(K, ctx, n=1 << 20, r=256, reps=2):
     """One fused product S = K R at n = 1,048,576, d = 8, r = 256 (about
     5.8e14 algorithmic flops), inputs resident, CUDA events."""
@@ -635,6 +688,7 @@ def main():
                     help="skip the gradient workload and the million-point product")
     ap.add_argument("--image", action="store_true", help="with --sample-only: MNIST-shaped rows (d=784)")
     ap.add_argument("--batch-only", action="store_true", help="only run the MNIST-shaped and batched-problems workloads")
+    ap.add_argument("--orderings-only", action="store_true", help="only run the comparison of the orderings")
     ap.add_argument("--sample-only", nargs=2, type=int, metavar=("N", "R"),
                     help="only run the fused sampling product at n=N, r=R (5 launches; for profilers)")
     args = ap.parse_args()
@@ -647,6 +701,13 @@ def main():
         ctx = K.Context()
         l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         print(json.dumps({"image_d784": bench_image(K, ctx, l2), "batch": bench_batch(K, ctx, l2)}), flush=True)
+    elif args.orderings_only:
+        import torch
+        import paper_1803_10274_gb300 as K
+        torch.cuda.set_device(0)
+        ctx = K.Context()
+        l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        print(json.dumps({"orderings": bench_orderings(K, ctx, l2)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

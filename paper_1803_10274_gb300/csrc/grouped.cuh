@@ -112,27 +112,31 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(const GemmProb<T> *pr
 }
 
 // Skinny products (N <= 16 columns per output tile: right-hand-side blocks
-// of the ULV solve): bound by reading A once, so A is staged through shared
-// memory in wide K chunks with coalesced loads in either layout (rows of A,
-// or columns of A^T), B's K range of the item staged once, and every thread
-// owns one output row: lane = row within a 32-row half, the warp picks the
-// half and one of four K groups; the groups are summed at the end.
+// of the ULV solve) are bound by reading A once.  A streams from global
+// memory with coalesced loads; only the item's rows of B (at most 512 x 16)
+// are staged in shared memory.  Every thread owns one output row (lane =
+// row within a 32-row half; the warp picks the half and one of four K
+// quarters, summed at the end), so no shuffle reductions are needed:
+//   op(A) = A^T (A stored K x M): consecutive lanes read consecutive rows;
+//   op(A) = A (A stored M x K): the warp reads 32 x 32 blocks row by row
+//     (coalesced along K) into its own shared-memory tile and reads them
+//     back transposed (only warp-level synchronization).
 template <class T>
 struct SkinnyCfg {
-    static constexpr int KC = sizeof(T) == 4 ? 128 : 64;  // K chunk of A in shared memory
-    static constexpr int KB = 512;                        // K of B staged at a time
+    static constexpr int KB = 512;  // K of B staged at a time
     static constexpr size_t smem() {
-        return sizeof(T) * (size_t(64) * (KC + 1) + size_t(KB) * 16);
+        return sizeof(T) * (size_t(KB) * 16 + size_t(4) * 64 * 16 + size_t(8) * 32 * 33);
     }
 };
 
 template <class T>
 __global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *probs, int np, int total_tiles) {
-    constexpr int KC = SkinnyCfg<T>::KC, KB = SkinnyCfg<T>::KB;
+    constexpr int KB = SkinnyCfg<T>::KB;
     extern __shared__ __align__(16) unsigned char skinny_smem[];
-    T *As = reinterpret_cast<T *>(skinny_smem);  // 64 x (KC + 1), then the group sums
-    T *Bs = As + 64 * (KC + 1);                   // KB x 16
+    T *Bs = reinterpret_cast<T *>(skinny_smem);  // KB x 16
+    T *red = Bs + KB * 16;                        // [4][64][16]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T *tw = red + 4 * 64 * 16 + warp * 32 * 33;   // this warp's 32 x 33 transpose tile
     const int row = 32 * (warp & 1) + lane, grp = warp >> 1;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         int lo = 0, hi = np - 1;
@@ -145,62 +149,70 @@ __global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *pro
         const int t = tile - P.tile0;
         const int i0 = (t / P.tn) * 64, j0 = (t % P.tn) * 16;
         const int M = P.M, K = P.K, nc = min(16, P.N - j0);
+        const int gi = i0 + row;
         T acc[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = T(0);
         for (int kb0 = 0; kb0 < K; kb0 += KB) {
             const int kbn = min(KB, K - kb0);
-            const int kbr = (kbn + KC - 1) / KC * KC;  // rows read by the chunks (zero past kbn)
             __syncthreads();
-            for (int e = tid; e < kbr * 16; e += 256) {
+            for (int e = tid; e < kbn * 16; e += 256) {
                 const int k = e >> 4, c = e & 15;
-                T w = T(0);
-                if (c < nc && k < kbn)
-                    w = P.tb ? P.B[int64_t(j0 + c) * P.ldb + kb0 + k] : P.B[int64_t(kb0 + k) * P.ldb + j0 + c];
-                Bs[e] = w;
+                Bs[e] = c < nc ? (P.tb ? P.B[int64_t(j0 + c) * P.ldb + kb0 + k] : P.B[int64_t(kb0 + k) * P.ldb + j0 + c])
+                               : T(0);
             }
-            for (int k0 = 0; k0 < kbn; k0 += KC) {
-                const int kn = min(KC, kbn - k0);
-                __syncthreads();
-                if (!P.ta) {  // A(i, k) = A[i * lda + k]: consecutive threads along k
-                    for (int e = tid; e < 64 * KC; e += 256) {
-                        const int ii = e / KC, kk = e % KC;
-                        const int gi = i0 + ii;
-                        As[ii * (KC + 1) + kk] =
-                            (gi < M && kk < kn) ? P.A[int64_t(gi) * P.lda + kb0 + k0 + kk] : T(0);
+            __syncthreads();
+            const int qn = (kbn + 3) / 4;
+            const int q0 = grp * qn, q1 = min(kbn, q0 + qn);
+            if (P.ta) {
+                if (gi < M) {
+                    const T *a = P.A + int64_t(kb0) * P.lda + gi;
+                    int k = q0;
+                    for (; k + 4 <= q1; k += 4) {
+                        const T a0 = a[int64_t(k) * P.lda], a1 = a[int64_t(k + 1) * P.lda];
+                        const T a2 = a[int64_t(k + 2) * P.lda], a3 = a[int64_t(k + 3) * P.lda];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            acc[c] += a0 * Bs[k * 16 + c] + a1 * Bs[(k + 1) * 16 + c] + a2 * Bs[(k + 2) * 16 + c] +
+                                      a3 * Bs[(k + 3) * 16 + c];
                     }
-                } else {      // A(i, k) = A[k * lda + i]: consecutive threads along i
-                    for (int e = tid; e < 64 * KC; e += 256) {
-                        const int kk = e / 64, ii = e % 64;
-                        const int gi = i0 + ii;
-                        As[ii * (KC + 1) + kk] =
-                            (gi < M && kk < kn) ? P.A[int64_t(kb0 + k0 + kk) * P.lda + gi] : T(0);
+                    for (; k < q1; ++k) {
+                        const T a0 = a[int64_t(k) * P.lda];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc[c] += a0 * Bs[k * 16 + c];
                     }
                 }
-                __syncthreads();
-                const T *ar = As + row * (KC + 1);
-                const T *bk = Bs + (k0 + grp * (KC / 4)) * 16;
-#pragma unroll 4
-                for (int kk = 0; kk < KC / 4; ++kk) {
-                    const T a = ar[grp * (KC / 4) + kk];
+            } else {
+                const int r0 = i0 + 32 * (warp & 1);  // first row of this warp's half
+                for (int k = q0; k < q1; k += 32) {
+                    const int kn = min(32, q1 - k);
+                    // rows r0 .. r0 + 31, K columns k .. k + kn - 1, read along K
+                    __syncwarp();
+#pragma unroll 8
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int gr = r0 + rr;
+                        tw[rr * 33 + lane] = (gr < M && lane < kn) ? P.A[int64_t(gr) * P.lda + kb0 + k + lane] : T(0);
+                    }
+                    __syncwarp();
+                    for (int kk = 0; kk < kn; ++kk) {
+                        const T a0 = tw[lane * 33 + kk];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) acc[c] += a * bk[kk * 16 + c];
+                        for (int c = 0; c < 16; ++c) acc[c] += a0 * Bs[(k + kk) * 16 + c];
+                    }
                 }
             }
         }
-        // sum the four K groups (the staging buffer is free after the sync)
         __syncthreads();
-        T *red = As;  // [4][64][16]
 #pragma unroll
         for (int c = 0; c < 16; ++c) red[(grp * 64 + row) * 16 + c] = acc[c];
         __syncthreads();
         for (int e = tid; e < 64 * 16; e += 256) {
             const int ii = e >> 4, c = e & 15;
-            const int gi = i0 + ii;
-            if (gi >= M || c >= nc) continue;
+            const int go = i0 + ii;
+            if (go >= M || c >= nc) continue;
             const T v = red[ii * 16 + c] + red[(64 + ii) * 16 + c] + red[(128 + ii) * 16 + c] +
                         red[(192 + ii) * 16 + c];
-            T *cp = P.C + int64_t(gi) * P.ldc + j0 + c;
+            T *cp = P.C + int64_t(go) * P.ldc + j0 + c;
             if (P.atomic) atomicAdd(cp, P.alpha * v);
             else *cp = P.beta == T(0) ? P.alpha * v : P.alpha * v + P.beta * *cp;
         }

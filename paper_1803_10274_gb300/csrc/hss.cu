@@ -600,7 +600,9 @@ __global__ void __launch_bounds__(cta::kNT) solve_gather_kernel(const NodeDesc *
     const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
     const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
     const int32_t *piv = I + N.piv;
-    for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
+    // gridDim.y CTAs share a node (the top levels have few, large nodes)
+    for (int64_t e = int64_t(blockIdx.y) * blockDim.x + threadIdx.x; e < int64_t(m) * nrhs;
+         e += int64_t(gridDim.y) * blockDim.x) {
         const int a = int(e / nrhs), c = int(e % nrhs);
         const int src = is_root ? a : piv[a];
         T v;
@@ -623,7 +625,8 @@ __global__ void __launch_bounds__(cta::kNT) solve_place_kernel(const NodeDesc *n
     const NodeDesc &N = nd[blockIdx.x];
     const int m = N.m, k = N.k;
     const int32_t *piv = I + N.piv;
-    for (int64_t e = threadIdx.x; e < int64_t(m) * nrhs; e += blockDim.x) {
+    for (int64_t e = int64_t(blockIdx.y) * blockDim.x + threadIdx.x; e < int64_t(m) * nrhs;
+         e += int64_t(gridDim.y) * blockDim.x) {
         const int a = int(e / nrhs), c = int(e % nrhs);
         const T v = a < k ? F[N.btil + int64_t(a) * nrhs + c] : F[N.zvec + int64_t(a - k) * nrhs + c];
         const int dst = piv[a];
@@ -648,8 +651,9 @@ __global__ void scatter_down_kernel(const NodeDesc *nd, const NodeDesc *all, int
     if (N.is_leaf) return;
     const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
     const T *x = F + N.xloc;
-    for (int64_t e = threadIdx.x; e < int64_t(A.k) * nrhs; e += blockDim.x) F[A.btil + e] = x[e];
-    for (int64_t e = threadIdx.x; e < int64_t(B.k) * nrhs; e += blockDim.x) F[B.btil + e] = x[int64_t(A.k) * nrhs + e];
+    const int64_t e0 = int64_t(blockIdx.y) * blockDim.x + threadIdx.x, step = int64_t(gridDim.y) * blockDim.x;
+    for (int64_t e = e0; e < int64_t(A.k) * nrhs; e += step) F[A.btil + e] = x[e];
+    for (int64_t e = e0; e < int64_t(B.k) * nrhs; e += step) F[B.btil + e] = x[int64_t(A.k) * nrhs + e];
 }
 
 __global__ void leaf_id_kernel(int64_t n, const int32_t *begin, const int32_t *end, const int32_t *isleaf, int nn,
@@ -1488,8 +1492,9 @@ int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64
         if (!nn) continue;
         HssImpl::LevelPlan &P = H->plan[h];
         const int is_root = h == H->H ? 1 : 0;
-        { solve_gather_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(P.dl.get(), H->ddesc.get(), yperm, ldy, nrhs, F,
-                                                                 H->IA.get(), is_root); ::krr::count_launch(); }
+        const unsigned per_node = unsigned(std::max(1, std::min(32, 2 * c->num_sms / nn)));
+        { solve_gather_kernel<T><<<dim3(nn, per_node), cta::kNT, 0, c->stream>>>(P.dl.get(), H->ddesc.get(), yperm,
+                                                                                 ldy, nrhs, F, H->IA.get(), is_root); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         if (is_root) {
             KRR_TRY(pick<T>(P, 0).run(c));
@@ -1503,14 +1508,17 @@ int ulv_solve(HssImpl *H, const T *yperm, int64_t ldy, int nrhs, T *xperm, int64
         const int nn = int(H->by_height[h].size());
         if (!nn) continue;
         HssImpl::LevelPlan &P = H->plan[h];
+        const unsigned per_node = unsigned(std::max(1, std::min(32, 2 * c->num_sms / nn)));
         if (h < H->H) {
             KRR_TRY(pick<T>(P, 4).run(c));
             KRR_TRY(pick<T>(P, 5).run(c));
-            { solve_place_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(P.dl.get(), nrhs, F, H->IA.get(), xperm, ldx); ::krr::count_launch(); }
+            { solve_place_kernel<T><<<dim3(nn, per_node), cta::kNT, 0, c->stream>>>(P.dl.get(), nrhs, F, H->IA.get(),
+                                                                                    xperm, ldx); ::krr::count_launch(); }
         } else if (H->desc[H->root].is_leaf) {  // single-leaf tree: the root's solve is the answer
             { root_leaf_out_kernel<T><<<1, cta::kNT, 0, c->stream>>>(P.dl.get(), nrhs, F, xperm, ldx); ::krr::count_launch(); }
         }
-        { scatter_down_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(P.dl.get(), H->ddesc.get(), nrhs, F); ::krr::count_launch(); }
+        { scatter_down_kernel<T><<<dim3(nn, per_node), cta::kNT, 0, c->stream>>>(P.dl.get(), H->ddesc.get(), nrhs,
+                                                                                 F); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
     }
     return KRR_OK;
