@@ -54,7 +54,11 @@ typedef enum {
     KRR_MIXED = 0, /* kernel products on tcgen05 tensor cores: FP16 operands
                       (split into hi/lo parts for the distances), FP32
                       accumulation; other steps in FP32                     */
-    KRR_FP64 = 1   /* every step in FP64 on the CUDA cores                  */
+    KRR_FP64 = 1,  /* every step in FP64 on the CUDA cores                  */
+    KRR_MIXED_F64 = 2 /* kernel products on tensor cores as KRR_MIXED; the
+                      interpolative decompositions, the factorization and
+                      the ULV solve in FP64 (for smooth kernels, whose
+                      blocks are large next to lambda)                     */
 } krr_precision;
 
 /* Optional device-memory allocator (e.g. a framework's caching allocator).

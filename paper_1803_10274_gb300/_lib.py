@@ -21,7 +21,7 @@ STATUS = {0: "KRR_OK", 1: "KRR_ERR_INVALID_ARG", 2: "KRR_ERR_NONFINITE_INPUT", 3
           8: "KRR_ERR_NOT_IMPLEMENTED", 9: "KRR_ERR_NO_CONVERGENCE"}
 KRR_TRUNCATE_AT_RMAX = 1
 KRR_LAMBDA_TOL = 2
-KRR_MIXED, KRR_FP64 = 0, 1
+KRR_MIXED, KRR_FP64, KRR_MIXED_F64 = 0, 1, 2
 KRR_ORDER_TWO_MEANS, KRR_ORDER_NATURAL, KRR_ORDER_KD, KRR_ORDER_PCA = 0, 1, 2, 3
 
 P = ctypes.c_void_p

@@ -11,10 +11,10 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_ORDER_KD, KRR_ORDER_NATURAL, KRR_ORDER_PCA,
+from ._lib import (KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_MIXED_F64, KRR_ORDER_KD, KRR_ORDER_NATURAL, KRR_ORDER_PCA,
                    KRR_ORDER_TWO_MEANS, KRR_TRUNCATE_AT_RMAX, KRRError, check, lib)
 
-__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "KRR_ORDER_TWO_MEANS",
+__all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_MIXED_F64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "KRR_ORDER_TWO_MEANS",
            "KRR_ORDER_NATURAL", "KRR_ORDER_KD", "KRR_ORDER_PCA", "krr_order", "krr_standardize", "krr_cluster", "krr_sample",
            "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "krr_one_vs_all", "HSS", "hss_compress", "default_options",
            "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]

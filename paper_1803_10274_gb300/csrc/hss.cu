@@ -756,6 +756,15 @@ __global__ void scale_rows_kernel(T *X, int64_t n, int d, const int32_t *grp, co
     if (e < n * d) X[e] = T(double(X[e]) * s[grp[e / d]]);
 }
 
+// dst(i, c) = src(i, c) for c < cols (strided FP32 -> FP64 columns)
+__global__ void widen_cols_kernel(const float *src, int64_t lds, int64_t n, int cols, double *dst, int64_t ldd) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * cols) return;
+    const int64_t i = e / cols;
+    const int c = int(e % cols);
+    dst[i * ldd + c] = double(src[i * lds + c]);
+}
+
 __global__ void axpy_kernel(double *a, const double *b, int64_t n) {
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e < n) a[e] += b[e];
@@ -834,7 +843,7 @@ struct HssImpl {
     bool is_top(int v) const { return !top.empty() && top[v]; }
     // IDs from the Gram matrix need eps^2 well above its rounding; tighter
     // tolerances take the QR of the samples
-    bool use_gram() const { return opt.eps_c >= (mixed() ? 1e-2 : 1e-5); }
+    bool use_gram() const { return opt.eps_c >= (f32() ? 1e-2 : 1e-5); }
     // KRR_LAMBDA_TOL: a decomposition stops only below eps_c * min(|R_11|,
     // lambda sqrt(rid)), i.e. also once the next singular value of the
     // block (a pivot is about sigma sqrt(rid) in sample units) is below
@@ -846,7 +855,10 @@ struct HssImpl {
     bool truncated = false;
     double max_test_err = 0;
     double t_cluster = 0, t_sample = 0, t_compress = 0, t_factor = 0, t_solve = 0;
-    bool mixed() const { return opt.precision == KRR_MIXED; }
+    // tc(): kernel products on tensor cores (KRR_MIXED, KRR_MIXED_F64);
+    // f32(): decompositions, factorization and ULV solve in FP32 (KRR_MIXED)
+    bool tc() const { return opt.precision != KRR_FP64; }
+    bool f32() const { return opt.precision == KRR_MIXED; }
     // The ULV solve as a captured CUDA graph, replayed on the context's
     // stream (valid for one plan, one pair of fixed buffers, one nrhs).
     cudaStream_t cap_stream = nullptr;
@@ -1029,13 +1041,21 @@ int sample_columns(HssImpl *H, int c0, int c1) {
     Ctx *c = H->c;
     const int dr = c1 - c0;
     const BlockDiag bd = H->bd_train();
-    if (H->mixed()) {
+    if (H->tc()) {
         KRR_TRY(random_block(c, H->n, dr, c0, H->opt.seed, KRR_MIXED, H->R32.get() + c0, H->r_cap));
         KRR_TRY(transpose_half(c, H->R32.get() + c0, H->n, dr, H->r_cap, H->RT.get() + int64_t(c0) * H->ldrt,
                                int(round_up(dr, 64)), H->ldrt));
         KRR_TRY(sample_mixed_prepared(c, H->XA.get(), H->n, H->XB.get(), H->n, H->d,
                                       H->RT.get() + int64_t(c0) * H->ldrt, dr, H->ldrt, H->leaf_of.get(),
                                       H->leaf_of.get(), H->S32.get() + c0, H->r_cap, false, H->bd_or_null(bd)));
+        if (!H->f32()) {  // FP64 decompositions: the new columns widened (R is FP16-exact)
+            const dim3 g(unsigned(cdiv(H->n * dr, 256)));
+            { widen_cols_kernel<<<g, 256, 0, c->stream>>>(H->R32.get() + c0, H->r_cap, H->n, dr, H->R64.get() + c0,
+                                                         H->r_cap); ::krr::count_launch(); }
+            { widen_cols_kernel<<<g, 256, 0, c->stream>>>(H->S32.get() + c0, H->r_cap, H->n, dr, H->S64.get() + c0,
+                                                         H->r_cap); ::krr::count_launch(); }
+            KRR_CUDA(cudaGetLastError());
+        }
     } else {
         KRR_TRY(random_block(c, H->n, dr, c0, H->opt.seed, KRR_FP64, H->R64.get() + c0, H->r_cap));
         KRR_TRY(launch_sample_f64(c, H->Xp64.get(), H->n, H->Xp64.get(), H->n, H->d, H->opt.h,
@@ -1051,10 +1071,10 @@ template <class T>
 int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
     Ctx *c = H->c;
     need_more = false;
-    const T *S = H->mixed() ? reinterpret_cast<const T *>(H->S32.get()) : reinterpret_cast<const T *>(H->S64.get());
-    const T *R = H->mixed() ? reinterpret_cast<const T *>(H->R32.get()) : reinterpret_cast<const T *>(H->R64.get());
+    const T *S = H->f32() ? reinterpret_cast<const T *>(H->S32.get()) : reinterpret_cast<const T *>(H->S64.get());
+    const T *R = H->f32() ? reinterpret_cast<const T *>(H->R32.get()) : reinterpret_cast<const T *>(H->R64.get());
     const T inv2h2 = T(1.0 / (2.0 * H->opt.h * H->opt.h));
-    const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
+    const T *X = H->f32() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
     const int kmax = H->r - kHoldOut - H->opt.p + 1;  // one past the budget: a rank there means "need more"
     // The arena is laid out level by level: a parent's m (the sum of its
     // children's ranks) is exact when its level comes, so every slot has its
@@ -1063,7 +1083,7 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
     T *F = nullptr;
     auto arena = [&](int h) -> int {
         layout_level(H, h, H->nrhs_cap, fo, io);
-        if (H->mixed()) {
+        if (H->f32()) {
             KRR_TRY(grow_arena(c, H->F32, H->arena_f, fo));
             F = reinterpret_cast<T *>(H->F32.get());
         } else {
@@ -1359,7 +1379,7 @@ int factor(HssImpl *H) {
     const double t0 = now_ms();
     T *F = farena<T>(H);
     const T inv2h2 = T(1.0 / (2.0 * H->opt.h * H->opt.h));
-    const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
+    const T *X = H->f32() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
     KRR_CUDA(cudaMemcpyAsync(H->ddesc.get(), H->desc.data(), H->desc.size() * sizeof(NodeDesc),
                              cudaMemcpyHostToDevice, c->stream));
     Tracer tr(c);
@@ -1577,7 +1597,7 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
               const BlockDiag *bd, const double *Xa64_rows = nullptr) {
     Ctx *c = H->c;
     const int64_t n = H->n;
-    if (H->mixed()) {
+    if (H->tc()) {
         const int cols = 2 * nrhs;
         const int rpad = int(round_up(cols, 64));
         DBuf<float> Rs_own, Sm_own;
@@ -1699,11 +1719,11 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
     }
     KRR_TRY((gather_rows<float, float>(c, X, d, H->perm.get(), n, d, H->Xp32.get(), d)));
     // batched: each problem's coordinates divided by its width (FP64 path: in FP64, below)
-    if (H->nprob > 0 && H->mixed()) KRR_TRY(scale_by_width(c, H->Xp32.get(), n, d, H->bgrp.get(), H->bh));
+    if (H->nprob > 0 && H->tc()) KRR_TRY(scale_by_width(c, H->Xp32.get(), n, d, H->bgrp.get(), H->bh));
     H->r_cap = int(round_up(std::max(o->r0, o->r_max), 64));
     H->r = int(round_up(o->r0, 64));
     H->nrhs_cap = 64;
-    if (H->mixed()) {
+    if (H->tc()) {
         H->kpad = aug_kpad(d);
         H->ldrt = round_up(n, 8);
         if (!H->XA.reset(c, size_t(n) * H->kpad) || !H->XB.reset(c, size_t(n) * H->kpad) ||
@@ -1712,15 +1732,17 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
             return fail(KRR_ERR_OOM, "hss_compress: out of memory");
         KRR_TRY(augment(c, H->Xp32.get(), n, d, H->opt.h, 0, H->XA.get(), H->kpad));
         KRR_TRY(augment(c, H->Xp32.get(), n, d, H->opt.h, 1, H->XB.get(), H->kpad));
-        KRR_TRY(compress<float>(H));
-    } else {
+    }
+    if (!H->f32()) {
         if (!H->Xp64.reset(c, size_t(n) * d) || !H->R64.reset(c, size_t(n) * H->r_cap) ||
             !H->S64.reset(c, size_t(n) * H->r_cap))
             return fail(KRR_ERR_OOM, "hss_compress: out of memory");
+        // KRR_MIXED_F64: Xp32 is already divided by the problems' widths
         KRR_TRY(widen(c, H->Xp32.get(), n * d, H->Xp64.get()));
-        if (H->nprob > 0) KRR_TRY(scale_by_width(c, H->Xp64.get(), n, d, H->bgrp.get(), H->bh));
-        KRR_TRY(compress<double>(H));
+        if (H->nprob > 0 && !H->tc()) KRR_TRY(scale_by_width(c, H->Xp64.get(), n, d, H->bgrp.get(), H->bh));
     }
+    if (H->f32()) KRR_TRY(compress<float>(H));
+    else KRR_TRY(compress<double>(H));
     // the samples are no longer needed
     H->R32.release();
     H->S32.release();
@@ -1733,7 +1755,7 @@ int hss_build(Ctx *c, const float *X, int64_t n, int d, const krr_options *o, Hs
 int hss_factor_impl(HssImpl *H) {
     H->plan_nrhs = -1;  // the cached solve plan refers to the old factors
     H->drop_graph();
-    return H->mixed() ? factor<float>(H) : factor<double>(H);
+    return H->f32() ? factor<float>(H) : factor<double>(H);
 }
 
 // Solve (K + lambda I) a = y in cluster order: yp, ap device double
@@ -1747,7 +1769,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
     DBuf<double> res(c, size_t(n) * nrhs), norms(c, 2 * nrhs);
     if (!res.get() || !norms.get()) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
     auto ulv = [&](const double *b, double *x) -> int {
-        if (H->mixed()) {
+        if (H->f32()) {
             if (H->ws_bf.n < size_t(n) * nrhs &&
                 (!H->ws_bf.reset(c, size_t(n) * nrhs) || !H->ws_xf.reset(c, size_t(n) * nrhs)))
                 return fail(KRR_ERR_OOM, "hss_solve: out of memory");
@@ -1938,7 +1960,7 @@ int hss_predict_impl(HssImpl *H, const float *Xt, int64_t m, const double *alpha
     if (!ap.get()) return fail(KRR_ERR_OOM, "krr_predict: out of memory");
     KRR_TRY((gather_rows<double, double>(c, alpha, lda, H->perm.get(), n, nrhs, ap.get(), nrhs)));
     DBuf<__half> xa;
-    if (H->mixed()) {
+    if (H->tc()) {
         if (!xa.reset(c, size_t(m) * H->kpad)) return fail(KRR_ERR_OOM, "krr_predict: out of memory");
         KRR_TRY(augment(c, Xt, m, H->d, H->opt.h, 0, xa.get(), H->kpad));
     }
@@ -1958,7 +1980,7 @@ int hss_predict_batched_impl(HssImpl *H, const float *Xt, int64_t m, const std::
     DBuf<double> xs64;
     KRR_CUDA(cudaMemcpyAsync(xs.get(), Xt, size_t(m) * d * 4, cudaMemcpyDeviceToDevice, c->stream));
     KRR_TRY(make_groups(c, toff, tgrp));
-    if (H->mixed()) {
+    if (H->tc()) {
         KRR_TRY(scale_by_width(c, xs.get(), m, d, tgrp.get(), H->bh));
     } else {
         if (!xs64.reset(c, size_t(m) * d)) return fail(KRR_ERR_OOM, "krr_predict_batched: out of memory");
@@ -2141,7 +2163,7 @@ int matvec_t(HssImpl *H, const double *xp, int nrhs, double *yp) {
     KRR_CUDA(cudaMemcpyAsync(doff.get(), off.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
     KRR_CUDA(cudaMemcpyAsync(ids.get(), order.data(), nn * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     const T *F = farena<T>(H);
-    const T *X = H->mixed() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
+    const T *X = H->f32() ? reinterpret_cast<const T *>(H->Xp32.get()) : reinterpret_cast<const T *>(H->Xp64.get());
     const T inv2h2 = T(1.0 / (2.0 * H->opt.h * H->opt.h));
     for (int h = 0; h < H->H; ++h) {
         const int cnt = lvl_start[h + 1] - lvl_start[h];
@@ -2170,7 +2192,7 @@ int hss_matvec_impl(HssImpl *H, const double *x, int nrhs, int64_t ldx, double *
     DBuf<double> xp(c, size_t(n) * nrhs), yp(c, size_t(n) * nrhs);
     if (!xp.get() || !yp.get()) return fail(KRR_ERR_OOM, "hss_matvec: out of memory");
     KRR_TRY((gather_rows<double, double>(c, x, ldx, H->perm.get(), n, nrhs, xp.get(), nrhs)));
-    if (H->mixed()) KRR_TRY(matvec_t<float>(H, xp.get(), nrhs, yp.get()));
+    if (H->f32()) KRR_TRY(matvec_t<float>(H, xp.get(), nrhs, yp.get()));
     else KRR_TRY(matvec_t<double>(H, xp.get(), nrhs, yp.get()));
     KRR_TRY((scatter_rows<double, double>(c, yp.get(), nrhs, H->perm.get(), n, nrhs, y, ldy)));
     return take_status(c, "hss_matvec");
@@ -2309,7 +2331,7 @@ int kprod(HssImpl *H, const __half *XAa, const double *Xa64, int64_t ma, const _
           int64_t nb, const double *V, int64_t ldv, int nv, double *out, int64_t ldo) {
     Ctx *c = H->c;
     if (ma == 0 || nv == 0) return KRR_OK;
-    if (H->mixed()) {
+    if (H->tc()) {
         const int cols = 2 * nv;
         const int rpad = int(round_up(cols, 64));
         const int64_t ldrt = round_up(nb, 8);
@@ -2351,7 +2373,7 @@ int heldout_grad_impl(HssImpl *H, const float *Xt, int64_t m, const double *y, c
     // held-out operands: augmented (mixed) or widened (FP64)
     DBuf<__half> tA, tB;
     DBuf<double> t64;
-    if (H->mixed()) {
+    if (H->tc()) {
         if (!tA.reset(c, size_t(m) * H->kpad) || (full && !tB.reset(c, size_t(m) * H->kpad)))
             return fail(KRR_ERR_OOM, "krr_heldout_grad: out of memory");
         KRR_TRY(augment(c, Xt, m, d, h, 0, tA.get(), H->kpad));
@@ -2417,7 +2439,7 @@ int64_t hss_memory_bytes(const HssImpl *H) {
         if (int(v) != H->root) e += int64_t(N.k) * (N.m - N.k) + N.k;
         if (!N.is_leaf) e += int64_t(H->desc[N.child_a].k) * H->desc[N.child_b].k;
     }
-    return e * (H->mixed() ? 4 : 8);
+    return e * (H->f32() ? 4 : 8);
 }
 
 }  // namespace krr
@@ -2434,10 +2456,11 @@ int hss_compress(krr_ctx *k, const float *X, int64_t n, int32_t d, const krr_opt
     if (out) *out = nullptr;
     if (!k || !X || !o || !out || n <= 0 || d <= 0) return fail(KRR_ERR_INVALID_ARG, "hss_compress: bad arguments");
     if (!(o->h > 0) || !(o->lambda > 0) || !(o->eps_c > 0) || o->eps_abs < 0 || o->leaf < 1 || o->r0 < 1 ||
-        o->p < 0 || o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64) ||
+        o->p < 0 || o->r_max < o->r0 ||
+        (o->precision != KRR_MIXED && o->precision != KRR_FP64 && o->precision != KRR_MIXED_F64) ||
         o->ordering < KRR_ORDER_TWO_MEANS || o->ordering > KRR_ORDER_PCA)
         return fail(KRR_ERR_INVALID_ARG, "hss_compress: bad options");
-    if (o->precision == KRR_MIXED && d > kMaxMixedDim)
+    if (o->precision != KRR_FP64 && d > kMaxMixedDim)
         return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress: mixed path supports d <= 1024");
     if (n > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "hss_compress: n too large");
     krr_hss *H = new (std::nothrow) krr_hss();
@@ -2457,9 +2480,10 @@ int hss_compress_batched(krr_ctx *k, const float *X, int64_t n, int32_t d, int32
     if (!k || !X || !o || !out || !offsets || !h || n <= 0 || d <= 0 || nprob < 1)
         return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: bad arguments");
     if (!(o->lambda > 0) || !(o->eps_c > 0) || o->eps_abs < 0 || o->leaf < 1 || o->r0 < 1 || o->p < 0 ||
-        o->r_max < o->r0 || (o->precision != KRR_MIXED && o->precision != KRR_FP64))
+        o->r_max < o->r0 ||
+        (o->precision != KRR_MIXED && o->precision != KRR_FP64 && o->precision != KRR_MIXED_F64))
         return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: bad options");
-    if (o->precision == KRR_MIXED && d > kMaxMixedDim)
+    if (o->precision != KRR_FP64 && d > kMaxMixedDim)
         return fail(KRR_ERR_NOT_IMPLEMENTED, "hss_compress_batched: mixed path supports d <= 1024");
     if (n > (int64_t(1) << 30)) return fail(KRR_ERR_INVALID_ARG, "hss_compress_batched: n too large");
     std::vector<int64_t> off(offsets, offsets + nprob + 1);

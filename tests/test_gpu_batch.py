@@ -168,3 +168,30 @@ def test_batched_argument_errors(K, ctx):
     with pytest.raises(K.KRRError):
         K.HSS.predict(H, X[:10], a)                    # the single-problem call refuses a batched handle
     H.close()
+
+
+@pytest.mark.parametrize("d,h,eps_c", [(8, 4.0, 0.02), (32, 4.0, 0.05)])
+def test_smooth_group_converges_with_fp64_factorization(K, ctx, d, h, eps_c):
+    """Smooth kernels (d / h^2 <= 2 on standardized data: blocks large next
+    to lambda = 1), which stall in GMRES behind an FP32 factorization: with
+    the decompositions and factorization in FP64 (KRR_MIXED_F64, products
+    still on tensor cores) a batch of such problems (n >= 4096 in all)
+    reaches the tolerance, and every problem's residual against the FP64
+    oracle's operator meets the bound."""
+    sizes = [1500, 2048, 1111]
+    Xs, ys, _, _ = _problems(sizes, d, 70 + d)
+    off = _offsets(Xs)
+    rng = np.random.default_rng(7)
+    Ys = [np.concatenate([y[:, None], rng.standard_normal((len(y), 3))], 1) for y in ys]
+    o = K.default_options(lambda_=1.0, eps_c=eps_c, eps_abs=1e-2, r_max=1024, leaf=128, seed=5,
+                          flags=K.KRR_TRUNCATE_AT_RMAX | K.KRR_LAMBDA_TOL, precision=K.KRR_MIXED_F64)
+    H = K.hss_compress_batched(ctx, torch.from_numpy(np.concatenate(Xs)).cuda(), off, [h] * len(sizes), o)
+    H.factor()
+    tol = 1e-4
+    a, res = H.solve(torch.from_numpy(np.ascontiguousarray(np.concatenate(Ys))).cuda(), tol=tol, max_refine=600)
+    assert 0 <= res <= tol
+    A = a.cpu().numpy()
+    for p in range(len(sizes)):
+        rho = solve.residual(Xs[p].astype(np.float64), h, 1.0, A[off[p]:off[p + 1]], Ys[p])
+        assert rho.max() <= 2 * tol, (p, rho)
+    H.close()
