@@ -75,6 +75,21 @@ def _traffic():
     return int(v) if v else None
 
 
+def _dense_accuracy():
+    """Test accuracy of the exact dense FP64 solve of this workload, written
+    by the oracle into tests/golden/dense_n65536.txt (its inputs are
+    standardized in FP64; the bench's on the GPU: the same data up to FP32
+    rounding)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "dense_n65536.txt")) as f:
+            for line in f:
+                if line.startswith("accuracy:"):
+                    return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
 def _inputs():
     import synth
     X, y, Xt, yt, _, _ = synth.mixture(WL["n"], WL["d"], WL["comps"], WL["sigma"], WL["seed"], WL["m_test"])
@@ -249,6 +264,29 @@ def run_ours(args):
     ach, tk = samp[256]
     peak = float(peaks["bf16_tflops"])
     traffic = _traffic()
+    # arithmetic-pipe rates measured now (krr_probe_rate) and the secondary
+    # bounds: the fused kernel's exponentials (n^2 per launch) against the
+    # SFU's ex2 rate, the FP64 comparator's product against the FP64 FMA rate
+    rates = {"fp32_fma_tflops": ctx.probe_rate(0) / 1e12, "fp64_fma_tflops": ctx.probe_rate(1) / 1e12,
+             "ex2_per_s": ctx.probe_rate(2), "f32_to_f16_per_s": ctx.probe_rate(3)}
+    n64 = 16384
+    Xf = torch.from_numpy(X[:n64].astype(np.float64)).cuda()
+    R64 = torch.from_numpy(np.random.default_rng(7).standard_normal((n64, 64))).cuda()
+    S64 = torch.empty(n64, 64, dtype=torch.float64, device="cuda")
+    K.krr_sample_f64(ctx, Xf, Xf, WL["h"], 0.0, R64, S=S64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    K.krr_sample_f64(ctx, Xf, Xf, WL["h"], 0.0, R64, S=S64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    f64_tflops = 2.0 * n64 * n64 * (d + 64) / t64 / 1e12
+    secondary = {"ex2_frac_r256": (n * n / samp[256][1]) / rates["ex2_per_s"],
+                 "ex2_frac_r64": (n * n / samp[64][1]) / rates["ex2_per_s"],
+                 "tensor_frac_r64": samp[64][0] / peak,
+                 "fp64_product_n16384_r64": {"seconds": t64, "tflops": f64_tflops,
+                                             "frac_of_fp64_fma": f64_tflops / rates["fp64_fma_tflops"]}}
 
     # ---- end to end through host buffers (H2D inputs, D2H weights + predictions inside the timed region)
     Xh = torch.from_numpy(X).pin_memory()
@@ -309,7 +347,8 @@ def run_ours(args):
         "data": "synthetic (seeded Gaussian mixture, SUSY-shaped)",
         "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "quality": {"resid_gpu": res, "test_accuracy": acc, "max_rank": st["max_rank"], "samples": st["samples"],
+        "quality": {"resid_gpu": res, "test_accuracy": acc, "test_accuracy_dense": _dense_accuracy(),
+                    "max_rank": st["max_rank"], "samples": st["samples"],
                     "rounds": st["rounds"], "gmres_iters": st["refine_steps"],
                     "hss_memory_MB": st["memory_bytes"] / 1e6},
         "phases_ms": {k: st[k] for k in ("t_cluster_ms", "t_sample_ms", "t_compress_ms", "t_factor_ms",
@@ -318,7 +357,8 @@ def run_ours(args):
         **extras,
         "sampling": {"tflops_r64": samp[64][0], "ms_r64": 1e3 * samp[64][1], "tflops_r256": samp[256][0],
                      "ms_r256": 1e3 * samp[256][1], "algorithmic_flops": "2 n^2 (d + r)",
-                     "share_of_step": t_sample_frac},
+                     "share_of_step": t_sample_frac, "secondary_bounds": secondary},
+        "measured_rates": rates,
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                      "traffic": traffic,
                      "note": "fused sampling kernel, n=65536, d=8, r=256, one launch timed alone (burst peak, %s)"
@@ -626,6 +666,33 @@ def bench_million(K, ctx, n=1 << 20, r=256, reps=2):
             "algorithmic_flops": "2 n^2 (d + r)"}
 
 
+def solve_only(reps=8):
+    """Compression and factorization of the benchmark workload, then reps
+    single ULV solves (no refinement) of its 10 right-hand sides, for
+    profiling the factor and solve kernels; prints the mean solve time."""
+    import torch
+    import paper_1803_10274_gb300 as K
+    torch.cuda.set_device(0)
+    ctx = K.Context()
+    X, Xt, Y, yt = _inputs()
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    K.krr_standardize(ctx, Xd)
+    o = K.default_options(h=WL["h"], lambda_=WL["lam"], eps_c=WL["eps_c"], leaf=WL["leaf"], precision=K.KRR_MIXED,
+                          seed=WL["seed"], r0=WL["r0"])
+    H = K.hss_compress(ctx, Xd, o)
+    H.factor()
+    H.solve(Yd, tol=0.0)
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(reps):
+        H.solve(Yd, tol=0.0)
+    e1.record(ctx.stream)
+    ctx.sync()
+    print(json.dumps({"n": WL["n"], "nrhs": WL["nrhs"], "ulv_solve_ms": e0.elapsed_time(e1) / reps}), flush=True)
+    H.close()
+
+
 def sample_only(n, r, image=False):
     """Five launches of the fused sampling product on the benchmark's data
     distribution (d=8, standardized), or with image=True on MNIST-shaped
@@ -673,8 +740,44 @@ def cpu_baseline(X):
     s = WL["n"] / n0
     est = (t1 - t0) * s * s + (t2 - t1) * s ** 3
     return {"value": est, "unit": "s", "cores": int(kernel.num_threads()), "kind": "oracle",
+            "timed_n": n0, "timed_seconds": t2 - t0, "extrapolated_to_n": WL["n"],
             "sample": "dense FP64 KRR (C kernel build + LAPACK Cholesky solve, 10 RHS) at n=%d, measured %.2f s, "
                       "extrapolated to n=65536 (build x%.0f, factor/solve x%.0f)" % (n0, t2 - t0, s * s, s ** 3)}
+
+
+def measure_peaks():
+    """Denominators besides MEASURED_PEAKS.json's copy and bf16 matmul:
+    the library's pipe probes (FP32 and FP64 FMA, SFU ex2, FP32 -> FP16
+    conversion) and torch matmuls measured the same way as the bf16 peak
+    (best of 10, CUDA events): FP32 with TF32 tensor cores at 8192^3 and
+    FP64 at 4096^3."""
+    import torch
+    import paper_1803_10274_gb300 as K
+    torch.cuda.set_device(0)
+    ctx = K.Context()
+    out = {"fp32_fma_tflops": ctx.probe_rate(0) / 1e12, "fp64_fma_tflops": ctx.probe_rate(1) / 1e12,
+           "ex2_per_s": ctx.probe_rate(2), "f32_to_f16_per_s": ctx.probe_rate(3)}
+
+    def mm(dt, nn, tf32):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(nn, nn, device="cuda", dtype=dt)
+        b = torch.randn(nn, nn, device="cuda", dtype=dt)
+        for _ in range(3):
+            a @ b
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        return 2.0 * nn ** 3 / best / 1e12
+
+    out["tf32_matmul_tflops"] = mm(torch.float32, 8192, True)
+    out["fp64_matmul_tflops"] = mm(torch.float64, 4096, False)
+    return out
 
 
 def run_reference(args):
@@ -711,6 +814,10 @@ def main():
     ap.add_argument("--image", action="store_true", help="with --sample-only: MNIST-shaped rows (d=784)")
     ap.add_argument("--batch-only", action="store_true", help="only run the MNIST-shaped and batched-problems workloads")
     ap.add_argument("--orderings-only", action="store_true", help="only run the comparison of the orderings")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="only compress, factor and run single ULV solves (for profilers)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the arithmetic-pipe rates and the TF32 / FP64 matmul rates, then exit")
     ap.add_argument("--sample-only", nargs=2, type=int, metavar=("N", "R"),
                     help="only run the fused sampling product at n=N, r=R (5 launches; for profilers)")
     args = ap.parse_args()
@@ -723,6 +830,10 @@ def main():
         ctx = K.Context()
         l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         print(json.dumps({"image_d784": bench_image(K, ctx, l2), "batch": bench_batch(K, ctx, l2)}), flush=True)
+    elif args.solve_only:
+        solve_only()
+    elif args.peaks:
+        print(json.dumps(measure_peaks()), flush=True)
     elif args.orderings_only:
         import torch
         import paper_1803_10274_gb300 as K

@@ -259,9 +259,10 @@ struct GemmBatch {
     int tiles = 0;
     // Skinny products (TN = 16: few output tiles over a long K) are split
     // into K-slices of kSlice that add into C atomically, so one product
-    // spreads over several CTAs; a product that overwrites C has C cleared
-    // first (only in plans, which run the clearing before the GEMMs).
-    static constexpr int kSlice = 256;
+    // spreads over several CTAs (the top levels of the tree have one or two
+    // nodes); a product that overwrites C has C cleared first (only in
+    // plans, which run the clearing before the GEMMs).
+    static constexpr int kSlice = 64;
     bool split_ok = false;
     void add(int M, int N, int K, T alpha, const T *A, int64_t lda, bool ta, const T *B, int64_t ldb, bool tb, T beta,
              T *C, int64_t ldc) {
