@@ -291,36 +291,42 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
     }
 }
 
-// One thread per node: stop test, centre update, accumulator reset.
+// One CTA per node: stop test, centre update (threads over the
+// coordinates), accumulator reset.
 __global__ void update_kernel(int nn, int d, const int64_t *nsize, NodeState *ns, int *n_running) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.x;
     if (v >= nn) return;
     NodeState &S = ns[v];
-    if (S.done) return;
+    if (S.done) return;  // the same for the whole block
+    __shared__ int s_stop0, s_it;
     const int64_t m = nsize[v];
     const int64_t c1 = int64_t(S.cnt1), c0 = m - c1;
-    bool stop = false;
-    if (!S.changed) {
-        stop = true;
-    } else if (c0 == 0 || c1 == 0) {
-        stop = true;
-    } else {
-        for (int k = 0; k < d; ++k) {
+    if (threadIdx.x == 0) {
+        s_stop0 = (!S.changed || c0 == 0 || c1 == 0) ? 1 : 0;
+        s_it = S.it;
+    }
+    __syncthreads();
+    const bool stop0 = s_stop0 != 0;
+    const bool stop = stop0 || s_it + 1 == kMaxIter;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        if (!stop0) {
             S.c0[k] = floor_div(2 * S.sum0[k] + c0, 2 * c0);
             S.c1[k] = floor_div(2 * S.sum1[k] + c1, 2 * c1);
         }
-        S.it += 1;
-        if (S.it == kMaxIter) stop = true;
+        if (!stop) S.sum0[k] = S.sum1[k] = 0;
     }
-    if (stop) {
-        S.done = 1;
-        if (c0 == 0 || c1 == 0) S.halved = 1;
-    } else {
-        S.cnt1 = 0;
-        for (int k = 0; k < d; ++k) S.sum0[k] = S.sum1[k] = 0;
-        S.changed = 0;
-        S.first = 0;
-        atomicAdd(n_running, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!stop0) S.it = s_it + 1;
+        if (stop) {
+            S.done = 1;
+            if (c0 == 0 || c1 == 0) S.halved = 1;
+        } else {
+            S.cnt1 = 0;
+            S.changed = 0;
+            S.first = 0;
+            atomicAdd(n_running, 1);
+        }
     }
 }
 
@@ -783,8 +789,23 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         }
         std::sort(active.begin(), active.end(), [&](int a, int b) { return nodes[a].b < nodes[b].b; });
     }
-    DBuf<int32_t> running(c, 1);
+    DBuf<int32_t> running(c, 2);
     if (!running.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+    // pinned host flags and events of the pipelined convergence check
+    struct IterSync {
+        int *pin = nullptr;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        ~IterSync() {
+            if (pin) cudaFreeHost(pin);
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } isync;
+    KRR_CUDA(cudaMallocHost(&isync.pin, 2 * sizeof(int)));
+    KRR_CUDA(cudaEventCreateWithFlags(&isync.ev[0], cudaEventDisableTiming));
+    KRR_CUDA(cudaEventCreateWithFlags(&isync.ev[1], cudaEventDisableTiming));
+    int *hrun_pin = isync.pin;
+    cudaEvent_t *iter_ev = isync.ev;
     DBuf<int32_t> eqflag;
     if (method == KRR_ORDER_KD && !eqflag.reset(c, n)) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
     while (!active.empty()) {
@@ -809,15 +830,21 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         if (method == KRR_ORDER_TWO_MEANS) {
             { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed, narrow); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
+            // The count of nodes still running is read one iteration late:
+            // iteration t + 1 is queued before the host waits for t's count
+            // (an iteration after the last is a no-op: every node is done).
             for (int iter = 0; iter <= kMaxIter; ++iter) {
-                KRR_CUDA(cudaMemsetAsync(running.get(), 0, 4, st));
+                const int slot = iter & 1;
+                KRR_CUDA(cudaMemsetAsync(running.get() + slot, 0, 4, st));
                 { assign_kernel<<<gn, kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get(), narrow); ::krr::count_launch(); }
-                { update_kernel<<<gv, 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get()); ::krr::count_launch(); }
+                { update_kernel<<<nn, 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get() + slot); ::krr::count_launch(); }
                 KRR_CUDA(cudaGetLastError());
-                int hrun = 0;
-                KRR_CUDA(cudaMemcpyAsync(&hrun, running.get(), 4, cudaMemcpyDeviceToHost, st));
-                KRR_CUDA(cudaStreamSynchronize(st));
-                if (hrun == 0) break;
+                KRR_CUDA(cudaMemcpyAsync(hrun_pin + slot, running.get() + slot, 4, cudaMemcpyDeviceToHost, st));
+                KRR_CUDA(cudaEventRecord(iter_ev[slot], st));
+                if (iter > 0) {
+                    KRR_CUDA(cudaEventSynchronize(iter_ev[slot ^ 1]));
+                    if (hrun_pin[slot ^ 1] == 0) break;
+                }
             }
             { finalize_labels_kernel<<<gn, kTB, 0, st>>>(n, node_of.get(), db.get(), ds.get(), dns.get(), label.get(),
                                                         zflag.get()); ::krr::count_launch(); }
