@@ -347,9 +347,10 @@ __global__ void __launch_bounds__(NT) gram_panel_kernel(const NodeDesc *nd, T *F
 }
 
 // After the factorization, in three steps.  gram_prep_kernel: the unchosen
-// rows appended to piv, skeleton ids and samples, R_loc in pivot order and
-// R-hat's first rows, L gathered into pivot order (m x k row-major in the
-// dmat slot) and the right-hand side L21^T in T's place.  Then T =
+// rows appended to piv, the skeleton ids; gram_copy_kernel (several CTAs
+// per node): skeleton samples, R_loc in pivot order and R-hat's first rows,
+// L gathered into pivot order (m x k row-major in the dmat slot) and the
+// right-hand side L21^T in T's place.  Then T =
 // R11^{-1} R12 (R = L^T) by blocked back substitution: per block of
 // kTrsmBlock rows from the bottom, the triangular diagonal block in one CTA
 // per node (gram_trsm_diag_kernel) and the update of the rows above as a
@@ -357,13 +358,11 @@ __global__ void __launch_bounds__(NT) gram_panel_kernel(const NodeDesc *nd, T *F
 constexpr int kTrsmBlock = 64;
 
 template <class T, int NT>
-__global__ void __launch_bounds__(NT) gram_prep_kernel(const NodeDesc *nd, const NodeDesc *all,
-                                                       const GramState<T> *st, const T *S, const T *R, int64_t ldsr,
-                                                       int r, T *F, int32_t *I) {
+__global__ void __launch_bounds__(NT) gram_prep_kernel(const NodeDesc *nd, const GramState<T> *st, const T *F,
+                                                       int32_t *I) {
     const NodeDesc &N = nd[blockIdx.x];
     const int m = N.m;
     const int k = st[blockIdx.x].k;
-    const T *Lc = F + N.w;
     const T *d = F + N.norm;
     int32_t *piv = I + N.piv;
     int32_t *pos = I + N.ipiv;
@@ -375,11 +374,28 @@ __global__ void __launch_bounds__(NT) gram_prep_kernel(const NodeDesc *nd, const
     }
     __syncthreads();
     for (int a = threadIdx.x; a < m; a += NT) pos[piv[a]] = a;
+    for (int a = threadIdx.x; a < k; a += NT) I[N.jsk + a] = rows[piv[a]];
+}
+
+// The node's data in pivot order, gridDim.y CTAs per node: skeleton
+// samples, R_loc (and R-hat's first k rows), L in pivot order (Lp, lower
+// part) and T's initial value L21^T, read straight from L through the
+// pivot order (T(a, c) = L(piv[k + c], a)).
+template <class T>
+__global__ void __launch_bounds__(256) gram_copy_kernel(const NodeDesc *nd, const NodeDesc *all,
+                                                        const GramState<T> *st, const T *S, const T *R, int64_t ldsr,
+                                                        int r, T *F, const int32_t *I) {
+    const NodeDesc &N = nd[blockIdx.x];
+    const int m = N.m;
+    const int k = st[blockIdx.x].k;
+    const T *Lc = F + N.w;
+    const int32_t *piv = I + N.piv;
+    const int32_t *pos = I + N.ipiv;
+    const int64_t t0 = int64_t(blockIdx.y) * blockDim.x + threadIdx.x, step = int64_t(gridDim.y) * blockDim.x;
     const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
     const int64_t lds = N.is_leaf ? ldsr : r;
     T *Sk = F + N.skel;
-    for (int a = threadIdx.x; a < k; a += NT) I[N.jsk + a] = rows[piv[a]];
-    for (int64_t e = threadIdx.x; e < int64_t(k) * r; e += NT) {
+    for (int64_t e = t0; e < int64_t(k) * r; e += step) {
         const int a = int(e / r), t = int(e % r);
         Sk[e] = Sorig[int64_t(piv[a]) * lds + t];
     }
@@ -387,7 +403,7 @@ __global__ void __launch_bounds__(NT) gram_prep_kernel(const NodeDesc *nd, const
     const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
     T *Rg = F + N.rg;
     T *Rh = F + N.rhat;
-    for (int64_t e = threadIdx.x; e < int64_t(m) * r; e += NT) {
+    for (int64_t e = t0; e < int64_t(m) * r; e += step) {
         const int a = int(e / r), t = int(e % r);
         const int src = piv[a];
         T v;
@@ -397,19 +413,17 @@ __global__ void __launch_bounds__(NT) gram_prep_kernel(const NodeDesc *nd, const
         Rg[e] = v;
         if (a < k) Rh[e] = v;
     }
-    __syncthreads();
     T *Lp = F + N.dmat;
-    for (int64_t e = threadIdx.x; e < int64_t(m) * k; e += NT) {  // reads of Lc coalesced over q
+    for (int64_t e = t0; e < int64_t(m) * k; e += step) {  // reads of Lc coalesced over q
         const int b = int(e / m), q = int(e % m);
         const int a = pos[q];
         Lp[int64_t(a) * k + b] = (b <= a) ? Lc[e] : T(0);
     }
-    __syncthreads();
     T *Tm = F + N.tmat;
     const int nr = m - k;
-    for (int64_t e = threadIdx.x; e < int64_t(k) * nr; e += NT) {
+    for (int64_t e = t0; e < int64_t(k) * nr; e += step) {
         const int a = int(e / nr), c = int(e % nr);
-        Tm[e] = Lp[int64_t(k + c) * k + a];
+        Tm[e] = Lc[int64_t(a) * m + piv[k + c]];
     }
 }
 
@@ -1230,8 +1244,9 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
                                      c->stream));
             KRR_CUDA(cudaStreamSynchronize(c->stream));
-            if (wide) { gram_prep_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), H->ddesc.get(), gs.get(), S, R, H->r_cap, r, F, H->IA.get()); ::krr::count_launch(); }
-            else { gram_prep_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), H->ddesc.get(), gs.get(), S, R, H->r_cap, r, F, H->IA.get()); ::krr::count_launch(); }
+            { gram_prep_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), gs.get(), F, H->IA.get()); ::krr::count_launch(); }
+            { gram_copy_kernel<T><<<dim3(nn, per_node), 256, 0, c->stream>>>(dl.get(), H->ddesc.get(), gs.get(), S, R,
+                                                                             H->r_cap, r, F, H->IA.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             int kmx = 0;
             for (int a = 0; a < nn; ++a) kmx = std::max(kmx, hs[a].k);
