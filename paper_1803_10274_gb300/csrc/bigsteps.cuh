@@ -5,7 +5,9 @@
 // single 1000 x 2000 decomposition spreads over every SM.
 //
 //   * Gauss-Jordan inverse with partial pivoting (the eliminated blocks
-//     and the root block of the ULV-type factorization);
+//     and the root block of the ULV-type factorization), in panels of
+//     kGjPanel pivots: one launch per panel per step, the rest as grouped
+//     GEMMs;
 //   * Householder QR with column pivoting of W^T (pivoting over the rows
 //     of W), stopped at the numerical rank: the row interpolative
 //     decomposition of the node samples.
@@ -29,62 +31,6 @@ struct InvItem {
 };
 
 template <class T>
-__global__ void __launch_bounds__(256) gj_pivot_kernel(const InvItem *items, T *F, int32_t *I, int j,
-                                                       DevStatus *st) {
-    const InvItem it = items[blockIdx.x];
-    const int n = it.n;
-    if (j >= n) return;
-    T *A = F + it.off;
-    T best = T(-1);
-    int bi = 0x7fffffff;
-    for (int i = j + threadIdx.x; i < n; i += 256) {
-        const T v = cta::tabs(A[int64_t(i) * n + j]);
-        if (v > best) { best = v; bi = i; }
-    }
-    cta::argmax_block(best, bi);
-    const int p = bi;
-    if (p != j)
-        for (int c = threadIdx.x; c < n; c += 256) {
-            const T t = A[int64_t(j) * n + c];
-            A[int64_t(j) * n + c] = A[int64_t(p) * n + c];
-            A[int64_t(p) * n + c] = t;
-        }
-    __syncthreads();
-    const T piv = A[int64_t(j) * n + j];
-    if (threadIdx.x == 0) I[it.ipiv + j] = p;
-    if (piv == T(0)) {
-        if (threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 202);
-        return;
-    }
-    __syncthreads();
-    const T inv = T(1) / piv;
-    for (int c = threadIdx.x; c < n; c += 256) {
-        const T v = c == j ? T(1) : A[int64_t(j) * n + c];
-        A[int64_t(j) * n + c] = v * inv;
-    }
-}
-
-// grid: (row blocks of the largest matrix, items)
-template <class T>
-__global__ void __launch_bounds__(256) gj_elim_kernel(const InvItem *items, T *F, int j) {
-    const InvItem it = items[blockIdx.y];
-    const int n = it.n;
-    if (j >= n) return;
-    T *A = F + it.off;
-    const T *rj = A + int64_t(j) * n;
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int i = blockIdx.x * kRowsPerBlock + w; i < min(n, (blockIdx.x + 1) * kRowsPerBlock); i += 8) {
-        if (i == j) continue;
-        T *ri = A + int64_t(i) * n;
-        const T f = ri[j];
-        __syncwarp();
-        if (f == T(0)) continue;
-        for (int c = l; c < n; c += 32) ri[c] = (c == j ? T(0) : ri[c]) - f * rj[c];
-    }
-}
-
-// undo the row interchanges as column interchanges (one CTA per matrix)
-template <class T>
 __global__ void __launch_bounds__(256) gj_unswap_kernel(const InvItem *items, T *F, const int32_t *I) {
     const InvItem it = items[blockIdx.x];
     const int n = it.n;
@@ -99,26 +45,6 @@ __global__ void __launch_bounds__(256) gj_unswap_kernel(const InvItem *items, T 
             }
         __syncthreads();
     }
-}
-
-template <class T>
-int gj_inverse_batched(Ctx *c, const std::vector<InvItem> &items, T *F, int32_t *I) {
-    if (items.empty()) return KRR_OK;
-    int nmax = 0;
-    for (const InvItem &it : items) nmax = it.n > nmax ? it.n : nmax;
-    if (nmax == 0) return KRR_OK;
-    DBuf<InvItem> d(c, items.size());
-    if (!d.get()) return fail(KRR_ERR_OOM, "inverse: out of memory");
-    KRR_CUDA(cudaMemcpyAsync(d.get(), items.data(), items.size() * sizeof(InvItem), cudaMemcpyHostToDevice, c->stream));
-    const int ni = int(items.size());
-    const dim3 eg(unsigned(cdiv(nmax, kRowsPerBlock)), unsigned(ni));
-    for (int j = 0; j < nmax; ++j) {
-        { gj_pivot_kernel<T><<<ni, 256, 0, c->stream>>>(d.get(), F, I, j, c->status); ::krr::count_launch(); }
-        { gj_elim_kernel<T><<<eg, 256, 0, c->stream>>>(d.get(), F, j); ::krr::count_launch(); }
-    }
-    { gj_unswap_kernel<T><<<ni, 256, 0, c->stream>>>(d.get(), F, I); ::krr::count_launch(); }
-    KRR_CUDA(cudaGetLastError());
-    return KRR_OK;
 }
 
 // ------------------------------------------- blocked Gauss-Jordan inverse

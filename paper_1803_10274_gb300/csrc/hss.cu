@@ -1436,8 +1436,9 @@ int factor(HssImpl *H) {
         } else {
             std::vector<big::InvItem> items;
             for (const NodeDesc &N : ld) items.push_back(big::InvItem{N.drr, N.ipiv, is_root ? N.m : N.m - N.k});
-            if (nmax_inv >= 256) KRR_TRY(big::gj_inverse_blocked<T>(c, items, F, H->IA.get()));
-            else KRR_TRY(big::gj_inverse_batched<T>(c, items, F, H->IA.get()));
+            // blocked panels: about 3 launches per 32 pivots (one launch pair
+            // per pivot for the unblocked batched form)
+            KRR_TRY(big::gj_inverse_blocked<T>(c, items, F, H->IA.get()));
         }
         tr.mark("f_invert", h, nn, mmax);
         if (!is_root) {
