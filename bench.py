@@ -181,6 +181,7 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     peaks, peak_src = _peaks()
     ctx = K.Context()
+    ctx.set_autotune(True)  # fused-product launch variants picked by measurement (during warm-up)
     stream = ctx.stream
     X, Xt, Y, yt = _inputs()
     Xd, Xtd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Xt).cuda(), torch.from_numpy(Y).cuda()

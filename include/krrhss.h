@@ -99,6 +99,18 @@ int krr_probe_rate(krr_ctx *ctx, int32_t which, double *ops_per_second);
  * error.  Synchronizes. */
 int krr_sync(krr_ctx *ctx);
 
+/* Autotuning of the fused product's launch variant (enable = 1; 0, the
+ * default, uses fixed rules).  The variants: pairs of row tiles in
+ * clusters of two CTAs sharing every column tile's loads, or one row tile
+ * per CTA; one or two threads issuing the tensor-core MMAs.  With the
+ * autotuner on, the first launch of a shape class (device, feature
+ * chunks, column width, split K, leaf masks, log2 of the tile count) on any
+ * context times every allowed variant on that call (synchronizing) and
+ * caches the fastest for the process; later launches of the class use it.
+ * Skipped while the context's stream is being captured.  The results of
+ * the variants differ only in the order of floating-point additions. */
+int krr_set_autotune(krr_ctx *ctx, int32_t enable);
+
 /* Limit, in SM clock cycles, of each hand-off wait inside the pipelined
  * tensor-core kernels (the fused products) that this context launches from
  * now on; cycles <= 0 restores the default (4e9 cycles, about two seconds).

@@ -58,6 +58,7 @@ SIGNATURES = {
     "krr_launch_count": (ctypes.c_longlong, []),
     "krr_sync": (i32, [P]),
     "krr_set_wait_limit": (i32, [P, i64]),
+    "krr_set_autotune": (i32, [P, i32]),
     "krr_probe_rate": (i32, [P, i32, ctypes.POINTER(f64)]),
     "krr_standardize": (i32, [P, P, i64, i32, P, i64, P, P]),
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),

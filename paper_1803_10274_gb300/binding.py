@@ -82,6 +82,11 @@ class Context:
         check(lib().krr_probe_rate(self.h, int(which), ctypes.byref(v)))
         return v.value
 
+    def set_autotune(self, enable=True):
+        """Time the fused product's launch variants per shape class on first
+        use and keep the fastest (krr_set_autotune)."""
+        check(lib().krr_set_autotune(self.h, 1 if enable else 0))
+
     def set_wait_limit(self, cycles=0):
         """Limit of each device-side hand-off wait of the pipelined kernels
         launched from now on, in SM clock cycles (0: the default)."""

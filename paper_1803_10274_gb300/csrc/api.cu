@@ -121,6 +121,12 @@ int krr_set_wait_limit(krr_ctx *k, int64_t cycles) {
     return KRR_OK;
 }
 
+int krr_set_autotune(krr_ctx *k, int32_t enable) {
+    if (!k || (enable != 0 && enable != 1)) return fail(KRR_ERR_INVALID_ARG, "krr_set_autotune: bad arguments");
+    k->c.autotune = enable != 0;
+    return KRR_OK;
+}
+
 int krr_sync(krr_ctx *k) {
     if (!k) return fail(KRR_ERR_INVALID_ARG, "krr_sync: ctx is NULL");
     KRR_CUDA(cudaStreamSynchronize(k->c.stream));

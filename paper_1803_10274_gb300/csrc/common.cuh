@@ -50,6 +50,7 @@ struct Ctx {
     int num_sms = 0;
     DevStatus *status = nullptr;  // device
     long long wait_cycles = kDefaultWaitCycles;
+    bool autotune = false;  // time the fused product's launch variants per shape class
 };
 
 // A kernel's dynamic shared-memory limit is an attribute of the device's

@@ -28,6 +28,10 @@
 // range ends or crosses a row tile.
 #include <cuda.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "common.cuh"
 #include "prep.cuh"
 #include "tc_ptx.cuh"
@@ -681,6 +685,115 @@ int make_map(CUtensorMap *m, const void *base, int64_t cols, int64_t rows, int64
     return KRR_OK;
 }
 
+// One launch of variant v (bit 1: pairs of row tiles in clusters of two
+// CTAs, bit 0: two MMA-issuing threads); P describes single row tiles.
+int launch_variant(Ctx *c, int v, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mR, tc::Params P,
+                   size_t smem, const __half *XB, int kpad, int box_k, int64_t nb, bool narrow) {
+    const bool pair = (v & 2) != 0, two = (v & 1) != 0;
+    auto kernel = pair ? (two ? tc::sample_tc_kernel<true, true> : tc::sample_tc_kernel<true, false>)
+                       : (two ? tc::sample_tc_kernel<false, true> : tc::sample_tc_kernel<false, false>);
+    static SmemLimitOnce smem_limit[4];
+    KRR_CUDA(raise_smem_limit(smem_limit[v & 3], c->device, kernel, 227 * 1024));
+    if (!pair) {
+        const int64_t T = P.n_tiles;
+        const int grid = int(T < c->num_sms ? T : c->num_sms);
+        { kernel<<<grid, tc::kThreads, smem, c->stream>>>(mA, mB, mR, P); ::krr::count_launch(); }
+        KRR_CUDA(cudaGetLastError());
+        return KRR_OK;
+    }
+    CUtensorMap mBh;
+    KRR_TRY(make_map(&mBh, XB, kpad, nb, kpad, box_k, tc::kBN / 2, narrow));  // half-tile boxes
+    P.n_row_tiles = cdiv(P.n_row_tiles, 2);  // row units of two row tiles
+    P.n_tiles = P.n_row_tiles * P.n_col_tiles;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(tc::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // clusters that can be resident at once (one CTA per SM), per device
+    static std::atomic<int> max_clusters[kMaxDevices][2];
+    const bool cached = c->device >= 0 && c->device < kMaxDevices;
+    int mc = cached ? max_clusters[c->device][two ? 1 : 0].load() : 0;
+    if (mc <= 0) {
+        cfg.gridDim = dim3(2 * (c->num_sms / 2));
+        KRR_CUDA(cudaOccupancyMaxActiveClusters(&mc, kernel, &cfg));
+        if (mc <= 0) return fail(KRR_ERR_CUDA, "sample_tc: no cluster of two CTAs fits on the device");
+        if (cached) max_clusters[c->device][two ? 1 : 0].store(mc);
+    }
+    const int64_t units = P.n_tiles < mc ? P.n_tiles : mc;
+    cfg.gridDim = dim3(unsigned(2 * units));
+    KRR_CUDA(cudaLaunchKernelEx(&cfg, kernel, mA, mBh, mR, P));
+    ::krr::count_launch();
+    return KRR_OK;
+}
+
+// The fused product's autotuner: a shape class (device, feature chunks,
+// narrow rows, column width, split K, leaf masks, log2 of the tile count)
+// maps to the fastest variant measured on its first launch.  Each trial
+// clears this launch's block of S, runs one variant and times it with CUDA
+// events; the winner runs last, so S holds its result.
+struct TuneKey {
+    int device, nchunk, narrow, rpad, split_k, masked, tiles_log2;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, nchunk, narrow, rpad, split_k, masked, tiles_log2) <
+               std::tie(o.device, o.nchunk, o.narrow, o.rpad, o.split_k, o.masked, o.tiles_log2);
+    }
+};
+
+int tune_variant(Ctx *c, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mR, const tc::Params &P,
+                 size_t smem, const __half *XB, int kpad, int box_k, int64_t nb, bool narrow, bool pair_ok, float *S,
+                 int64_t lds, int &variant) {
+    static std::mutex mu;
+    static std::map<TuneKey, int> cache;
+    int tl = 0;
+    for (int64_t t = P.n_tiles; t > 1; t >>= 1) ++tl;
+    const TuneKey key{c->device, P.nchunk, narrow ? 1 : 0, P.r, P.split_k, P.leaf_a != nullptr ? 1 : 0, tl};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            variant = it->second;
+            return KRR_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    KRR_CUDA(cudaEventCreate(&e0));
+    KRR_CUDA(cudaEventCreate(&e1));
+    int best = variant;
+    float best_ms = 0.f;
+    for (int v = pair_ok ? 3 : 1; v >= 0; --v) {
+        KRR_CUDA(cudaMemset2DAsync(S, size_t(lds) * 4, 0, size_t(P.r_valid) * 4, size_t(P.ma), c->stream));
+        KRR_CUDA(cudaEventRecord(e0, c->stream));
+        const int st = launch_variant(c, v, mA, mB, mR, P, smem, XB, kpad, box_k, nb, narrow);
+        if (st != KRR_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        KRR_CUDA(cudaEventRecord(e1, c->stream));
+        KRR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        KRR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (v == (pair_ok ? 3 : 1) || ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    KRR_CUDA(cudaMemset2DAsync(S, size_t(lds) * 4, 0, size_t(P.r_valid) * 4, size_t(P.ma), c->stream));
+    variant = best;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+    return KRR_OK;
+}
+
 }  // namespace
 
 // S (+)= W o K(XA rows, XB rows) RT^T, accumulated atomically into S
@@ -760,55 +873,25 @@ int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int
     P.wait = c->wait_cycles;
 
     if (P.n_tiles <= 0) return KRR_OK;
-    // Pairs of row tiles share every column tile's loads (clusters of two
-    // CTAs, multicast); block-diagonal tile lists keep one row tile per CTA.
-#ifndef KRR_PAIR_OFF
-    const bool pair = bd == nullptr && P.n_row_tiles >= 2;
-#else
-    const bool pair = false;
+    // Variant: pairs of row tiles sharing every column tile's loads
+    // (clusters of two CTAs, multicast; not for block-diagonal tile lists)
+    // and one or two MMA-issuing threads.  Rules measured on GB300: pairs
+    // whenever allowed; two issuers where each tile's MMAs are small
+    // (+22 % at r = 64, 5 % slower at r = 256).  With the context's
+    // autotuner on, the first launch of a shape class times every allowed
+    // variant on this very call and caches the fastest per device.
+    const bool pair_ok = bd == nullptr && P.n_row_tiles >= 2;
+    int variant = (pair_ok ? 2 : 0) + ((rpad <= 128 || split_k) ? 1 : 0);
+#ifdef KRR_PAIR_OFF
+    variant &= 1;
 #endif
-    // two issuing threads where each tile's MMAs are small (measured: +22 %
-    // at r = 64, 5 % slower at r = 256)
-    const bool two = rpad <= 128 || split_k;
-    auto kernel = pair ? (two ? tc::sample_tc_kernel<true, true> : tc::sample_tc_kernel<true, false>)
-                       : (two ? tc::sample_tc_kernel<false, true> : tc::sample_tc_kernel<false, false>);
-    static SmemLimitOnce smem_limit[4];
-    KRR_CUDA(raise_smem_limit(smem_limit[(pair ? 2 : 0) + (two ? 1 : 0)], c->device, kernel, 227 * 1024));
-    if (!pair) {
-        const int64_t T = P.n_tiles;
-        const int grid = int(T < c->num_sms ? T : c->num_sms);
-        { kernel<<<grid, tc::kThreads, smem, c->stream>>>(mA, mB, mR, P); ::krr::count_launch(); }
-        KRR_CUDA(cudaGetLastError());
-        return KRR_OK;
+    if (c->autotune && bd == nullptr) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        KRR_CUDA(cudaStreamIsCapturing(c->stream, &cs));
+        if (cs == cudaStreamCaptureStatusNone) KRR_TRY(tune_variant(c, mA, mB, mR, P, smem, XB, kpad, box_k, nb,
+                                                                    narrow, pair_ok, S, lds, variant));
     }
-    KRR_TRY(make_map(&mB, XB, kpad, nb, kpad, box_k, tc::kBN / 2, narrow));  // half-tile boxes
-    P.n_row_tiles = cdiv(P.n_row_tiles, 2);  // row units of two row tiles
-    P.n_tiles = P.n_row_tiles * P.n_col_tiles;
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(tc::kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = c->stream;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // clusters that can be resident at once (one CTA per SM), per device
-    static std::atomic<int> max_clusters[kMaxDevices];
-    int mc = (c->device >= 0 && c->device < kMaxDevices) ? max_clusters[c->device].load() : 0;
-    if (mc <= 0) {
-        cfg.gridDim = dim3(2 * (c->num_sms / 2));
-        KRR_CUDA(cudaOccupancyMaxActiveClusters(&mc, kernel, &cfg));
-        if (mc <= 0) return fail(KRR_ERR_CUDA, "sample_tc: no cluster of two CTAs fits on the device");
-        if (c->device >= 0 && c->device < kMaxDevices) max_clusters[c->device].store(mc);
-    }
-    const int64_t units = P.n_tiles < mc ? P.n_tiles : mc;
-    cfg.gridDim = dim3(unsigned(2 * units));
-    KRR_CUDA(cudaLaunchKernelEx(&cfg, kernel, mA, mB, mR, P));
-    ::krr::count_launch();
-    return KRR_OK;
+    return launch_variant(c, variant, mA, mB, mR, P, smem, XB, kpad, box_k, nb, narrow);
 }
 
 }  // namespace krr

@@ -169,3 +169,27 @@ def test_random_block_matches_oracle(K, ctx):
     ulp = np.abs(np.spacing(w16.astype(np.float16))).astype(np.float64)
     assert np.all(diff <= ulp)                      # equal except a rare rounding tie
     assert np.mean(diff == 0) > 0.999
+
+
+@pytest.mark.parametrize("ma,nb,d,r,masked", [(3000, 2500, 8, 64, False), (2048, 2048, 8, 256, True),
+                                              (1500, 1500, 30, 100, False)])
+def test_autotuned_product_matches_oracle(K, ma, nb, d, r, masked):
+    """With the autotuner on, the first call of a shape class times every
+    launch variant on the call itself (clearing S before each trial) and
+    leaves the fastest one's result; the second call uses the cached
+    choice.  Both match the oracle at the mixed bound."""
+    c = K.Context()
+    try:
+        c.set_autotune(True)
+        Xa = synth.mixture(ma, d, 4, 0.7, 60 + d)[0].astype(np.float32)
+        Xb = synth.mixture(nb, d, 4, 0.7, 61 + d)[0].astype(np.float32) if not masked else Xa
+        R = synth.gaussian_block(Xb.shape[0], r, 62).astype(np.float32)
+        leaf = (np.arange(Xa.shape[0]) // 128).astype(np.int32) if masked else None
+        args = [_cuda(leaf), _cuda(leaf)] if masked else []
+        ref, ref_abs = kernel.kernel_product(Xa, Xb, 1.1, R, leaf, leaf, want_abs=True)
+        for _ in range(2):
+            S = K.krr_sample(c, _cuda(Xa), _cuda(Xb), 1.1, 0.0, _cuda(R), *args)
+            c.sync()
+            assert np.all(np.abs(S.cpu().numpy() - ref) <= _mixed_tol(ref_abs, R))
+    finally:
+        c.close()
