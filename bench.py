@@ -694,6 +694,33 @@ def solve_only(reps=8):
     H.close()
 
 
+def step_only(steps, warmup):
+    """warmup + steps whole KRR steps of the benchmark workload (standardize,
+    compress, factor, GMRES, predict) with nothing else around them, for
+    launch lists under a profiler; prints the phase times of the last step."""
+    import torch
+    import paper_1803_10274_gb300 as K
+    torch.cuda.set_device(0)
+    ctx = K.Context()
+    X, Xt, Y, yt = _inputs()
+    Xd, Xtd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Xt).cuda(), torch.from_numpy(Y).cuda()
+    o = K.default_options(h=WL["h"], lambda_=WL["lam"], eps_c=WL["eps_c"], leaf=WL["leaf"], precision=K.KRR_MIXED,
+                          seed=WL["seed"], r0=WL["r0"])
+    st = None
+    for _ in range(warmup + steps):
+        Xs, Xts = Xd.clone(), Xtd.clone()
+        K.krr_standardize(ctx, Xs, Xts)
+        H = K.hss_compress(ctx, Xs, o)
+        H.factor()
+        a, res = H.solve(Yd, tol=0.5 * 10 * WL["eps"], max_refine=200)
+        H.predict(Xts, a[:, :1].contiguous())
+        st = H.stats()
+        H.close()
+    ctx.sync()
+    print(json.dumps({k: st[k] for k in ("t_cluster_ms", "t_compress_ms", "t_factor_ms", "t_solve_ms",
+                                         "refine_steps")}), flush=True)
+
+
 def sample_only(n, r, image=False):
     """Five launches of the fused sampling product on the benchmark's data
     distribution (d=8, standardized), or with image=True on MNIST-shaped
@@ -817,6 +844,8 @@ def main():
     ap.add_argument("--orderings-only", action="store_true", help="only run the comparison of the orderings")
     ap.add_argument("--solve-only", action="store_true",
                     help="only compress, factor and run single ULV solves (for profilers)")
+    ap.add_argument("--step-only", action="store_true",
+                    help="only run --warmup + --steps KRR steps, nothing else (for launch lists)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the arithmetic-pipe rates and the TF32 / FP64 matmul rates, then exit")
     ap.add_argument("--sample-only", nargs=2, type=int, metavar=("N", "R"),
@@ -833,6 +862,8 @@ def main():
         print(json.dumps({"image_d784": bench_image(K, ctx, l2), "batch": bench_batch(K, ctx, l2)}), flush=True)
     elif args.solve_only:
         solve_only()
+    elif args.step_only:
+        step_only(args.steps, args.warmup)
     elif args.peaks:
         print(json.dumps(measure_peaks()), flush=True)
     elif args.orderings_only:

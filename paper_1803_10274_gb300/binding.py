@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import atexit
 import ctypes
+import weakref
 
 import torch
 
@@ -51,6 +52,7 @@ class Context:
         self.stream = stream or torch.cuda.current_stream()
         self.device = torch.cuda.current_device()
         self._keep = []
+        self._handles = weakref.WeakSet()  # HSS handles made on this context
         al = None
         if torch_allocator:
             dev, st = self.device, self.stream
@@ -94,6 +96,9 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            # handles made on this context are freed through it: close them first
+            for hss in list(getattr(self, "_handles", ())):
+                hss.close()
             if not _shutting_down[0]:
                 lib().krr_destroy(self.h)
             self.h = None
@@ -265,6 +270,7 @@ class HSS:
 
     def __init__(self, ctx, handle, n):
         self.ctx, self.h, self.n = ctx, handle, n
+        ctx._handles.add(self)
 
     def factor(self):
         check(lib().hss_factor(self.h))
@@ -349,7 +355,8 @@ class HSS:
 
     def close(self):
         if getattr(self, "h", None):
-            if not _shutting_down[0]:
+            # after its context's close the handle is already gone
+            if not _shutting_down[0] and getattr(self.ctx, "h", None):
                 lib().hss_destroy(self.h)
             self.h = None
 

@@ -244,3 +244,17 @@ def test_argument_and_budget_errors(K, ctx):
     with pytest.raises(K.KRRError) as e:
         K.hss_compress(ctx, Xn, K.default_options())
     assert e.value.code == 2            # KRR_ERR_NONFINITE_INPUT
+
+
+def test_handle_outliving_its_context(K):
+    """An HSS handle still open when its context closes is destroyed with
+    the context first; its own close (or garbage collection) afterwards is
+    a no-op instead of a use of the freed context."""
+    c = K.Context()
+    X, y, *_ = synth.mixture(500, 4, 3, 0.7, 8)
+    o = K.default_options(h=1.0, lambda_=1.0, eps_c=0.05, leaf=64, precision=K.KRR_MIXED, seed=1)
+    H = K.hss_compress(c, torch.from_numpy(X.astype(np.float32)).cuda(), o)
+    c.close()
+    assert H.h is None
+    H.close()
+    del H

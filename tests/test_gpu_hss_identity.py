@@ -29,9 +29,12 @@ def _kappa(X, h, lam):
     return float(w[-1] / w[0])
 
 
-@pytest.mark.parametrize("prec,eps_c,n", [("fp64", 1e-4, 2048), ("fp64", 1e-6, 2048), ("mixed", 0.05, 2048),
-                                          ("mixed", 0.05, 8192)])
-def test_hss_matvec_and_ulv_identity(prec, eps_c, n):
+@pytest.mark.parametrize("prec,eps_c,n,r0", [("fp64", 1e-4, 2048, 64), ("fp64", 1e-6, 2048, 64),
+                                             ("mixed", 0.05, 2048, 64), ("mixed", 0.05, 8192, 64),
+                                             ("fp64", 1e-4, 2048, 16), ("mixed", 0.05, 8192, 16)])
+def test_hss_matvec_and_ulv_identity(prec, eps_c, n, r0):
+    """r0 = 16: several adaptive rounds (every decomposition recomputed with
+    the doubled sample count); the same gates hold."""
     import paper_1803_10274_gb300 as K
     h, lam, leaf = 1.0, 1.0, 64
     X = synth.mixture(n, 8, 8, 0.7, 51)[0]
@@ -41,10 +44,12 @@ def test_hss_matvec_and_ulv_identity(prec, eps_c, n):
     ctx = K.Context()
     try:
         P = K.KRR_FP64 if prec == "fp64" else K.KRR_MIXED
-        o = K.default_options(h=h, lambda_=lam, eps_c=eps_c, leaf=leaf, precision=P, seed=3)
+        o = K.default_options(h=h, lambda_=lam, eps_c=eps_c, leaf=leaf, precision=P, seed=3, r0=r0)
         H = K.hss_compress(ctx, torch.from_numpy(Z).cuda(), o)
         st = H.stats()
         assert 0 < st["max_rank"] < n // 2          # real ranks, neither 0 nor full
+        if r0 == 16:
+            assert st["rounds"] >= 3, st
         xd = torch.from_numpy(x).cuda()
         Hx = H.matvec(xd)
         Ax = kernel.kernel_product(Zo, Zo, h, x) + lam * x
