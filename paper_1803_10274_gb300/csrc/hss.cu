@@ -427,24 +427,48 @@ __global__ void __launch_bounds__(256) gram_copy_kernel(const NodeDesc *nd, cons
     }
 }
 
-// Rows [a0, min(a1, k)) of T: back substitution with the diagonal block of L11^T.
-template <class T, int NT>
-__global__ void __launch_bounds__(NT) gram_trsm_diag_kernel(const NodeDesc *nd, const GramState<T> *st, T *F, int a0,
-                                                            int a1) {
+// Rows [a0, min(a1, k)) of T: back substitution with the diagonal block of
+// L11^T.  The columns of T are independent: gridDim.y CTAs of 128 threads
+// per node, one column per thread held in registers, the diagonal block of
+// L staged in shared memory (zero outside the block, so the fixed-size
+// loops add exact zeros past its end).
+constexpr int kTrsmCols = 128;
+
+template <class T>
+__global__ void __launch_bounds__(kTrsmCols) gram_trsm_diag_kernel(const NodeDesc *nd, const GramState<T> *st, T *F,
+                                                                   int a0, int a1) {
     const NodeDesc &N = nd[blockIdx.x];
     const int k = st[blockIdx.x].k;
     const int hi = min(a1, k);
-    if (hi <= a0) return;
     const int nr = N.m - k;
+    const int c0 = int(blockIdx.y) * kTrsmCols;
+    if (hi <= a0 || c0 >= nr) return;
+    const int nb = hi - a0;
+    __shared__ T Ls[kTrsmBlock][kTrsmBlock + 1];  // Ls[b][a] = L(a0 + b, a0 + a), b >= a
     const T *Lp = F + N.dmat;
+    for (int e = threadIdx.x; e < kTrsmBlock * kTrsmBlock; e += kTrsmCols) {
+        const int b = e / kTrsmBlock, a = e % kTrsmBlock;
+        Ls[b][a] = (a <= b && b < nb) ? Lp[int64_t(a0 + b) * k + a0 + a] : T(0);
+    }
+    __syncthreads();
+    const int c = c0 + int(threadIdx.x);
+    if (c >= nr) return;
     T *Tm = F + N.tmat;
-    for (int c = threadIdx.x; c < nr; c += NT) {
-        for (int a = hi - 1; a >= a0; --a) {
-            T sacc = Tm[int64_t(a) * nr + c];
-            for (int b = a + 1; b < hi; ++b) sacc -= Lp[int64_t(b) * k + a] * Tm[int64_t(b) * nr + c];
-            Tm[int64_t(a) * nr + c] = sacc / Lp[int64_t(a) * k + a];
+    T x[kTrsmBlock];
+#pragma unroll
+    for (int a = 0; a < kTrsmBlock; ++a) x[a] = a < nb ? Tm[int64_t(a0 + a) * nr + c] : T(0);
+#pragma unroll
+    for (int a = kTrsmBlock - 1; a >= 0; --a) {
+        if (a < nb) {
+            T sacc = x[a];
+#pragma unroll
+            for (int b = a + 1; b < kTrsmBlock; ++b) sacc -= Ls[b][a] * x[b];
+            x[a] = sacc / Ls[a][a];
         }
     }
+#pragma unroll
+    for (int a = 0; a < kTrsmBlock; ++a)
+        if (a < nb) Tm[int64_t(a0 + a) * nr + c] = x[a];
 }
 
 template <class T, int NT>
@@ -571,20 +595,22 @@ __global__ void __launch_bounds__(cta::kNT) factor_build_kernel(const NodeDesc *
         if (a < ka) return F[N.bmat + int64_t(a) * kb + (b - ka)];
         return F[N.bmat + int64_t(b) * kb + (a - ka)];
     };
+    // gridDim.y CTAs share a node (the top levels have few, large nodes)
+    const int64_t t0 = int64_t(blockIdx.y) * blockDim.x + threadIdx.x, step = int64_t(gridDim.y) * blockDim.x;
     if (is_root) {
-        for (int64_t e = threadIdx.x; e < int64_t(m) * m; e += blockDim.x) F[N.drr + e] = dval(int(e / m), int(e % m));
+        for (int64_t e = t0; e < int64_t(m) * m; e += step) F[N.drr + e] = dval(int(e / m), int(e % m));
         return;
     }
     const int k = N.k, nr = m - k;
     const int32_t *piv = I + N.piv;
-    for (int64_t e = threadIdx.x; e < int64_t(k) * k; e += blockDim.x)
+    for (int64_t e = t0; e < int64_t(k) * k; e += step)
         F[N.dtil + e] = dval(piv[e / k], piv[e % k]);
-    for (int64_t e = threadIdx.x; e < int64_t(nr) * k; e += blockDim.x) {
+    for (int64_t e = t0; e < int64_t(nr) * k; e += step) {
         const T v = dval(piv[k + e / k], piv[e % k]);
         F[N.dmat + e] = v;
         F[N.drs + e] = v;
     }
-    for (int64_t e = threadIdx.x; e < int64_t(nr) * nr; e += blockDim.x)
+    for (int64_t e = t0; e < int64_t(nr) * nr; e += step)
         F[N.drr + e] = dval(piv[k + e / nr], piv[k + e % nr]);
 }
 
@@ -1248,11 +1274,15 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             { gram_copy_kernel<T><<<dim3(nn, per_node), 256, 0, c->stream>>>(dl.get(), H->ddesc.get(), gs.get(), S, R,
                                                                              H->r_cap, r, F, H->IA.get()); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
-            int kmx = 0;
-            for (int a = 0; a < nn; ++a) kmx = std::max(kmx, hs[a].k);
+            int kmx = 0, nrmx = 0;
+            for (int a = 0; a < nn; ++a) {
+                kmx = std::max(kmx, hs[a].k);
+                nrmx = std::max(nrmx, lvdesc[a].m - hs[a].k);
+            }
+            const unsigned tcb = unsigned(std::max<int64_t>(1, cdiv(nrmx, kTrsmCols)));
             for (int a1 = int(round_up(kmx, kTrsmBlock)); a1 > 0; a1 -= kTrsmBlock) {
                 const int a0 = a1 - kTrsmBlock;
-                { gram_trsm_diag_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), gs.get(), F, a0, a1); ::krr::count_launch(); }
+                { gram_trsm_diag_kernel<T><<<dim3(nn, tcb), kTrsmCols, 0, c->stream>>>(dl.get(), gs.get(), F, a0, a1); ::krr::count_launch(); }
                 KRR_CUDA(cudaGetLastError());
                 if (a0 == 0) break;
                 // rows [0, a0) of T -= (L(a0:a1, 0:a0))^T T(a0:a1, :)
@@ -1410,7 +1440,8 @@ int factor(HssImpl *H) {
         DBuf<NodeDesc> dl(c, nn);
         if (!dl.get()) return fail(KRR_ERR_OOM, "hss_factor: out of memory");
         KRR_CUDA(cudaMemcpyAsync(dl.get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
-        { factor_build_kernel<T><<<nn, cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), X, H->d, inv2h2,
+        const unsigned per_node = unsigned(std::max(1, std::min(64, 4 * c->num_sms / nn)));
+        { factor_build_kernel<T><<<dim3(nn, per_node), cta::kNT, 0, c->stream>>>(dl.get(), H->ddesc.get(), X, H->d, inv2h2,
                                                                  T(H->lambda), F, H->IA.get(), is_root); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         if (!is_root) {
