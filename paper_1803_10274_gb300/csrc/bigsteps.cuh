@@ -133,6 +133,96 @@ __global__ void __launch_bounds__(1024) gjb_panel_kernel(const InvItem *items, T
     }
 }
 
+// The same panel with its n x kGjPanel block staged in shared memory (row
+// stride kGjPanel + 1, so column reads hit distinct banks): the pivot
+// search, scaling and eliminations run there, latency-free; only the row
+// interchanges of the columns outside the panel touch global memory.
+constexpr int kGjLd = kGjPanel + 1;
+constexpr int kGjSmemMax = 200 * 1024;  // panel bytes staged in shared memory at most
+
+template <class T>
+__global__ void __launch_bounds__(1024) gjb_panel_smem_kernel(const InvItem *items, T *F, int32_t *I, int j0,
+                                                             DevStatus *st) {
+    extern __shared__ __align__(16) unsigned char gj_smem[];
+    T *P = reinterpret_cast<T *>(gj_smem);  // P[i * kGjLd + c] = A(i, j0 + c)
+    const InvItem it = items[blockIdx.x];
+    const int n = it.n;
+    if (j0 >= n) return;
+    T *A = F + it.off;
+    const int jend = min(j0 + kGjPanel, n), b = jend - j0;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __shared__ T sv[32];
+    __shared__ int si[32];
+    for (int i = w; i < n; i += 32) P[i * kGjLd + l] = l < b ? A[int64_t(i) * n + j0 + l] : T(0);
+    __syncthreads();
+    for (int j = j0; j < jend; ++j) {
+        const int jl = j - j0;
+        T best = T(-1);
+        int bi = 0x7fffffff;
+        for (int i = j + threadIdx.x; i < n; i += 1024) {
+            const T v = cta::tabs(P[i * kGjLd + jl]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (l == 0) { sv[w] = best; si[w] = bi; }
+        __syncthreads();
+        if (w == 0) {
+            best = sv[l];
+            bi = si[l];
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (l == 0) { sv[0] = best; si[0] = bi; }
+        }
+        __syncthreads();
+        const int p = si[0];
+        if (p != j) {
+            for (int c = threadIdx.x; c < n - b; c += 1024) {  // columns outside the panel
+                const int cc = c < j0 ? c : c + b;
+                const T t = A[int64_t(j) * n + cc];
+                A[int64_t(j) * n + cc] = A[int64_t(p) * n + cc];
+                A[int64_t(p) * n + cc] = t;
+            }
+            if (w == 0) {
+                const T t = P[j * kGjLd + l];
+                P[j * kGjLd + l] = P[p * kGjLd + l];
+                P[p * kGjLd + l] = t;
+            }
+        }
+        if (threadIdx.x == 0) I[it.ipiv + j] = p;
+        __syncthreads();
+        const T piv = P[j * kGjLd + jl];
+        if (piv == T(0)) {
+            if (threadIdx.x == 0) dev_fail(st, KRR_ERR_SINGULAR, 204);
+            return;  // every thread read the same pivot
+        }
+        const T inv = T(1) / piv;
+        __syncthreads();
+        if (w == 0 && l < b) {
+            const T v = l == jl ? T(1) : P[j * kGjLd + l];
+            P[j * kGjLd + l] = v * inv;
+        }
+        __syncthreads();
+        // other rows, panel columns: lane c of a warp owns panel column c
+        const T rj = P[j * kGjLd + l];
+        for (int i = w; i < n; i += 32) {
+            if (i == j) continue;
+            const T f = P[i * kGjLd + jl];
+            __syncwarp();
+            P[i * kGjLd + l] = (l == jl ? T(0) : P[i * kGjLd + l]) - f * rj;
+        }
+        __syncthreads();
+    }
+    for (int i = w; i < n; i += 32)
+        if (l < b) A[int64_t(i) * n + j0 + l] = P[i * kGjLd + l];
+}
+
 // Rows [j0, jend) outside the panel's columns: copied to Tt (kGjPanel rows
 // of n - (jend - j0), in column order with the panel removed) and zeroed.
 template <class T>
@@ -166,8 +256,17 @@ int gj_inverse_blocked(Ctx *c, const std::vector<InvItem> &items, T *F, int32_t 
     DBuf<T> Tt(c, size_t(ni) * tstride);
     if (!d.get() || !Tt.get()) return fail(KRR_ERR_OOM, "inverse: out of memory");
     KRR_CUDA(cudaMemcpyAsync(d.get(), items.data(), ni * sizeof(InvItem), cudaMemcpyHostToDevice, c->stream));
+    const size_t psmem = size_t(nmax) * kGjLd * sizeof(T);
+    const bool staged = psmem <= size_t(kGjSmemMax);
+    if (staged) {
+        static SmemLimitOnce smem_limit;
+        KRR_CUDA(raise_smem_limit(smem_limit, c->device, gjb_panel_smem_kernel<T>, kGjSmemMax));
+    }
     for (int j0 = 0; j0 < nmax; j0 += kGjPanel) {
-        { gjb_panel_kernel<T><<<ni, 1024, 0, c->stream>>>(d.get(), F, I, j0, c->status); ::krr::count_launch(); }
+        if (staged)
+            { gjb_panel_smem_kernel<T><<<ni, 1024, psmem, c->stream>>>(d.get(), F, I, j0, c->status); ::krr::count_launch(); }
+        else
+            { gjb_panel_kernel<T><<<ni, 1024, 0, c->stream>>>(d.get(), F, I, j0, c->status); ::krr::count_launch(); }
         const dim3 cg(unsigned(std::min<int64_t>(cdiv(int64_t(kGjPanel) * nmax, 256), 64)), unsigned(ni));
         { gjb_copyout_kernel<T><<<cg, 256, 0, c->stream>>>(d.get(), F, Tt.get(), tstride, j0); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
