@@ -129,22 +129,26 @@ struct SkinnyCfg {
     }
 };
 
+// One output tile of a skinny product list, by a CTA of 256 threads with
+// SkinnyCfg<T>::smem() bytes of shared memory (every thread calls it).
+// tp: the problem of every tile (plans), or NULL (binary search over tile0).
 template <class T>
-__global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *probs, int np, int total_tiles) {
+__device__ void skinny_tile(const GemmProb<T> *probs, int np, int tile, unsigned char *smem, const int32_t *tp) {
     constexpr int KB = SkinnyCfg<T>::KB;
-    extern __shared__ __align__(16) unsigned char skinny_smem[];
-    T *Bs = reinterpret_cast<T *>(skinny_smem);  // KB x 16
+    T *Bs = reinterpret_cast<T *>(smem);          // KB x 16
     T *red = Bs + KB * 16;                        // [4][64][16]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     T *tw = red + 4 * 64 * 16 + warp * 32 * 33;   // this warp's 32 x 33 transpose tile
     const int row = 32 * (warp & 1) + lane, grp = warp >> 1;
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    {
         int lo = 0, hi = np - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (probs[mid].tile0 <= tile) lo = mid;
-            else hi = mid - 1;
-        }
+        if (tp) lo = tp[tile];
+        else
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (probs[mid].tile0 <= tile) lo = mid;
+                else hi = mid - 1;
+            }
         const GemmProb<T> &P = probs[lo];
         const int t = tile - P.tile0;
         const int i0 = (t / P.tn) * 64, j0 = (t % P.tn) * 16;
@@ -158,7 +162,10 @@ __global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *pro
             __syncthreads();
             for (int e = tid; e < kbn * 16; e += 256) {
                 const int k = e >> 4, c = e & 15;
-                Bs[e] = c < nc ? (P.tb ? P.B[int64_t(j0 + c) * P.ldb + kb0 + k] : P.B[int64_t(kb0 + k) * P.ldb + j0 + c])
+                // B (a right-hand-side block another CTA may have written
+                // earlier in a one-launch sweep) is read through L2
+                Bs[e] = c < nc ? (P.tb ? __ldcg(P.B + int64_t(j0 + c) * P.ldb + kb0 + k)
+                                       : __ldcg(P.B + int64_t(kb0 + k) * P.ldb + j0 + c))
                                : T(0);
             }
             __syncthreads();
@@ -187,12 +194,14 @@ __global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *pro
                 for (int k = q0; k < q1; k += 32) {
                     const int kn = min(32, q1 - k);
                     // rows r0 .. r0 + 31, K columns k .. k + kn - 1, read along K
+                    // all 32 loads issued before the first shared-memory store
+                    T av[32];
+#pragma unroll
+                    for (int rr = 0; rr < 32; ++rr)
+                        av[rr] = (r0 + rr < M && lane < kn) ? P.A[int64_t(r0 + rr) * P.lda + kb0 + k + lane] : T(0);
                     __syncwarp();
-#pragma unroll 8
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const int gr = r0 + rr;
-                        tw[rr * 33 + lane] = (gr < M && lane < kn) ? P.A[int64_t(gr) * P.lda + kb0 + k + lane] : T(0);
-                    }
+#pragma unroll
+                    for (int rr = 0; rr < 32; ++rr) tw[rr * 33 + lane] = av[rr];
                     __syncwarp();
                     for (int kk = 0; kk < kn; ++kk) {
                         const T a0 = tw[lane * 33 + kk];
@@ -214,20 +223,28 @@ __global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *pro
                         red[(192 + ii) * 16 + c];
             T *cp = P.C + int64_t(go) * P.ldc + j0 + c;
             if (P.atomic) atomicAdd(cp, P.alpha * v);
-            else *cp = P.beta == T(0) ? P.alpha * v : P.alpha * v + P.beta * *cp;
+            else *cp = P.beta == T(0) ? P.alpha * v : P.alpha * v + P.beta * __ldcg(cp);
         }
     }
 }
 
+template <class T>
+__global__ void __launch_bounds__(256) skinny_gemm_kernel(const GemmProb<T> *probs, int np, int total_tiles,
+                                                          const int32_t *tp) {
+    extern __shared__ __align__(16) unsigned char skinny_smem[];
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x)
+        skinny_tile<T>(probs, np, tile, skinny_smem, tp);
+}
+
 template <class T, int TN>
-inline cudaError_t launch_grouped(Ctx *c, const GemmProb<T> *probs, int np, int tiles) {
+inline cudaError_t launch_grouped(Ctx *c, const GemmProb<T> *probs, int np, int tiles, const int32_t *tp = nullptr) {
     const int grid = tiles < 4 * c->num_sms ? tiles : 4 * c->num_sms;
     if (TN == 16) {
         static SmemLimitOnce once;
         const int bytes = int(SkinnyCfg<T>::smem());
         const cudaError_t e = raise_smem_limit(once, c->device, skinny_gemm_kernel<T>, bytes);
         if (e != cudaSuccess) return e;
-        skinny_gemm_kernel<T><<<grid, 256, bytes, c->stream>>>(probs, np, tiles);
+        skinny_gemm_kernel<T><<<grid, 256, bytes, c->stream>>>(probs, np, tiles, tp);
     } else {
         grouped_gemm_kernel<T, TN><<<grid, 256, 0, c->stream>>>(probs, np, tiles);
     }
@@ -240,6 +257,7 @@ template <class T, int TN>
 struct GemmPlan {
     DBuf<GemmProb<T>> d;
     DBuf<ZeroJob<T>> z;
+    DBuf<int32_t> tp;  // problem of each tile (skinny plans)
     int np = 0, tiles = 0, nz = 0, zmax = 0;
     int run(Ctx *c) const {
         if (nz > 0) {
@@ -247,7 +265,7 @@ struct GemmPlan {
             { zero_jobs_kernel<T><<<g, 256, 0, c->stream>>>(z.get(), nz); ::krr::count_launch(); }
         }
         if (np == 0) return KRR_OK;
-        KRR_CUDA((launch_grouped<T, TN>(c, d.get(), np, tiles)));
+        KRR_CUDA((launch_grouped<T, TN>(c, d.get(), np, tiles, tp.get())));
         return KRR_OK;
     }
 };
@@ -313,6 +331,16 @@ struct GemmBatch {
             if (!plan.d.reset(c, v.size())) return fail(KRR_ERR_OOM, "grouped gemm: out of memory");
             KRR_CUDA(cudaMemcpyAsync(plan.d.get(), v.data(), v.size() * sizeof(GemmProb<T>), cudaMemcpyHostToDevice,
                                      c->stream));
+            if (TN == 16 && tiles > 0) {
+                std::vector<int32_t> tp(size_t(tiles), 0);
+                for (size_t q = 0; q < v.size(); ++q) {
+                    const int nt = int(cdiv(v[q].M, 64)) * v[q].tn;
+                    for (int t = 0; t < nt; ++t) tp[size_t(v[q].tile0 + t)] = int32_t(q);
+                }
+                if (!plan.tp.reset(c, tp.size())) return fail(KRR_ERR_OOM, "grouped gemm: out of memory");
+                KRR_CUDA(cudaMemcpyAsync(plan.tp.get(), tp.data(), tp.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                         c->stream));
+            }
         }
         if (!zj.empty()) {
             if (!plan.z.reset(c, zj.size())) return fail(KRR_ERR_OOM, "grouped gemm: out of memory");

@@ -630,29 +630,36 @@ __global__ void __launch_bounds__(cta::kNT) invert_kernel(const NodeDesc *nd, T 
 // The root's whole block goes to zvec.  The eliminations follow as
 // grouped GEMMs over the level:
 //   xloc -= T^T btil ; zvec = D'_rr^{-1} xloc ; btil -= D'_rs^T zvec
-// and at the root xloc = D^{-1} zvec.
+// and at the root xloc = D^{-1} zvec.  The bodies below take the node and
+// the part (y of ny CTAs) a CTA handles, so the kernels (one CTA per part)
+// and the one-launch sweep share them; vectors another CTA wrote earlier in
+// the sweep are read through L2 (__ldcg), never a stale L1 line.
 template <class T>
-__global__ void __launch_bounds__(cta::kNT) solve_gather_kernel(const NodeDesc *nd, const NodeDesc *all,
-                                                                const T *yperm, int64_t ldy, int nrhs, T *F,
-                                                                const int32_t *I, int is_root) {
-    const NodeDesc &N = nd[blockIdx.x];
+__device__ __forceinline__ void solve_gather_body(const NodeDesc &N, const NodeDesc *all, const T *yperm,
+                                                  int64_t ldy, int nrhs, T *F, const int32_t *I, int is_root, int y,
+                                                  int ny) {
     const int m = N.m, k = is_root ? 0 : N.k;
     const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
     const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
     const int32_t *piv = I + N.piv;
-    // gridDim.y CTAs share a node (the top levels have few, large nodes)
-    for (int64_t e = int64_t(blockIdx.y) * blockDim.x + threadIdx.x; e < int64_t(m) * nrhs;
-         e += int64_t(gridDim.y) * blockDim.x) {
+    for (int64_t e = int64_t(y) * blockDim.x + threadIdx.x; e < int64_t(m) * nrhs; e += int64_t(ny) * blockDim.x) {
         const int a = int(e / nrhs), c = int(e % nrhs);
         const int src = is_root ? a : piv[a];
         T v;
         if (N.is_leaf) v = yperm[(N.leaf_begin + int64_t(src)) * ldy + c];
-        else if (src < A->k) v = F[A->btil + int64_t(src) * nrhs + c];
-        else v = F[B->btil + int64_t(src - A->k) * nrhs + c];
+        else if (src < A->k) v = __ldcg(F + A->btil + int64_t(src) * nrhs + c);
+        else v = __ldcg(F + B->btil + int64_t(src - A->k) * nrhs + c);
         if (is_root) F[N.zvec + e] = v;
         else if (a < k) F[N.btil + int64_t(a) * nrhs + c] = v;
         else F[N.xloc + int64_t(a - k) * nrhs + c] = v;
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(cta::kNT) solve_gather_kernel(const NodeDesc *nd, const NodeDesc *all,
+                                                                const T *yperm, int64_t ldy, int nrhs, T *F,
+                                                                const int32_t *I, int is_root) {
+    solve_gather_body<T>(nd[blockIdx.x], all, yperm, ldy, nrhs, F, I, is_root, blockIdx.y, gridDim.y);
 }
 
 // Down-sweep, last step (one CTA per node): after
@@ -660,15 +667,13 @@ __global__ void __launch_bounds__(cta::kNT) solve_gather_kernel(const NodeDesc *
 // the local x in the node's original row order -> xloc; leaves write
 // their rows of the solution.
 template <class T>
-__global__ void __launch_bounds__(cta::kNT) solve_place_kernel(const NodeDesc *nd, int nrhs, T *F, const int32_t *I,
-                                                               T *xperm, int64_t ldx) {
-    const NodeDesc &N = nd[blockIdx.x];
+__device__ __forceinline__ void solve_place_body(const NodeDesc &N, int nrhs, T *F, const int32_t *I, T *xperm,
+                                                 int64_t ldx, int y, int ny) {
     const int m = N.m, k = N.k;
     const int32_t *piv = I + N.piv;
-    for (int64_t e = int64_t(blockIdx.y) * blockDim.x + threadIdx.x; e < int64_t(m) * nrhs;
-         e += int64_t(gridDim.y) * blockDim.x) {
+    for (int64_t e = int64_t(y) * blockDim.x + threadIdx.x; e < int64_t(m) * nrhs; e += int64_t(ny) * blockDim.x) {
         const int a = int(e / nrhs), c = int(e % nrhs);
-        const T v = a < k ? F[N.btil + int64_t(a) * nrhs + c] : F[N.zvec + int64_t(a - k) * nrhs + c];
+        const T v = a < k ? __ldcg(F + N.btil + int64_t(a) * nrhs + c) : __ldcg(F + N.zvec + int64_t(a - k) * nrhs + c);
         const int dst = piv[a];
         if (N.is_leaf) xperm[(N.leaf_begin + int64_t(dst)) * ldx + c] = v;
         else F[N.xloc + int64_t(dst) * nrhs + c] = v;
@@ -676,24 +681,292 @@ __global__ void __launch_bounds__(cta::kNT) solve_place_kernel(const NodeDesc *n
 }
 
 template <class T>
-__global__ void root_leaf_out_kernel(const NodeDesc *nd, int nrhs, const T *F, T *xperm, int64_t ldx) {
-    const NodeDesc &N = nd[0];
-    for (int64_t e = threadIdx.x; e < int64_t(N.m) * nrhs; e += blockDim.x) {
+__global__ void __launch_bounds__(cta::kNT) solve_place_kernel(const NodeDesc *nd, int nrhs, T *F, const int32_t *I,
+                                                               T *xperm, int64_t ldx) {
+    solve_place_body<T>(nd[blockIdx.x], nrhs, F, I, xperm, ldx, blockIdx.y, gridDim.y);
+}
+
+// Single-leaf tree: the root's solve is the answer.
+template <class T>
+__device__ __forceinline__ void root_leaf_out_body(const NodeDesc &N, int nrhs, const T *F, T *xperm, int64_t ldx,
+                                                   int y, int ny) {
+    for (int64_t e = int64_t(y) * blockDim.x + threadIdx.x; e < int64_t(N.m) * nrhs; e += int64_t(ny) * blockDim.x) {
         const int a = int(e / nrhs), c = int(e % nrhs);
-        xperm[(N.leaf_begin + int64_t(a)) * ldx + c] = F[N.xloc + e];
+        xperm[(N.leaf_begin + int64_t(a)) * ldx + c] = __ldcg(F + N.xloc + e);
     }
+}
+
+template <class T>
+__global__ void root_leaf_out_kernel(const NodeDesc *nd, int nrhs, const T *F, T *xperm, int64_t ldx) {
+    root_leaf_out_body<T>(nd[0], nrhs, F, xperm, ldx, 0, 1);
 }
 
 // Hand the parent's local x to its children (x'_s slots).
 template <class T>
-__global__ void scatter_down_kernel(const NodeDesc *nd, const NodeDesc *all, int nrhs, T *F) {
-    const NodeDesc &N = nd[blockIdx.x];
+__device__ __forceinline__ void scatter_down_body(const NodeDesc &N, const NodeDesc *all, int nrhs, T *F, int y,
+                                                  int ny) {
     if (N.is_leaf) return;
     const NodeDesc &A = all[N.child_a], &B = all[N.child_b];
     const T *x = F + N.xloc;
-    const int64_t e0 = int64_t(blockIdx.y) * blockDim.x + threadIdx.x, step = int64_t(gridDim.y) * blockDim.x;
-    for (int64_t e = e0; e < int64_t(A.k) * nrhs; e += step) F[A.btil + e] = x[e];
-    for (int64_t e = e0; e < int64_t(B.k) * nrhs; e += step) F[B.btil + e] = x[int64_t(A.k) * nrhs + e];
+    const int64_t e0 = int64_t(y) * blockDim.x + threadIdx.x, step = int64_t(ny) * blockDim.x;
+    for (int64_t e = e0; e < int64_t(A.k) * nrhs; e += step) F[A.btil + e] = __ldcg(x + e);
+    for (int64_t e = e0; e < int64_t(B.k) * nrhs; e += step) F[B.btil + e] = __ldcg(x + int64_t(A.k) * nrhs + e);
+}
+
+template <class T>
+__global__ void scatter_down_kernel(const NodeDesc *nd, const NodeDesc *all, int nrhs, T *F) {
+    scatter_down_body<T>(nd[blockIdx.x], all, nrhs, F, blockIdx.y, gridDim.y);
+}
+
+// ------------------------------------- small nodes: one CTA per node step
+// A node with m <= kFuseMax rows takes its whole up-sweep step (gather,
+// x_r -= T^T b_s, z = D'_rr^{-1} x_r, b_s -= D'_rs^T z) or down-sweep step
+// (z -= Y b, b -= T z, placement into the children's or the solution's
+// rows) in one CTA of 256 threads, its vectors (16 columns) in shared
+// memory, instead of one grid-wide phase per product.
+constexpr int kFuseMax = 128;
+constexpr int kFuseRhs = 16;
+
+// out(i, :) += sign sum_j A[j lda + i] v(j, :), i < M, j < K (A stored K x M;
+// v, out in shared memory, 16 columns).  Each warp takes 32 x 32 blocks of
+// A: lane l reads column i0 + l of 32 consecutive rows (each row segment
+// one coalesced 128-byte read, all 32 in flight at once) and sums them into
+// output row i0 + l; parts added with shared-memory atomics.
+template <class T>
+__device__ void cta_gemv_t(const T *A, int64_t lda, int M, int K, const T *v, T *out, T sign) {
+    if (M <= 0 || K <= 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkc = (K + 31) / 32, nitems = ((M + 31) / 32) * nkc;
+    for (int item = warp; item < nitems; item += int(blockDim.x >> 5)) {
+        const int i = (item / nkc) * 32 + lane, j0 = (item % nkc) * 32, jn = min(32, K - j0);
+        T a[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) a[jj] = (i < M && jj < jn) ? A[int64_t(j0 + jj) * lda + i] : T(0);
+        T acc[kFuseRhs];
+#pragma unroll
+        for (int c = 0; c < kFuseRhs; ++c) acc[c] = T(0);
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj)
+            if (jj < jn)  // rows of v past K are not part of it (uniform over the warp)
+#pragma unroll
+                for (int c = 0; c < kFuseRhs; ++c) acc[c] += a[jj] * v[(j0 + jj) * kFuseRhs + c];
+        if (i < M)
+#pragma unroll
+            for (int c = 0; c < kFuseRhs; ++c) atomicAdd(out + i * kFuseRhs + c, sign * acc[c]);
+    }
+}
+
+// out(i, :) += sign sum_j A[i lda + j] v(j, :) (A stored M x K): each warp
+// takes 32-row x 32-column blocks of A, read along rows (coalesced) into
+// its own 32 x 33 tile and read back transposed; parts added with
+// shared-memory atomics.
+template <class T>
+__device__ void cta_gemv_n(const T *A, int64_t lda, int M, int K, const T *v, T *out, T sign, T *tiles) {
+    if (M <= 0 || K <= 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *tw = tiles + warp * 32 * 33;
+    const int nkc = (K + 31) / 32, nitems = ((M + 31) / 32) * nkc;
+    for (int item = warp; item < nitems; item += int(blockDim.x >> 5)) {
+        const int r0 = (item / nkc) * 32, k0 = (item % nkc) * 32, kn = min(32, K - k0);
+        // all 32 loads issued before the first shared-memory store (a store
+        // through the generic pointer would otherwise order each load after
+        // the previous store)
+        T a[32];
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr)
+            a[rr] = (r0 + rr < M && lane < kn) ? A[int64_t(r0 + rr) * lda + k0 + lane] : T(0);
+        __syncwarp();
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) tw[rr * 33 + lane] = a[rr];
+        __syncwarp();
+        T acc[kFuseRhs];
+#pragma unroll
+        for (int c = 0; c < kFuseRhs; ++c) acc[c] = T(0);
+        for (int kk = 0; kk < kn; ++kk) {
+            const T a = tw[lane * 33 + kk];
+#pragma unroll
+            for (int c = 0; c < kFuseRhs; ++c) acc[c] += a * v[(k0 + kk) * kFuseRhs + c];
+        }
+        if (r0 + lane < M)
+#pragma unroll
+            for (int c = 0; c < kFuseRhs; ++c) atomicAdd(out + (r0 + lane) * kFuseRhs + c, sign * acc[c]);
+    }
+}
+
+template <class T>
+constexpr size_t fused_smem() {
+    return sizeof(T) * (size_t(2) * kFuseMax * kFuseRhs + size_t(8) * 32 * 33);
+}
+
+// Up-sweep step of a small node (see solve_gather_body for the steps).
+template <class T>
+__device__ void fused_up_body(const NodeDesc &N, const NodeDesc *all, const T *yperm, int nrhs, T *F,
+                              const int32_t *I, unsigned char *smem) {
+    T *L = reinterpret_cast<T *>(smem);    // m x 16: local rhs in pivot order, skeleton rows first
+    T *Z = L + kFuseMax * kFuseRhs;        // nr x 16
+    T *tiles = Z + kFuseMax * kFuseRhs;    // per-warp 32 x 33
+    const int m = N.m, k = N.k, nr = m - k;
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
+    const int32_t *piv = I + N.piv;
+    __syncthreads();  // shared memory may still be read by the CTA's previous item
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {  // one row per thread, its loads all in flight
+        const int src = piv[a];
+        const T *row = N.is_leaf ? yperm + (N.leaf_begin + int64_t(src)) * nrhs
+                       : src < A->k ? F + A->btil + int64_t(src) * nrhs
+                                    : F + B->btil + int64_t(src - A->k) * nrhs;
+        T v[kFuseRhs];
+#pragma unroll
+        for (int c = 0; c < kFuseRhs; ++c) v[c] = c < nrhs ? __ldcg(row + c) : T(0);
+#pragma unroll
+        for (int c = 0; c < kFuseRhs; ++c) L[a * kFuseRhs + c] = v[c];
+    }
+    for (int e = threadIdx.x; e < nr * kFuseRhs; e += blockDim.x) Z[e] = T(0);
+    __syncthreads();
+    cta_gemv_t<T>(F + N.tmat, nr, nr, k, L, L + k * kFuseRhs, T(-1));  // x_r -= T^T b_s
+    __syncthreads();
+    cta_gemv_n<T>(F + N.drr, nr, nr, nr, L + k * kFuseRhs, Z, T(1), tiles);  // z = D'_rr^{-1} x_r
+    __syncthreads();
+    cta_gemv_t<T>(F + N.drs, k, k, nr, Z, L, T(-1));  // b_s -= D'_rs^T z
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) F[N.btil + e] = L[(e / nrhs) * kFuseRhs + e % nrhs];
+    for (int e = threadIdx.x; e < nr * nrhs; e += blockDim.x) F[N.zvec + e] = Z[(e / nrhs) * kFuseRhs + e % nrhs];
+    __syncthreads();
+}
+
+// Down-sweep step of a small node (its b set by its parent): z -= Y b,
+// b -= T z, then the local x in original row order goes to the children's
+// b slots (parent) or to the solution's rows (leaf).
+template <class T>
+__device__ void fused_down_body(const NodeDesc &N, const NodeDesc *all, int nrhs, T *F, const int32_t *I,
+                                T *xperm, unsigned char *smem) {
+    T *L = reinterpret_cast<T *>(smem);    // k x 16
+    T *Z = L + kFuseMax * kFuseRhs;        // nr x 16
+    T *tiles = Z + kFuseMax * kFuseRhs;
+    const int m = N.m, k = N.k, nr = m - k;
+    __syncthreads();
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {  // b rows then z rows, one per thread
+        const T *row = a < k ? F + N.btil + int64_t(a) * nrhs : F + N.zvec + int64_t(a - k) * nrhs;
+        T *dst = a < k ? L + a * kFuseRhs : Z + (a - k) * kFuseRhs;
+        T v[kFuseRhs];
+#pragma unroll
+        for (int c = 0; c < kFuseRhs; ++c) v[c] = c < nrhs ? __ldcg(row + c) : T(0);
+#pragma unroll
+        for (int c = 0; c < kFuseRhs; ++c) dst[c] = v[c];
+    }
+    __syncthreads();
+    cta_gemv_n<T>(F + N.ymat, k, nr, k, L, Z, T(-1), tiles);  // z -= Y b
+    __syncthreads();
+    cta_gemv_n<T>(F + N.tmat, nr, k, nr, Z, L, T(-1), tiles);  // b -= T z
+    __syncthreads();
+    const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
+    const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
+    const int32_t *piv = I + N.piv;
+    for (int e = threadIdx.x; e < m * nrhs; e += blockDim.x) {
+        const int a = e / nrhs, c = e % nrhs;
+        const T v = a < k ? L[a * kFuseRhs + c] : Z[(a - k) * kFuseRhs + c];
+        const int dst = piv[a];
+        if (N.is_leaf) xperm[(N.leaf_begin + int64_t(dst)) * nrhs + c] = v;
+        else if (dst < A->k) F[A->btil + int64_t(dst) * nrhs + c] = v;
+        else F[B->btil + int64_t(dst - A->k) * nrhs + c] = v;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------- ULV solve in one launch
+// The whole sweep (up the tree, the root, down the tree) as one persistent
+// cooperative launch: a list of phases (a level's gathers, one of its
+// grouped skinny products, its placements, its hand-downs), each spread
+// over every CTA, separated by a grid-wide barrier.  The launch replaces
+// about a hundred dependent kernel launches per solve.
+enum UlvKind { kUlvGather = 0, kUlvGemm = 1, kUlvPlace = 2, kUlvScatter = 3, kUlvRootLeaf = 4 };
+
+template <class T>
+struct UlvPhase {
+    const NodeDesc *fl;        // small nodes whose whole step runs first in this phase (fdir 1 up, 2 down)
+    int nf, fdir;
+    int kind, is_root;
+    int nn, per_node;          // node phases: nn nodes x per_node parts
+    const NodeDesc *dl;
+    const GemmProb<T> *probs;  // product phases
+    const int32_t *tp;
+    int np, tiles;
+    const ZeroJob<T> *z;       // gather phases: regions cleared for the level's split products
+    int nz, zparts;
+    int items;                 // work items of the phase
+};
+
+// Grid-wide barrier over the CTAs of a cooperative launch (all resident):
+// the last CTA to arrive resets the count and advances the generation.
+// The wait is bounded: past `budget` SM cycles the status latches
+// KRR_ERR_TIMEOUT and the CTA leaves the sweep.
+struct GridBar {
+    unsigned count, gen;
+};
+
+__device__ bool grid_barrier(GridBar *b, unsigned nblocks, long long budget, DevStatus *st) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &b->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&b->count, 1u) + 1u == nblocks) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > budget) {
+                    dev_fail(st, KRR_ERR_TIMEOUT, 301);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) ulv_sweep_kernel(const UlvPhase<T> *phases, int nph, const NodeDesc *all,
+                                                        const T *yperm, T *xperm, int nrhs, T *F, const int32_t *I,
+                                                        GridBar *bar, long long budget, DevStatus *st) {
+    extern __shared__ __align__(16) unsigned char ulv_smem[];
+    for (int p = 0; p < nph; ++p) {
+        const UlvPhase<T> &P = phases[p];
+        const int nodes = P.nn * P.per_node;
+        for (int i2 = blockIdx.x; i2 < P.items; i2 += gridDim.x) {
+            if (i2 < P.nf) {
+                if (P.fdir == 1) fused_up_body<T>(P.fl[i2], all, yperm, nrhs, F, I, ulv_smem);
+                else fused_down_body<T>(P.fl[i2], all, nrhs, F, I, xperm, ulv_smem);
+                continue;
+            }
+            const int it = i2 - P.nf;
+            if (P.kind == kUlvGemm) {
+                skinny_tile<T>(P.probs, P.np, it, ulv_smem, P.tp);
+            } else if (it < nodes) {
+                const NodeDesc &N = P.dl[it / P.per_node];
+                const int y = it % P.per_node;
+                if (P.kind == kUlvGather) solve_gather_body<T>(N, all, yperm, nrhs, nrhs, F, I, P.is_root, y, P.per_node);
+                else if (P.kind == kUlvPlace) solve_place_body<T>(N, nrhs, F, I, xperm, nrhs, y, P.per_node);
+                else if (P.kind == kUlvScatter) scatter_down_body<T>(N, all, nrhs, F, y, P.per_node);
+                else root_leaf_out_body<T>(N, nrhs, F, xperm, nrhs, y, P.per_node);
+            } else {  // clearing of a split product's output (gather phases)
+                const int q = it - nodes;
+                const ZeroJob<T> z = P.z[q / P.zparts];
+                for (int64_t e = int64_t(q % P.zparts) * blockDim.x + threadIdx.x; e < int64_t(z.M) * z.N;
+                     e += int64_t(P.zparts) * blockDim.x)
+                    z.C[(e / z.N) * z.ldc + e % z.N] = T(0);
+            }
+        }
+        if (p + 1 < nph && !grid_barrier(bar, gridDim.x, budget, st)) return;
+    }
 }
 
 __global__ void leaf_id_kernel(int64_t n, const int32_t *begin, const int32_t *end, const int32_t *isleaf, int nn,
@@ -848,9 +1121,23 @@ struct HssImpl {
         DBuf<NodeDesc> dl;
         GemmPlan<float, 16> f2, f3, f4, f1, fd1, fd2;
         GemmPlan<double, 16> e2, e3, e4, e1, ed1, ed2;
+        // the one-launch sweep: small nodes (one CTA per node step) and the
+        // rest, whose products (sf / se: up-sweep 0-3 and down-sweep 4-5 as
+        // above) and clearing jobs (ZeroJob<T>) run as grid-wide phases
+        DBuf<NodeDesc> dl_small, dl_big;
+        int n_small = 0, n_big = 0;
+        GemmPlan<float, 16> sf[6];
+        GemmPlan<double, 16> se[6];
+        DBuf<unsigned char> zall;
+        int nzall = 0, zmax_all = 0;
     };
     std::vector<LevelPlan> plan;
     int plan_nrhs = -1;
+    // the one-launch ULV sweep: its phase list (UlvPhase<T>), barrier,
+    // grid (CTAs resident at once; 0 = use the captured graph instead)
+    DBuf<unsigned char> ulv_ph;
+    int ulv_nph = 0, ulv_grid = -1;
+    DBuf<unsigned> ulv_bar;
     DBuf<float> ws_bf, ws_xf, ws_rs, ws_sm;
     DBuf<__half> ws_rt;
     int ws_nrhs = -1;
@@ -1492,6 +1779,13 @@ int factor(HssImpl *H) {
 }
 
 template <class T>
+GemmPlan<T, 16> &pick_s(HssImpl::LevelPlan &P, int which);
+template <>
+GemmPlan<float, 16> &pick_s<float>(HssImpl::LevelPlan &P, int which) { return P.sf[which]; }
+template <>
+GemmPlan<double, 16> &pick_s<double>(HssImpl::LevelPlan &P, int which) { return P.se[which]; }
+
+template <class T>
 GemmPlan<T, 16> &pick(HssImpl::LevelPlan &P, int which);
 template <>
 GemmPlan<float, 16> &pick<float>(HssImpl::LevelPlan &P, int which) {
@@ -1506,6 +1800,96 @@ GemmPlan<double, 16> &pick<double>(HssImpl::LevelPlan &P, int which) {
 
 // Per-level descriptors and GEMM problem lists of the ULV sweeps for nrhs
 // right-hand sides, uploaded once per factorization.
+// The phase list of the one-launch ULV sweep (the same steps, in the same
+// order, as ulv_solve below), for a grid of H->ulv_grid CTAs.
+template <class T>
+int build_sweep(HssImpl *H) {
+    static_assert(fused_smem<T>() <= SkinnyCfg<T>::smem(), "the sweep's shared memory holds a small-node step");
+    Ctx *c = H->c;
+    if (H->ulv_grid < 0) {
+        H->ulv_grid = 0;
+        int coop = 0, nb = 0;
+        KRR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+        const int smem = int(SkinnyCfg<T>::smem());
+        static SmemLimitOnce smem_limit;
+        KRR_CUDA(raise_smem_limit(smem_limit, c->device, ulv_sweep_kernel<T>, smem));
+        KRR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ulv_sweep_kernel<T>, 256, smem));
+        if (coop && nb > 0) H->ulv_grid = nb * c->num_sms;
+        if (H->ulv_grid > 0 && !H->ulv_bar.reset(c, 2)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+    }
+    if (H->ulv_grid == 0) return KRR_OK;
+    const int G = H->ulv_grid;
+    std::vector<UlvPhase<T>> ph;
+    // a phase over the level's large nodes (nn x per_node items), with the
+    // level's small nodes' whole steps first when fdir != 0
+    auto node_phase = [&](int kind, int h, int fdir) {
+        HssImpl::LevelPlan &P = H->plan[h];
+        UlvPhase<T> q{};
+        q.kind = kind;
+        q.is_root = h == H->H ? 1 : 0;
+        q.nn = P.n_big;
+        q.per_node = P.n_big ? std::max(1, std::min(32, G / P.n_big)) : 1;
+        q.dl = P.dl_big.get();
+        if (fdir) {
+            q.fl = P.dl_small.get();
+            q.nf = P.n_small;
+            q.fdir = fdir;
+        }
+        q.items = q.nf + q.nn * q.per_node;
+        return q;
+    };
+    auto gemm_phase = [&](const GemmPlan<T, 16> &gp, UlvPhase<T> q) {
+        q.kind = kUlvGemm;
+        q.probs = gp.d.get();
+        q.tp = gp.tp.get();
+        q.np = gp.np;
+        q.tiles = gp.np ? gp.tiles : 0;
+        q.items = q.nf + q.tiles;
+        if (q.items > 0) ph.push_back(q);
+    };
+    const UlvPhase<T> none{};
+    for (int h = 0; h <= H->H; ++h) {
+        if (H->by_height[h].empty()) continue;
+        HssImpl::LevelPlan &P = H->plan[h];
+        UlvPhase<T> g = node_phase(kUlvGather, h, 1);
+        if (P.nzall > 0) {
+            g.z = reinterpret_cast<const ZeroJob<T> *>(P.zall.get());
+            g.nz = P.nzall;
+            g.zparts = int(std::min<int64_t>(64, std::max<int64_t>(1, cdiv(P.zmax_all, 256))));
+            g.items += g.nz * g.zparts;
+        }
+        if (g.items > 0) ph.push_back(g);
+        if (h == H->H) {
+            gemm_phase(pick_s<T>(P, 0), none);
+            break;
+        }
+        for (int q = 1; q <= 3; ++q) gemm_phase(pick_s<T>(P, q), none);
+    }
+    for (int h = H->H; h >= 0; --h) {
+        if (H->by_height[h].empty()) continue;
+        HssImpl::LevelPlan &P = H->plan[h];
+        if (h < H->H) {
+            UlvPhase<T> f = node_phase(kUlvGemm, h, 2);  // small nodes' down steps with the first product
+            f.nn = 0;
+            gemm_phase(pick_s<T>(P, 4), f);
+            gemm_phase(pick_s<T>(P, 5), none);
+            if (P.n_big) {
+                ph.push_back(node_phase(kUlvPlace, h, 0));
+                if (h > 0) ph.push_back(node_phase(kUlvScatter, h, 0));  // height 0 holds leaves only
+            }
+        } else {
+            if (H->desc[H->root].is_leaf) ph.push_back(node_phase(kUlvRootLeaf, h, 0));
+            else ph.push_back(node_phase(kUlvScatter, h, 0));
+        }
+    }
+    H->ulv_nph = int(ph.size());
+    if (!H->ulv_ph.reset(c, ph.size() * sizeof(UlvPhase<T>))) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+    KRR_CUDA(cudaMemcpyAsync(H->ulv_ph.get(), ph.data(), ph.size() * sizeof(UlvPhase<T>), cudaMemcpyHostToDevice,
+                             c->stream));
+    KRR_CUDA(cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
 template <class T>
 int build_solve_plan(HssImpl *H, int nrhs) {
     Ctx *c = H->c;
@@ -1522,29 +1906,57 @@ int build_solve_plan(HssImpl *H, int nrhs) {
         for (int a = 0; a < nn; ++a) ld[a] = H->desc[lv[a]];
         if (!P.dl.reset(c, nn)) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
         KRR_CUDA(cudaMemcpyAsync(P.dl.get(), ld.data(), nn * sizeof(NodeDesc), cudaMemcpyHostToDevice, c->stream));
-        GemmBatch<T, 16> g1, g2, g3, g4, d1, d2;
-        g1.split_ok = g2.split_ok = g3.split_ok = g4.split_ok = d1.split_ok = d2.split_ok = true;
-        if (h == H->H) {
-            for (const NodeDesc &N : ld)
-                g1.add(N.m, nrhs, N.m, T(1), F + N.drr, N.m, false, F + N.zvec, nrhs, false, T(0), F + N.xloc, nrhs);
-        } else {
-            for (const NodeDesc &N : ld) {
+        GemmBatch<T, 16> g[6], sw[6];  // every node (graph path); the sweep's large nodes
+        for (int q = 0; q < 6; ++q) g[q].split_ok = sw[q].split_ok = true;
+        std::vector<NodeDesc> small, big;
+        for (const NodeDesc &N : ld) {
+            const bool fuse = h < H->H && nrhs <= kFuseRhs && N.m <= kFuseMax;
+            (fuse ? small : big).push_back(N);
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1 && fuse) break;
+                GemmBatch<T, 16> *b = pass == 0 ? g : sw;
+                if (h == H->H) {
+                    b[0].add(N.m, nrhs, N.m, T(1), F + N.drr, N.m, false, F + N.zvec, nrhs, false, T(0), F + N.xloc,
+                             nrhs);
+                    continue;
+                }
                 const int k = N.k, nr = N.m - N.k;
-                g2.add(nr, nrhs, k, T(-1), F + N.tmat, nr, true, F + N.btil, nrhs, false, T(1), F + N.xloc, nrhs);
-                g3.add(nr, nrhs, nr, T(1), F + N.drr, nr, false, F + N.xloc, nrhs, false, T(0), F + N.zvec, nrhs);
-                g4.add(k, nrhs, nr, T(-1), F + N.drs, k, true, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
-                d1.add(nr, nrhs, k, T(-1), F + N.ymat, k, false, F + N.btil, nrhs, false, T(1), F + N.zvec, nrhs);
-                d2.add(k, nrhs, nr, T(-1), F + N.tmat, nr, false, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
+                b[1].add(nr, nrhs, k, T(-1), F + N.tmat, nr, true, F + N.btil, nrhs, false, T(1), F + N.xloc, nrhs);
+                b[2].add(nr, nrhs, nr, T(1), F + N.drr, nr, false, F + N.xloc, nrhs, false, T(0), F + N.zvec, nrhs);
+                b[3].add(k, nrhs, nr, T(-1), F + N.drs, k, true, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
+                b[4].add(nr, nrhs, k, T(-1), F + N.ymat, k, false, F + N.btil, nrhs, false, T(1), F + N.zvec, nrhs);
+                b[5].add(k, nrhs, nr, T(-1), F + N.tmat, nr, false, F + N.zvec, nrhs, false, T(1), F + N.btil, nrhs);
             }
         }
-        KRR_TRY(g1.freeze(c, pick<T>(P, 0)));
-        KRR_TRY(g2.freeze(c, pick<T>(P, 1)));
-        KRR_TRY(g3.freeze(c, pick<T>(P, 2)));
-        KRR_TRY(g4.freeze(c, pick<T>(P, 3)));
-        KRR_TRY(d1.freeze(c, pick<T>(P, 4)));
-        KRR_TRY(d2.freeze(c, pick<T>(P, 5)));
+        P.n_small = int(small.size());
+        P.n_big = int(big.size());
+        if ((P.n_small && !P.dl_small.reset(c, small.size())) || (P.n_big && !P.dl_big.reset(c, big.size())))
+            return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+        if (P.n_small)
+            KRR_CUDA(cudaMemcpyAsync(P.dl_small.get(), small.data(), small.size() * sizeof(NodeDesc),
+                                     cudaMemcpyHostToDevice, c->stream));
+        if (P.n_big)
+            KRR_CUDA(cudaMemcpyAsync(P.dl_big.get(), big.data(), big.size() * sizeof(NodeDesc), cudaMemcpyHostToDevice,
+                                     c->stream));
+        {
+            std::vector<ZeroJob<T>> zs;
+            for (int q = 0; q < 4; ++q) zs.insert(zs.end(), sw[q].zj.begin(), sw[q].zj.end());
+            P.nzall = int(zs.size());
+            P.zmax_all = 0;
+            for (const ZeroJob<T> &z : zs) P.zmax_all = std::max(P.zmax_all, z.M * z.N);
+            if (!zs.empty()) {
+                if (!P.zall.reset(c, zs.size() * sizeof(ZeroJob<T>))) return fail(KRR_ERR_OOM, "hss_solve: out of memory");
+                KRR_CUDA(cudaMemcpyAsync(P.zall.get(), zs.data(), zs.size() * sizeof(ZeroJob<T>),
+                                         cudaMemcpyHostToDevice, c->stream));
+            }
+        }
+        for (int q = 0; q < 6; ++q) {
+            KRR_TRY(g[q].freeze(c, pick<T>(P, q)));
+            KRR_TRY(sw[q].freeze(c, pick_s<T>(P, q)));
+        }
     }
     H->plan_nrhs = nrhs;
+    KRR_TRY(build_sweep<T>(H));
     return KRR_OK;
 }
 
@@ -1599,6 +2011,23 @@ template <class T>
 int ulv_solve_graph(HssImpl *H, const T *y, T *x, int nrhs) {
     Ctx *c = H->c;
     if (H->plan_nrhs != nrhs) KRR_TRY(build_solve_plan<T>(H, nrhs));
+    if (H->ulv_grid > 0) {  // the whole sweep in one cooperative launch
+        KRR_CUDA(cudaMemsetAsync(H->ulv_bar.get(), 0, sizeof(GridBar), c->stream));
+        const UlvPhase<T> *phases = reinterpret_cast<const UlvPhase<T> *>(H->ulv_ph.get());
+        int nph = H->ulv_nph;
+        const NodeDesc *all = H->ddesc.get();
+        T *F = farena<T>(H);
+        const int32_t *I = H->IA.get();
+        GridBar *bar = reinterpret_cast<GridBar *>(H->ulv_bar.get());
+        long long budget = c->wait_cycles;
+        DevStatus *st = c->status;
+        void *args[] = {(void *)&phases, (void *)&nph, (void *)&all, (void *)&y, (void *)&x, (void *)&nrhs,
+                        (void *)&F, (void *)&I, (void *)&bar, (void *)&budget, (void *)&st};
+        KRR_CUDA(cudaLaunchCooperativeKernel((const void *)ulv_sweep_kernel<T>, dim3(unsigned(H->ulv_grid)), dim3(256),
+                                             args, SkinnyCfg<T>::smem(), c->stream));
+        count_launch();
+        return KRR_OK;
+    }
     if (!H->ulv_exec || H->g_y != y || H->g_x != x || H->g_nrhs != nrhs) {
         H->drop_graph();
         if (!H->cap_stream) KRR_CUDA(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
