@@ -95,6 +95,23 @@ long long krr_launch_count(void);
  * warm-up.  Synchronizes. */
 int krr_probe_rate(krr_ctx *ctx, int32_t which, double *ops_per_second);
 
+/* Batched FP32 products C_b = alpha op(A_b) op(B_b) + beta C_b, b < batch,
+ * through the library's grouped product (the interpolative decompositions'
+ * and the factorization's node products use the same code).  A_b = A + b sA
+ * is M x K (ta = 0: row-major, element (i, k) at A_b[i lda + k]) or stored
+ * K x M (ta = 1: element (i, k) at A_b[k lda + i]); B_b = B + b sB is K x N
+ * (tb = 0: B_b[k ldb + j]) or stored N x K (tb = 1: B_b[j ldb + k]);
+ * C_b = C + b sC is M x N row-major (C_b[i ldc + j]).  All device float
+ * pointers; C must not overlap A or B.  path: 0 = the library's choice,
+ * 1 = tensor cores (tcgen05 kind::tf32, each operand split into two TF32
+ * parts, three products: about FP32 accuracy), 2 = CUDA cores (FP32 FMA).
+ * Asynchronous on the context's stream. */
+int krr_gemm_f32_batched(krr_ctx *ctx, int32_t batch, int32_t M, int32_t N,
+                         int32_t K, float alpha, const float *A, int64_t lda,
+                         int64_t sA, int32_t ta, const float *B, int64_t ldb,
+                         int64_t sB, int32_t tb, float beta, float *C,
+                         int64_t ldc, int64_t sC, int32_t path);
+
 /* Wait for the context's stream and return (and clear) any latched device
  * error.  Synchronizes. */
 int krr_sync(krr_ctx *ctx);

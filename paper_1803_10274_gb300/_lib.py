@@ -60,6 +60,8 @@ SIGNATURES = {
     "krr_set_wait_limit": (i32, [P, i64]),
     "krr_set_autotune": (i32, [P, i32]),
     "krr_probe_rate": (i32, [P, i32, ctypes.POINTER(f64)]),
+    "krr_gemm_f32_batched": (i32, [P, i32, i32, i32, i32, ctypes.c_float, P, i64, i64, i32, P, i64, i64, i32,
+                                   ctypes.c_float, P, i64, i64, i32]),
     "krr_standardize": (i32, [P, P, i64, i32, P, i64, P, P]),
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),
     "krr_order": (i32, [P, P, i64, i32, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),

@@ -17,7 +17,7 @@ from ._lib import (KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_MIXED_F64, KRR_ORDER
 
 __all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_MIXED_F64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "KRR_ORDER_TWO_MEANS",
            "KRR_ORDER_NATURAL", "KRR_ORDER_KD", "KRR_ORDER_PCA", "krr_order", "krr_standardize", "krr_cluster", "krr_sample",
-           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "krr_one_vs_all", "HSS", "hss_compress", "default_options",
+           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "krr_one_vs_all", "krr_gemm_f32_batched", "HSS", "hss_compress", "default_options",
            "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]
 
 
@@ -246,6 +246,30 @@ def krr_random_block(ctx, n, r, col0, seed, precision=KRR_MIXED, device=None):
     out = torch.empty(n, r, dtype=dt, device=device or torch.device("cuda", ctx.device))
     check(lib().krr_random_block(ctx.h, n, r, col0, seed, precision, _ptr(out), out.stride(0)))
     return out
+
+
+def krr_gemm_f32_batched(ctx, A, B, C=None, alpha=1.0, beta=0.0, ta=False, tb=False, path=0):
+    """C[b] = alpha op(A[b]) op(B[b]) + beta C[b] for 3-D contiguous float32
+    CUDA tensors: A (batch, M, K), or (batch, K, M) with ta; B (batch, K, N),
+    or (batch, N, K) with tb; C (batch, M, N), allocated when None.  path: 0
+    library's choice, 1 tensor cores (three TF32 products), 2 CUDA cores."""
+    _need(A, torch.float32, "A", dims=3)
+    _need(B, torch.float32, "B", dims=3)
+    A, B = A.contiguous(), B.contiguous()
+    batch = A.shape[0]
+    M, K = (A.shape[2], A.shape[1]) if ta else (A.shape[1], A.shape[2])
+    N = B.shape[1] if tb else B.shape[2]
+    if (B.shape[2] if tb else B.shape[1]) != K or B.shape[0] != batch:
+        raise ValueError("krr_gemm_f32_batched: A and B do not conform")
+    if C is None:
+        C = torch.zeros(batch, M, N, dtype=torch.float32, device=A.device)
+    _need(C, torch.float32, "C", dims=3)
+    if tuple(C.shape) != (batch, M, N) or not C.is_contiguous():
+        raise ValueError("krr_gemm_f32_batched: C must be a contiguous (batch, M, N) tensor")
+    check(lib().krr_gemm_f32_batched(ctx.h, batch, M, N, K, float(alpha), _ptr(A), A.shape[2], A.stride(0),
+                                     int(bool(ta)), _ptr(B), B.shape[2], B.stride(0), int(bool(tb)), float(beta),
+                                     _ptr(C), N, C.stride(0), int(path)))
+    return C
 
 
 def krr_one_vs_all(ctx, cls, c):

@@ -3,6 +3,7 @@
 // output tiles of all problems form one list that persistent CTAs walk, so
 // a level with two large nodes still spreads over every SM.
 #pragma once
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -270,6 +271,12 @@ struct GemmPlan {
     }
 };
 
+// Large FP32 batches on the tensor cores (tcgen05 kind::tf32 with a
+// three-term split, FP32 accuracy; gemm_tc.cu): whether a batch qualifies,
+// and its launch.
+bool tc_gemm_wanted(const Ctx *c, const std::vector<GemmProb<float>> &v);
+int launch_grouped_tc(Ctx *c, const std::vector<GemmProb<float>> &v);
+
 template <class T, int TN = 64>
 struct GemmBatch {
     std::vector<GemmProb<T>> v;
@@ -282,6 +289,7 @@ struct GemmBatch {
     // plans, which run the clearing before the GEMMs).
     static constexpr int kSlice = 64;
     bool split_ok = false;
+    bool force_cuda_cores = false;  // never the tensor-core path (comparisons)
     void add(int M, int N, int K, T alpha, const T *A, int64_t lda, bool ta, const T *B, int64_t ldb, bool tb, T beta,
              T *C, int64_t ldc) {
         if (M <= 0 || N <= 0) return;
@@ -366,6 +374,14 @@ struct GemmBatch {
             zj.clear();
         }
         if (v.empty()) return KRR_OK;
+        if constexpr (std::is_same<T, float>::value && TN == 64) {
+            if (!force_cuda_cores && tc_gemm_wanted(c, v)) {
+                KRR_TRY(launch_grouped_tc(c, v));
+                v.clear();
+                tiles = 0;
+                return KRR_OK;
+            }
+        }
         DBuf<GemmProb<T>> d(c, v.size());
         if (!d.get()) return fail(KRR_ERR_OOM, "grouped gemm: out of memory");
         KRR_CUDA(cudaMemcpyAsync(d.get(), v.data(), v.size() * sizeof(GemmProb<T>), cudaMemcpyHostToDevice, c->stream));
