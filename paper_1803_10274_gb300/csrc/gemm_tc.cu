@@ -368,6 +368,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(Params P) {
 // The tensor-core path pays off for batches with enough work in full
 // tiles: at least 1 GFLOP, the problems' tiles on average at least a
 // quarter full, and K at least 256 on average (weighted by output size).
+#ifndef KRR_TC_MIN_K
+#define KRR_TC_MIN_K 256
+#endif
+#ifndef KRR_TC_MIN_FLOPS
+#define KRR_TC_MIN_FLOPS 1e9
+#endif
+constexpr int kTcMinK = KRR_TC_MIN_K;           // average K (weighted by output size) at least
+constexpr double kTcMinFlops = KRR_TC_MIN_FLOPS;  // batch work at least
+
 bool tc_gemm_wanted(const Ctx *c, const std::vector<GemmProb<float>> &v) {
     if (v.empty()) return false;
     double flops = 0, tile_area = 0, area = 0;
@@ -380,7 +389,7 @@ bool tc_gemm_wanted(const Ctx *c, const std::vector<GemmProb<float>> &v) {
     for (const GemmProb<float> &p : v) mnk += double(p.M) * p.N * double(p.K);
     // short K (panel updates, R-hat, S_loc corrections) stays on the CUDA
     // cores, whose epilogue costs less per output
-    return flops >= 1e9 && area >= 0.25 * tile_area && mnk >= 256.0 * area;
+    return flops >= kTcMinFlops && area >= 0.25 * tile_area && mnk >= double(kTcMinK) * area;
 }
 
 int launch_grouped_tc(Ctx *c, const std::vector<GemmProb<float>> &v) {

@@ -1025,28 +1025,49 @@ __global__ void combine_kernel(const TS *S, int64_t lds, int split, const double
 }
 
 // dots[i][c] += sum_rows A_i(row, c) * B(row, c) for blocks A_i = A + i * bstride
-__global__ void multidot_kernel(const double *A, int64_t bstride, int nb, const double *B, int64_t n, int nr,
-                                double *dots) {
-    extern __shared__ double sh[];
-    const int i = blockIdx.y;
-    for (int c = threadIdx.x; c < nr; c += blockDim.x) sh[c] = 0.0;
-    __syncthreads();
+// dots[i][c] += sum_row A_i(row, c) B(row, c) for the nb blocks A_i = A +
+// i bstride (n x nr, row-major), blockIdx.y = i, blockIdx.z = a group of 16
+// columns: each thread sums its rows in registers, the CTA reduces by warp
+// shuffles, and one atomic add per column per CTA goes to memory.
+__global__ void __launch_bounds__(256) multidot_kernel(const double *A, int64_t bstride, int nb, const double *B,
+                                                       int64_t n, int nr, double *dots) {
+    __shared__ double part[8][16];
+    const int i = blockIdx.y, c0 = 16 * blockIdx.z;
+    const int nc = min(16, nr - c0);
     const double *Ai = A + int64_t(i) * bstride;
-    const int64_t tot = n * nr;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < tot; e += int64_t(gridDim.x) * blockDim.x)
-        atomicAdd(&sh[e % nr], Ai[e] * B[e]);
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < n; row += int64_t(gridDim.x) * blockDim.x) {
+        const double *a = Ai + row * nr + c0;
+        const double *b = B + row * nr + c0;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < nc) acc[c] += a[c] * b[c];
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp][c] = v;
+    }
     __syncthreads();
-    for (int c = threadIdx.x; c < nr; c += blockDim.x) atomicAdd(&dots[i * nr + c], sh[c]);
+    if (threadIdx.x < nc) {
+        double v = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) v += part[w][threadIdx.x];
+        atomicAdd(&dots[i * nr + c0 + threadIdx.x], v);
+    }
 }
 
-// W(row, c) += sum_i coef[i][c] * A_i(row, c)   (coef already carries signs)
-__global__ void combo_kernel(double *W, const double *A, int64_t bstride, int nb, const double *coef, int64_t n,
-                             int nr) {
+// W(row, c) += sign sum_i coef[i][c] * A_i(row, c)
+__global__ void combo_kernel(double *W, const double *A, int64_t bstride, int nb, const double *coef, double sign,
+                             int64_t n, int nr) {
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= n * nr) return;
     const int c = int(e % nr);
     double s = W[e];
-    for (int i = 0; i < nb; ++i) s += coef[i * nr + c] * A[int64_t(i) * bstride + e];
+    for (int i = 0; i < nb; ++i) s += (sign * coef[i * nr + c]) * A[int64_t(i) * bstride + e];
     W[e] = s;
 }
 
@@ -1054,6 +1075,15 @@ __global__ void combo_kernel(double *W, const double *A, int64_t bstride, int nb
 __global__ void colscale_kernel(double *A, const double *B, const double *scale, int64_t n, int nr) {
     const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e < n * nr) A[e] = B[e] * scale[e % nr];
+}
+
+// A(row, c) = B(row, c) / |B(:, c)| from the squared norms (0 for a zero
+// column): the next Krylov vector, normalized on the device.
+__global__ void colnorm_kernel(double *A, const double *B, const double *normsq, int64_t n, int nr) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * nr) return;
+    const double h = sqrt(fmax(normsq[e % nr], 0.0));
+    A[e] = B[e] * (h > 0 ? 1.0 / h : 0.0);
 }
 
 template <class Tin, class Tout>
@@ -2276,23 +2306,28 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
         // the true residual with the precise (split-K) fused product.
         const int mres = 30;
         const int64_t nn = n * nrhs;
-        DBuf<double> V(c, size_t(mres + 1) * nn), Wv(c, nn), Zv(c, nn), dots(c, size_t(mres + 1) * nrhs),
+        // dots: the two Gram-Schmidt passes' coefficients (mres + 1 rows of
+        // nrhs each) and the new vector's squared norms, read back together
+        DBuf<double> V(c, size_t(mres + 1) * nn), Wv(c, nn), Zv(c, nn), dots(c, size_t(2 * (mres + 1) + 1) * nrhs),
             coef(c, size_t(mres + 1) * nrhs), sc(c, nrhs), ynorm(c, 2 * nrhs);
         if (!V.get() || !Wv.get() || !Zv.get() || !dots.get() || !coef.get() || !sc.get() || !ynorm.get())
             return fail(KRR_ERR_OOM, "hss_solve: out of memory");
         KRR_CUDA(cudaMemsetAsync(ap, 0, nn * sizeof(double), c->stream));
         const unsigned g1 = unsigned(cdiv(nn, 256));
-        const unsigned gd = unsigned(std::min<int64_t>(256, cdiv(nn, 256)));
-        auto mdot = [&](const double *A, int nb, const double *B) -> int {
-            KRR_CUDA(cudaMemsetAsync(dots.get(), 0, size_t(nb) * nrhs * sizeof(double), c->stream));
-            { multidot_kernel<<<dim3(gd, nb), 256, nrhs * sizeof(double), c->stream>>>(A, nn, nb, B, n, nrhs, dots.get()); ::krr::count_launch(); }
+        const unsigned gd = unsigned(std::min<int64_t>(2 * c->num_sms, cdiv(n, 256)));
+        const unsigned gz = unsigned(cdiv(nrhs, 16));
+        // out[i][c] = <A_i(:, c), B(:, c)> (out zeroed here)
+        auto mdot = [&](const double *A, int nb, const double *B, double *out) -> int {
+            KRR_CUDA(cudaMemsetAsync(out, 0, size_t(nb) * nrhs * sizeof(double), c->stream));
+            { multidot_kernel<<<dim3(gd, nb, gz), 256, 0, c->stream>>>(A, nn, nb, B, n, nrhs, out); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
             return KRR_OK;
         };
-        std::vector<double> ynrm(nrhs), hd((mres + 1) * nrhs), hd2((mres + 1) * nrhs);
+        double *d1 = dots.get(), *d2 = dots.get() + size_t(mres + 1) * nrhs, *dw = dots.get() + size_t(2 * (mres + 1)) * nrhs;
+        std::vector<double> ynrm(nrhs), hd((mres + 1) * nrhs), hdots(size_t(2 * (mres + 1) + 1) * nrhs);
         Tracer tr(c);
-        KRR_TRY(mdot(yp, 1, yp));
-        KRR_CUDA(cudaMemcpyAsync(ynrm.data(), dots.get(), nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
+        KRR_TRY(mdot(yp, 1, yp, d1));
+        KRR_CUDA(cudaMemcpyAsync(ynrm.data(), d1, nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
         KRR_CUDA(cudaStreamSynchronize(c->stream));
         for (auto &v : ynrm) v = std::sqrt(v) > 0 ? std::sqrt(v) : 1.0;
         // per-column Hessenberg (column-major (mres+1) x mres), Givens, rhs
@@ -2332,27 +2367,22 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                 KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, Zv.get(), nrhs, nrhs, Wv.get(), nrhs, H->lambda,
                                   nullptr, 0, nullptr, H->bd_or_null(btrain)));
                 tr.mark("g_apply", j, 0, 0);
-                // two passes of classical Gram-Schmidt
-                std::fill(hd.begin(), hd.end(), 0.0);
+                // two passes of classical Gram-Schmidt on the device (the
+                // coefficients stay there), the next vector normalized there
+                // too; one read-back per iteration for the Hessenberg column
                 for (int pass = 0; pass < 2; ++pass) {
-                    KRR_TRY(mdot(V.get(), j + 1, Wv.get()));
-                    KRR_CUDA(cudaMemcpyAsync(hd2.data(), dots.get(), size_t(j + 1) * nrhs * 8, cudaMemcpyDeviceToHost,
-                                             c->stream));
-                    KRR_CUDA(cudaStreamSynchronize(c->stream));
-                    std::vector<double> neg(size_t(j + 1) * nrhs);
-                    for (size_t e = 0; e < neg.size(); ++e) {
-                        hd[e] += hd2[e];
-                        neg[e] = -hd2[e];
-                    }
-                    KRR_CUDA(cudaMemcpyAsync(coef.get(), neg.data(), neg.size() * 8, cudaMemcpyHostToDevice, c->stream));
-                    { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, j + 1, coef.get(), n, nrhs); ::krr::count_launch(); }
+                    double *dp = pass == 0 ? d1 : d2;
+                    KRR_TRY(mdot(V.get(), j + 1, Wv.get(), dp));
+                    { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, j + 1, dp, -1.0, n, nrhs); ::krr::count_launch(); }
                 }
-                tr.mark("g_ortho", j, 0, 0);
-                KRR_TRY(mdot(Wv.get(), 1, Wv.get()));
-                std::vector<double> wn(nrhs);
-                KRR_CUDA(cudaMemcpyAsync(wn.data(), dots.get(), nrhs * 8, cudaMemcpyDeviceToHost, c->stream));
+                KRR_TRY(mdot(Wv.get(), 1, Wv.get(), dw));
+                { colnorm_kernel<<<g1, 256, 0, c->stream>>>(V.get() + int64_t(j + 1) * nn, Wv.get(), dw, n, nrhs); ::krr::count_launch(); }
+                KRR_CUDA(cudaGetLastError());
+                KRR_CUDA(cudaMemcpyAsync(hdots.data(), dots.get(), hdots.size() * 8, cudaMemcpyDeviceToHost, c->stream));
                 KRR_CUDA(cudaStreamSynchronize(c->stream));
-                std::vector<double> inv2(nrhs);
+                tr.mark("g_ortho", j, 0, 0);
+                for (size_t e = 0; e < size_t(j + 1) * nrhs; ++e) hd[e] = hdots[e] + hdots[size_t(mres + 1) * nrhs + e];
+                const double *wn = hdots.data() + size_t(2 * (mres + 1)) * nrhs;
                 est = 0;
                 for (int q = 0; q < nrhs; ++q) {
                     double *Hq = Hm.data() + size_t(q) * (mres + 1) * mres;
@@ -2361,7 +2391,6 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                     if (!std::isfinite(wn[q])) return fail(KRR_ERR_NO_CONVERGENCE, "hss_solve: non-finite Krylov vector");
                     const double hn1 = std::sqrt(std::max(wn[q], 0.0));
                     col[j + 1] = hn1;
-                    inv2[q] = hn1 > 0 ? 1.0 / hn1 : 0.0;
                     double *csq = cs.data() + size_t(q) * mres, *snq = sn.data() + size_t(q) * mres;
                     double *gq = g.data() + size_t(q) * (mres + 1);
                     for (int i = 0; i < j; ++i) {
@@ -2379,8 +2408,6 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                     gq[j] = csq[j] * gq[j];
                     est = std::max(est, std::fabs(gq[j + 1]) / ynrm[q]);
                 }
-                KRR_CUDA(cudaMemcpyAsync(sc.get(), inv2.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
-                { colscale_kernel<<<g1, 256, 0, c->stream>>>(V.get() + int64_t(j + 1) * nn, Wv.get(), sc.get(), n, nrhs); ::krr::count_launch(); }
                 jdone = j + 1;
                 // stop a little below tol so the true residual also meets it
                 if (est <= 0.5 * tol) break;
@@ -2398,7 +2425,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
             }
             KRR_CUDA(cudaMemcpyAsync(coef.get(), yv.data(), size_t(jdone) * nrhs * 8, cudaMemcpyHostToDevice, c->stream));
             KRR_CUDA(cudaMemsetAsync(Wv.get(), 0, nn * sizeof(double), c->stream));
-            { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, jdone, coef.get(), n, nrhs); ::krr::count_launch(); }
+            { combo_kernel<<<g1, 256, 0, c->stream>>>(Wv.get(), V.get(), nn, jdone, coef.get(), 1.0, n, nrhs); ::krr::count_launch(); }
             KRR_TRY(ulv(Wv.get(), Zv.get()));
             { axpy_kernel<<<g1, 256, 0, c->stream>>>(ap, Zv.get(), nn); ::krr::count_launch(); }
             KRR_CUDA(cudaGetLastError());
