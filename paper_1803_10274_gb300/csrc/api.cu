@@ -64,7 +64,9 @@ int sample_mixed_prepared(Ctx *c, const __half *XA, int64_t ma, const __half *XB
     const int rmax = wide ? 128 : nchunk == 1 ? 256 : nchunk <= 3 ? 128 : 64;
     for (int col = 0; col < r_total; col += rmax) {
         const int rv = r_total - col < rmax ? r_total - col : rmax;
-        const int rpad = int(round_up(rv, 64));
+        // the product MMA is 32 columns wide for up to 32 columns (the
+        // streamed wide-row kernel keeps multiples of 64)
+        const int rpad = !wide && rv <= 32 ? 32 : int(round_up(rv, 64));
         if (wide)
             KRR_TRY(launch_sample_tc_wide(c, XA, ma, XB, nb, nchunk, aug_kmma(d), RT + int64_t(col) * ldrt, rpad, ldrt,
                                           rv, leaf_a, leaf_b, S + col, lds, split_k, bd));

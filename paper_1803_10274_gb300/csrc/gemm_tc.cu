@@ -11,19 +11,19 @@
 // which leaves out A_lo B_lo and the low bits of x_lo (together about
 // 2^-21 relative to |A||B|) next to the FP32 accumulation itself.
 //
-// One CTA of 256 threads per SM walks a list of 128 x 128 output tiles over
-// all problems, in 32-wide K chunks through a three-step pipeline:
-//   1. cp.async copies the chunk's FP32 blocks of A and B (zero-filled past
-//      the matrix edges, coalesced along whichever dimension is contiguous)
-//      into one of two raw stages, two chunks ahead;
-//   2. all threads split the raw block into the four operand tiles (A_hi,
+// One CTA per SM walks a list of 128 x 128 output tiles over all problems,
+// in 32-wide K chunks through a three-step pipeline:
+//   1. warps 0-7 copy (cp.async) the chunk's FP32 blocks of A and B
+//      (zero-filled past the matrix edges, coalesced along whichever
+//      dimension is contiguous) into one of two raw stages, two chunks ahead;
+//   2. warps 0-7 split the raw block into the four operand tiles (A_hi,
 //      A_lo, B_hi, B_lo: 128 rows of 128 bytes, K-major, 128-byte swizzle)
-//      of one of two MMA stages;
-//   3. thread 0 issues the chunk's 12 MMAs (4 K-steps x 3 terms) and commits
-//      them to the MMA stage's mbarrier.
-// The epilogue reads the accumulator with tcgen05.ld (warps w and w + 4 own
-// tensor-memory lanes 32 (w mod 4) ..; one column half each), stages it in
-// shared memory and writes C row by row, coalesced.
+//      of one of two MMA stages and arrive on its FULL barrier;
+//   3. warp 8 waits FULL, issues the chunk's 12 MMAs (4 K-steps x 3 terms)
+//      and commits them to the stage's EMPTY barrier.
+// The epilogue (warps 0-7) reads the accumulator with tcgen05.ld (warps w
+// and w + 4 own tensor-memory lanes 32 (w mod 4) ..; one column half each),
+// stages it in shared memory and writes C row by row, coalesced.
 #include <algorithm>
 #include <vector>
 

@@ -52,7 +52,7 @@ static_assert(kBM == kTcTile && kBN == kTcTile, "tile lists assume square 128-ro
 struct Params {
     int64_t ma, nb;
     int64_t n_row_tiles, n_col_tiles;
-    int r;        // R / S columns handled by this launch (multiple of 64, <= 256)
+    int r;        // R / S columns handled by this launch (32, or a multiple of 64 up to 256)
     int r_valid;  // columns actually stored (<= r)
     int nchunk;   // 64-element chunks of an augmented row
     int kmma;     // K=16 MMA steps of the distance GEMM
@@ -184,7 +184,8 @@ __device__ __forceinline__ void flush_s(const Params &P, uint64_t *bars, volatil
         if (i < P.ma) {
             float *dst = P.S + i * P.lds;
             const int cbase = g * rh + cc;
-            for (int c = 0; c < 32; ++c)
+            const int cend = min(32, rh - cc);  // r = 32: each half is 16 columns
+            for (int c = 0; c < cend; ++c)
                 if (cbase + c < P.r_valid) atomicAdd(dst + cbase + c, __uint_as_float(sv[c]));
         }
     }
@@ -803,7 +804,8 @@ int tune_variant(Ctx *c, const CUtensorMap &mA, const CUtensorMap &mB, const CUt
 int launch_sample_tc(Ctx *c, const __half *XA, int64_t ma, const __half *XB, int64_t nb, int nchunk, int kmma,
                      const __half *RT, int rpad, int64_t ldrt, int r_valid, const int32_t *leaf_a,
                      const int32_t *leaf_b, float *S, int64_t lds, bool split_k, const BlockDiag *bd) {
-    if (rpad % 64 != 0 || rpad < 64 || rpad > 256) return fail(KRR_ERR_INVALID_ARG, "sample_tc: r must be 64..256, /64");
+    if ((rpad % 64 != 0 && rpad != 32) || rpad < 32 || rpad > 256)
+        return fail(KRR_ERR_INVALID_ARG, "sample_tc: r must be 32, or 64..256 in steps of 64");
     if (nchunk < 1 || nchunk > 4) return fail(KRR_ERR_INVALID_ARG, "sample_tc: feature dimension too large");
     if (ma <= 0 || nb <= 0) return KRR_OK;
     if (ldrt % 8 != 0) return fail(KRR_ERR_INVALID_ARG, "sample_tc: ldrt must be a multiple of 8");

@@ -46,7 +46,10 @@ def _cuda(a):
                                          (1500, 2000, 19, 100, 2.0),    # one 64-wide feature chunk, full
                                          (700, 900, 33, 300, 1.5),      # two chunks, 2 launches of columns
                                          (640, 1000, 54, 100, 2.0),     # three chunks, one row-tile buffer
-                                         (300, 513, 80, 64, 3.0)])      # four chunks
+                                         (300, 513, 80, 64, 3.0),       # four chunks
+                                         (1000, 1300, 8, 20, 1.0),      # 32-column product (10 GMRES columns x 2)
+                                         (900, 700, 19, 32, 1.5),       # 32 columns, one 64-wide chunk
+                                         (500, 600, 54, 7, 2.0)])       # 32 columns, three chunks
 def test_mixed_matches_oracle(K, ctx, ma, nb, d, r, h):
     Xa = synth.mixture(ma, d, 4, 0.7, 10 + d)[0].astype(np.float32)
     Xb = synth.mixture(nb, d, 4, 0.7, 20 + d)[0].astype(np.float32)
@@ -59,8 +62,9 @@ def test_mixed_matches_oracle(K, ctx, ma, nb, d, r, h):
     assert np.all(err <= tol), float((err / tol).max())
 
 
-def test_mixed_masked_and_lambda(K, ctx):
-    n, d, r, h, lam = 1200, 8, 64, 1.0, 4.0
+@pytest.mark.parametrize("r", [64, 20])
+def test_mixed_masked_and_lambda(K, ctx, r):
+    n, d, h, lam = 1200, 8, 1.0, 4.0
     X = synth.mixture(n, d, 6, 0.7, 3)[0].astype(np.float32)
     R = synth.gaussian_block(n, r, 6).astype(np.float32)
     leaf = (np.arange(n) * 7 // 97).astype(np.int32)      # uneven leaves, not tile aligned
