@@ -667,15 +667,18 @@ def bench_million(K, ctx, n=1 << 20, r=256, reps=2):
             "algorithmic_flops": "2 n^2 (d + r)"}
 
 
-def solve_only(reps=8):
-    """Compression and factorization of the benchmark workload, then reps
-    single ULV solves (no refinement) of its 10 right-hand sides, for
-    profiling the factor and solve kernels; prints the mean solve time."""
+def solve_only(reps=8, n=None):
+    """Compression and factorization of the benchmark workload (or of its
+    first n points), then reps single ULV solves (no refinement) of its 10
+    right-hand sides, for profiling the factor and solve kernels; prints the
+    mean solve time."""
     import torch
     import paper_1803_10274_gb300 as K
     torch.cuda.set_device(0)
     ctx = K.Context()
     X, Xt, Y, yt = _inputs()
+    if n:
+        X, Y = X[:n], np.ascontiguousarray(Y[:n])
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     K.krr_standardize(ctx, Xd)
     o = K.default_options(h=WL["h"], lambda_=WL["lam"], eps_c=WL["eps_c"], leaf=WL["leaf"], precision=K.KRR_MIXED,
@@ -690,8 +693,36 @@ def solve_only(reps=8):
         H.solve(Yd, tol=0.0)
     e1.record(ctx.stream)
     ctx.sync()
-    print(json.dumps({"n": WL["n"], "nrhs": WL["nrhs"], "ulv_solve_ms": e0.elapsed_time(e1) / reps}), flush=True)
+    print(json.dumps({"n": len(X), "nrhs": WL["nrhs"], "ulv_solve_ms": e0.elapsed_time(e1) / reps}), flush=True)
     H.close()
+
+
+def gemm_only(nb):
+    """nb Gram products S_b S_b^T of 128 x 2032 FP32 blocks (a level of
+    interpolative decompositions at 2048 samples) through
+    krr_gemm_f32_batched on the tensor cores and on the CUDA cores; prints
+    the mean time and TFLOP/s of each (for profilers)."""
+    import torch
+    import paper_1803_10274_gb300 as K
+    torch.cuda.set_device(0)
+    ctx = K.Context()
+    m, k = 128, 2032
+    S = torch.randn(nb, m, k, generator=torch.Generator().manual_seed(1)).cuda()
+    out = {"batch": nb, "m": m, "k": k}
+    for path, name in ((1, "tensor_cores"), (2, "cuda_cores")):
+        C = torch.zeros(nb, m, m, device="cuda")
+        for _ in range(3):
+            K.krr_gemm_f32_batched(ctx, S, S, C, tb=True, path=path)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(5):
+            K.krr_gemm_f32_batched(ctx, S, S, C, tb=True, path=path)
+        e1.record(ctx.stream)
+        ctx.sync()
+        ms = e0.elapsed_time(e1) / 5
+        out[name] = {"ms": ms, "tflops": 2.0 * nb * m * m * k / ms / 1e9}
+    print(json.dumps(out), flush=True)
 
 
 def step_only(steps, warmup):
@@ -842,7 +873,9 @@ def main():
     ap.add_argument("--image", action="store_true", help="with --sample-only: MNIST-shaped rows (d=784)")
     ap.add_argument("--batch-only", action="store_true", help="only run the MNIST-shaped and batched-problems workloads")
     ap.add_argument("--orderings-only", action="store_true", help="only run the comparison of the orderings")
-    ap.add_argument("--solve-only", action="store_true",
+    ap.add_argument("--gemm-only", type=int, metavar="NB",
+                    help="only run NB batched 128 x 128 x 2032 Gram products on both GEMM paths (for profilers)")
+    ap.add_argument("--solve-only", nargs="?", type=int, const=0, default=None, metavar="N",
                     help="only compress, factor and run single ULV solves (for profilers)")
     ap.add_argument("--step-only", action="store_true",
                     help="only run --warmup + --steps KRR steps, nothing else (for launch lists)")
@@ -860,8 +893,10 @@ def main():
         ctx = K.Context()
         l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
         print(json.dumps({"image_d784": bench_image(K, ctx, l2), "batch": bench_batch(K, ctx, l2)}), flush=True)
-    elif args.solve_only:
-        solve_only()
+    elif args.solve_only is not None:
+        solve_only(n=args.solve_only or None)
+    elif args.gemm_only:
+        gemm_only(args.gemm_only)
     elif args.step_only:
         step_only(args.steps, args.warmup)
     elif args.peaks:
