@@ -291,59 +291,93 @@ __global__ void __launch_bounds__(NT) gram_init_kernel(const NodeDesc *nd, T *F,
 // Pivots [j0, j0 + kPanel) of every unfinished node: column j of L is
 // (G(q, p_j) - sum_{t in [j0, j)} L(q, t) L(p_j, t)) / L(p_j, j) over the
 // rows not yet chosen, G already updated by the earlier panels.  Stops at
-// the rank rule or at jmax.
+// the rank rule or at jmax.  The remaining diagonal d lives in shared
+// memory for the panel, and so do the panel's columns of L when they fit
+// (ldl >= m rows; else they are read from global memory); row p_j of the
+// panel is broadcast through shared memory.  Rows already chosen get 0 in
+// the panel's later columns.  Three CTA barriers per pivot.
 template <class T, int NT>
 __global__ void __launch_bounds__(NT) gram_panel_kernel(const NodeDesc *nd, T *F, int32_t *I, GramState<T> *st,
-                                                        int j0, int rid, int kmax, T eps, T eps_abs, T r11_cap) {
+                                                        int j0, int rid, int kmax, T eps, T eps_abs, T r11_cap,
+                                                        int ldl) {
+    extern __shared__ __align__(16) unsigned char gp_smem[];
+    __shared__ T prow[kPanel];
     GramState<T> &S = st[blockIdx.x];
     if (S.done) return;
     const NodeDesc &N = nd[blockIdx.x];
     const int m = N.m;
     const T *A = F + N.drr;
     T *Lc = F + N.w;
-    T *d = F + N.norm;
+    T *dg = F + N.norm;
     int32_t *piv = I + N.piv;
+    T *ds = reinterpret_cast<T *>(gp_smem);       // m entries
+    T *Ls = ds + ((ldl > 0 ? ldl : m) + 3) / 4 * 4;  // kPanel x ldl (column t at Ls + t ldl)
+    const bool in_sm = ldl >= m;
     const int jmax = min(min(m, rid), kmax);
     const int jend = min(j0 + kPanel, jmax);
+    for (int q = threadIdx.x; q < m; q += NT) ds[q] = dg[q];
+    __syncthreads();
     T r11 = S.r11;
     int j = j0;
     for (; j < jend; ++j) {
         T best = T(-1);
         int bi = 0x7fffffff;
         for (int q = threadIdx.x; q < m; q += NT)
-            if (d[q] > best) { best = d[q]; bi = q; }
+            if (ds[q] > best) { best = ds[q]; bi = q; }
         argmax_nt<T, NT>(best, bi);  // synchronizes
         const T nrm = sqrt(best > T(0) ? best : T(0));
         if (j == 0) r11 = nrm < r11_cap ? nrm : r11_cap;
         if (!(nrm > eps * r11) || !(nrm > eps_abs)) break;
         const int p = bi;
         const T inv = T(1) / nrm;
+        const int nt = j - j0;
+        if (threadIdx.x < nt) prow[threadIdx.x] = in_sm ? Ls[threadIdx.x * ldl + p] : Lc[int64_t(j0 + threadIdx.x) * m + p];
+        __syncthreads();
         const T *gp = A + int64_t(p) * m;  // row p of the symmetric G: column p
         for (int q = threadIdx.x; q < m; q += NT) {
+            T v;
             if (q == p) {
-                Lc[int64_t(j) * m + q] = nrm;
-                continue;
+                v = nrm;
+                ds[q] = -INFINITY;
+            } else if (!(ds[q] >= T(0))) {
+                v = T(0);  // already chosen
+            } else {
+                T sacc = gp[q];
+                if (in_sm)
+                    for (int t = 0; t < nt; ++t) sacc -= Ls[t * ldl + q] * prow[t];
+                else
+                    for (int t = 0; t < nt; ++t) sacc -= Lc[int64_t(j0 + t) * m + q] * prow[t];
+                v = sacc * inv;
+                const T dq = ds[q] - v * v;
+                ds[q] = dq > T(0) ? dq : T(0);
             }
-            if (!(d[q] >= T(0))) continue;  // already chosen
-            T sacc = gp[q];
-            for (int t = j0; t < j; ++t) sacc -= Lc[int64_t(t) * m + q] * Lc[int64_t(t) * m + p];
-            const T v = sacc * inv;
-            Lc[int64_t(j) * m + q] = v;
-            const T dq = d[q] - v * v;
-            d[q] = dq > T(0) ? dq : T(0);
+            if (in_sm) Ls[nt * ldl + q] = v;
+            else Lc[int64_t(j) * m + q] = v;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            piv[j] = p;
-            d[p] = -INFINITY;
-        }
+        if (threadIdx.x == 0) piv[j] = p;
         __syncthreads();
     }
+    // the panel's columns of L and the remaining diagonal back to global memory
+    if (in_sm)
+        for (int t = 0; t < j - j0; ++t)
+            for (int q = threadIdx.x; q < m; q += NT) Lc[int64_t(j0 + t) * m + q] = Ls[t * ldl + q];
+    for (int q = threadIdx.x; q < m; q += NT) dg[q] = ds[q];
     if (threadIdx.x == 0) {
         S.r11 = r11;
         S.k = j;
         if (j < jend || j == jmax) S.done = 1;
     }
+}
+
+// Shared memory of gram_panel_kernel for nodes of up to mmax rows: the
+// diagonal, and the panel's columns of L when all fit in 200 KB (ldl = mmax,
+// else ldl = 0: L stays in global memory).
+template <class T>
+inline void gram_panel_smem(int mmax, int &ldl, size_t &bytes) {
+    const size_t dbytes = size_t((mmax + 3) / 4 * 4) * sizeof(T);
+    const size_t lbytes = size_t(kPanel) * mmax * sizeof(T);
+    ldl = dbytes + lbytes <= size_t(200) * 1024 ? mmax : 0;
+    bytes = dbytes + (ldl ? lbytes : 0);
 }
 
 // After the factorization, in three steps.  gram_prep_kernel: the unchosen
@@ -1565,9 +1599,17 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             const int jmax = std::min(std::min(mmax, rid), kmax);
             std::vector<GramState<T>> hs(nn);
             std::vector<char> live(nn, 1);
+            int ldl = 0;
+            size_t psm = 0;
+            gram_panel_smem<T>(mmax, ldl, psm);
+            {
+                static SmemLimitOnce lim1024, lim256;
+                if (wide) KRR_CUDA(raise_smem_limit(lim1024, c->device, gram_panel_kernel<T, 1024>, int(psm)));
+                else KRR_CUDA(raise_smem_limit(lim256, c->device, gram_panel_kernel<T, 256>, int(psm)));
+            }
             for (int j0 = 0; j0 < jmax; j0 += kPanel) {
-                if (wide) { gram_panel_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid))); ::krr::count_launch(); }
-                else { gram_panel_kernel<T, 256><<<nn, 256, 0, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid))); ::krr::count_launch(); }
+                if (wide) { gram_panel_kernel<T, 1024><<<nn, 1024, psm, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid)), ldl); ::krr::count_launch(); }
+                else { gram_panel_kernel<T, 256><<<nn, 256, psm, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid)), ldl); ::krr::count_launch(); }
                 KRR_CUDA(cudaGetLastError());
                 KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
                                          c->stream));
