@@ -1,6 +1,8 @@
 // Data-preparation kernels: feature standardization, row gathers, the
 // augmented FP16 operands of the fused product, FP16 transposes, and the
 // method's random block (Philox4x64-10 + Box-Muller).
+#include <algorithm>
+
 #include "common.cuh"
 #include "prep.cuh"
 
@@ -275,6 +277,105 @@ __global__ void random_block_kernel(int64_t n, int r, int col0, uint64_t seed, i
     }
 }
 
+// The mixed path stores every element rounded to FP16, so FP32 arithmetic
+// suffices wherever the value is not close to an FP16 rounding boundary.
+// Same counters and words as random_block_kernel; the Box-Muller steps in
+// FP32 with the argument reductions done exactly in integers:
+//   u1 = (2 m1 + 1) 2^-54:  ln u1 = logf(u1) for u1 <= 1/2, else
+//                           log1pf(-(1 - u1)) with 1 - u1 = (2^54 - 2 m1 - 1) 2^-54;
+//   2 pi u2 = pi t 2^-53, t = 2 m2 + 1:  quadrant q = t >> 52 and the
+//                           remainder f (or 1/2 - f, the octant's mirror) in
+//                           [0, 1/4], then sincospif and a quarter-turn rotation.
+// Each value is then within a few FP32 ulps of the exact one.  A value
+// within 2^-19 (relative) of an FP16 rounding boundary is listed and
+// recomputed by the FP64 steps (random_fix_kernel), so the stored FP16
+// values are those of the FP64 computation.
+__device__ __forceinline__ void box_muller_f32(uint64_t w1, uint64_t w2, float &z0, float &z1) {
+    const uint64_t m1 = w1 >> 11, m2 = w2 >> 11;
+    const uint64_t t1 = 2 * m1 + 1;  // u1 = t1 2^-54
+    float L;
+    if (t1 <= (uint64_t(1) << 53)) L = logf(__ull2float_rn(t1) * 5.551115123125783e-17f);  // 2^-54
+    else L = log1pf(-(__ull2float_rn((uint64_t(1) << 54) - t1) * 5.551115123125783e-17f));
+    const float rho = sqrtf(-2.f * L);
+    const uint64_t t2 = 2 * m2 + 1;  // 2 u2 = t2 2^-53
+    const int q = int(t2 >> 52);
+    const uint64_t rem = t2 - (uint64_t(q) << 52);  // f = rem 2^-53 in [0, 1/2)
+    float sf, cf;  // sin(pi f), cos(pi f)
+    if (rem <= (uint64_t(1) << 51)) {
+        sincospif(__ull2float_rn(rem) * 1.1102230246251565e-16f, &sf, &cf);  // 2^-53
+    } else {
+        float sg, cg;
+        sincospif(__ull2float_rn((uint64_t(1) << 52) - rem) * 1.1102230246251565e-16f, &sg, &cg);
+        sf = cg;
+        cf = sg;
+    }
+    float c, sn;  // cos and sin of pi (q / 2 + f)
+    if (q == 0) { c = cf; sn = sf; }
+    else if (q == 1) { c = -sf; sn = cf; }
+    else if (q == 2) { c = -cf; sn = -sf; }
+    else { c = sf; sn = -cf; }
+    z0 = rho * c;
+    z1 = rho * sn;
+}
+
+__device__ __forceinline__ bool near_half_tie(float z) {
+    const float e = 1.9073486328125e-06f;  // 2^-19
+    return __float2half_rn(z * (1.f + e)) != __float2half_rn(z * (1.f - e));
+}
+
+__device__ __forceinline__ double box_muller_f64(const U64x4 &w, int t) {
+    const int pr = t >> 1;
+    const double u1 = u01(w.v[2 * pr]), u2 = u01(w.v[2 * pr + 1]);
+    const double rho = sqrt(-2.0 * log(u1));
+    double sv, cv;
+    sincospi(2.0 * u2, &sv, &cv);
+    return (t & 1) ? rho * sv : rho * cv;
+}
+
+__global__ void random_block16_kernel(int64_t n, int r, int col0, uint64_t seed, float *out, int64_t ld,
+                                      uint64_t *fix, unsigned *nfix, unsigned cap) {
+    const int ng = (r + 3) / 4;
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n * ng) return;
+    const int64_t j = k / ng;
+    const int g = int(k % ng);
+    const U64x4 w = philox4x64_10(uint64_t(j), uint64_t(col0 / 4 + g), 0, 0, seed, kStreamR);
+    float z[4];
+    box_muller_f32(w.v[0], w.v[1], z[0], z[1]);
+    box_muller_f32(w.v[2], w.v[3], z[2], z[3]);
+    for (int t = 0; t < 4; ++t) {
+        const int cc = 4 * g + t;
+        if (cc >= r) break;
+        if (near_half_tie(z[t])) {
+            const unsigned slot = atomicAdd(nfix, 1u);
+            if (slot < cap) fix[slot] = (uint64_t(j) << 24) | uint64_t(cc);
+        }
+        out[j * ld + cc] = __half2float(__float2half_rn(z[t]));
+    }
+}
+
+// The listed values by the FP64 steps of random_block_kernel (every value
+// when the list overflowed).
+__global__ void random_fix_kernel(int64_t n, int r, int col0, uint64_t seed, float *out, int64_t ld,
+                                  const uint64_t *fix, const unsigned *nfix, unsigned cap) {
+    const unsigned cnt = *nfix;
+    const int64_t total = cnt <= cap ? int64_t(cnt) : n * r;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        int64_t j;
+        int cc;
+        if (cnt <= cap) {
+            j = int64_t(fix[e] >> 24);
+            cc = int(fix[e] & 0xFFFFFFu);
+        } else {
+            j = e / r;
+            cc = int(e % r);
+        }
+        const U64x4 w = philox4x64_10(uint64_t(j), uint64_t(col0 / 4 + cc / 4), 0, 0, seed, kStreamR);
+        out[j * ld + cc] = __half2float(__double2half(box_muller_f64(w, cc & 3)));
+    }
+}
+
 int random_block(Ctx *c, int64_t n, int r, int col0, uint64_t seed, int precision, void *out, int64_t ld) {
     if (col0 % 4 != 0) return fail(KRR_ERR_INVALID_ARG, "random_block: col0 must be a multiple of 4");
     if (n == 0 || r == 0) return KRR_OK;
@@ -282,8 +383,19 @@ int random_block(Ctx *c, int64_t n, int r, int col0, uint64_t seed, int precisio
     const unsigned grid = unsigned(cdiv(n * ng, 256));
     if (precision == KRR_FP64)
         { random_block_kernel<double><<<grid, 256, 0, c->stream>>>(n, r, col0, seed, 0, static_cast<double *>(out), ld); ::krr::count_launch(); }
-    else
+    else if (r >= (1 << 24))
         { random_block_kernel<float><<<grid, 256, 0, c->stream>>>(n, r, col0, seed, 1, static_cast<float *>(out), ld); ::krr::count_launch(); }
+    else {
+        // FP32 steps, the values near an FP16 rounding boundary redone in FP64
+        // (about 1 % expected; a list of 1/16 of the block, all redone if it overflows)
+        const unsigned cap = unsigned(std::min<int64_t>(int64_t(1) << 30, std::max<int64_t>(4096, n * r / 16)));
+        DBuf<uint64_t> fix(c, cap);
+        DBuf<unsigned> nfix(c, 1);
+        if (!fix.get() || !nfix.get()) return fail(KRR_ERR_OOM, "random_block: out of memory");
+        KRR_CUDA(cudaMemsetAsync(nfix.get(), 0, sizeof(unsigned), c->stream));
+        { random_block16_kernel<<<grid, 256, 0, c->stream>>>(n, r, col0, seed, static_cast<float *>(out), ld, fix.get(), nfix.get(), cap); ::krr::count_launch(); }
+        { random_fix_kernel<<<unsigned(2 * c->num_sms), 256, 0, c->stream>>>(n, r, col0, seed, static_cast<float *>(out), ld, fix.get(), nfix.get(), cap); ::krr::count_launch(); }
+    }
     KRR_CUDA(cudaGetLastError());
     return KRR_OK;
 }
