@@ -181,7 +181,10 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     peaks, peak_src = _peaks()
     ctx = K.Context()
-    ctx.set_autotune(True)  # fused-product launch variants picked by measurement (during warm-up)
+    # The step runs the fused product's default launch variants: autotuned
+    # variants change the products' summation order, and with it the IDs and
+    # the GMRES iteration count (23 against 27 at this size), by more than
+    # they gain.  The kernel-alone measurements below are autotuned.
     stream = ctx.stream
     X, Xt, Y, yt = _inputs()
     Xd, Xtd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Xt).cuda(), torch.from_numpy(Y).cuda()
@@ -241,6 +244,7 @@ def run_ours(args):
         return
 
     # ---- fused sampling kernel alone: algorithmic TFLOP/s (CUDA events on the library's stream)
+    ctx.set_autotune(True)  # launch variants picked by measurement (first call of each shape class)
     Xs = Xd.clone()
     K.krr_standardize(ctx, Xs)
     samp = {}
@@ -289,6 +293,7 @@ def run_ours(args):
                  "fp64_product_n16384_r64": {"seconds": t64, "tflops": f64_tflops,
                                              "frac_of_fp64_fma": f64_tflops / rates["fp64_fma_tflops"]}}
 
+    ctx.set_autotune(False)  # the end-to-end steps and the extra workloads: default variants, as the step
     # ---- end to end through host buffers (H2D inputs, D2H weights + predictions inside the timed region)
     Xh = torch.from_numpy(X).pin_memory()
     Xth = torch.from_numpy(Xt).pin_memory()
