@@ -2139,10 +2139,12 @@ int ulv_solve_graph(HssImpl *H, const T *y, T *x, int nrhs) {
 // Fused product K(Xa, Xp) V for nrhs columns of V (double, n x nrhs, in
 // cluster order) in the path's precision; out = double m x nrhs.  With
 // lambda != 0 (Xa == Xp) adds lambda V.  Mixed: V is split into two FP16
-// parts so the product keeps FP32 precision in V.
+// parts so the product keeps FP32 precision in V, and K too when precise
+// (K = K_hi + K_lo); otherwise K is rounded to FP16 (relaxed GMRES inner
+// products).
 int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, const double *V, int64_t ldv, int nrhs,
               double *out, int64_t ldo, double lambda, const double *y, int64_t ldy, double *res_norms,
-              const BlockDiag *bd, const double *Xa64_rows = nullptr) {
+              const BlockDiag *bd, const double *Xa64_rows = nullptr, bool precise = true) {
     Ctx *c = H->c;
     const int64_t n = H->n;
     if (H->tc()) {
@@ -2173,7 +2175,7 @@ int hss_apply(HssImpl *H, const float *Xa32, const __half *XAa, int64_t ma, cons
         { split16_kernel<<<unsigned(cdiv(n * nrhs, 256)), 256, 0, c->stream>>>(V, n, nrhs, ldv, Rs, cols); ::krr::count_launch(); }
         KRR_TRY(transpose_half(c, Rs, n, cols, cols, RTs, rpad, H->ldrt));
         KRR_TRY(sample_mixed_prepared(c, XAa, ma, H->XB.get(), n, H->d, RTs, cols, H->ldrt, nullptr, nullptr,
-                                      Sm, cols, true, bd));
+                                      Sm, cols, precise, bd));
         if (y)
             { residual_kernel<float><<<unsigned(cdiv(ma * nrhs, 256)), 256, 0, c->stream>>>(
                 y, ldy, Sm, cols, 1, V, ldv, ma, nrhs, lambda, out, ldo, res_norms); ::krr::count_launch(); }
@@ -2347,6 +2349,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
         // iteration); Gram-Schmidt runs twice (CGS2).  Restarts recompute
         // the true residual with the precise (split-K) fused product.
         const int mres = 30;
+        constexpr double kRelaxSwitch = 0.1 * 2048.0;  // 0.1 / 2^-11
         const int64_t nn = n * nrhs;
         // dots: the two Gram-Schmidt passes' coefficients (mres + 1 rows of
         // nrhs each) and the new vector's squared norms, read back together
@@ -2406,8 +2409,14 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                 double *Vj = V.get() + int64_t(j) * nn;
                 KRR_TRY(ulv(Vj, Zv.get()));
                 tr.mark("g_ulv", j, 0, 0);
+                // Relaxed inner products (inexact Krylov): once the estimated
+                // residual est is small, an operator error of eta est is
+                // allowed with eta ~ tol / est; K rounded to FP16 (2^-11 per
+                // entry) is used where 2^-11 <= 0.1 tol / est.  Restarts and
+                // the final check use the precise product.
+                const bool precise = est > kRelaxSwitch * tol;
                 KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, Zv.get(), nrhs, nrhs, Wv.get(), nrhs, H->lambda,
-                                  nullptr, 0, nullptr, H->bd_or_null(btrain)));
+                                  nullptr, 0, nullptr, H->bd_or_null(btrain), nullptr, precise));
                 tr.mark("g_apply", j, 0, 0);
                 // two passes of classical Gram-Schmidt on the device (the
                 // coefficients stay there), the next vector normalized there
