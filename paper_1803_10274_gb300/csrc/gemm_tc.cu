@@ -381,6 +381,7 @@ bool tc_gemm_wanted(const Ctx *c, const std::vector<GemmProb<float>> &v) {
     if (v.empty()) return false;
     double flops = 0, tile_area = 0, area = 0;
     for (const GemmProb<float> &p : v) {
+        if (p.skip) return false;  // run-time skips are the CUDA-core kernel's
         flops += 2.0 * p.M * p.N * double(p.K);
         area += double(p.M) * p.N;
         tile_area += double(cdiv(p.M, gtc::kBM) * gtc::kBM) * double(cdiv(p.N, gtc::kBN) * gtc::kBN);

@@ -19,6 +19,7 @@ struct GemmProb {
     T alpha, beta;
     int tile0, tn;  // first tile index of this problem, tiles along N
     int atomic;     // 1: one K-slice of a split product, added into C atomically
+    const int *skip;  // the product is skipped when *skip != 0 at run time (NULL: never)
 };
 
 // A region of C to clear before split products add into it.
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(256) grouped_gemm_kernel(const GemmProb<T> *pr
             else hi = mid - 1;
         }
         const GemmProb<T> &P = probs[lo];
+        if (P.skip && __ldcg(P.skip)) continue;  // the same for the whole CTA
         const int t = tile - P.tile0;
         const int i0 = (t / P.tn) * 64, j0 = (t % P.tn) * TN;
         const int M = P.M, N = P.N, K = P.K;
@@ -310,6 +312,7 @@ struct GemmBatch {
               T beta, T *C, int64_t ldc, int atomic) {
         GemmProb<T> p;
         p.atomic = atomic;
+        p.skip = nullptr;
         p.A = A;
         p.B = B;
         p.C = C;

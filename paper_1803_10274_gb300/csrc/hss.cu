@@ -1607,20 +1607,28 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
                 if (wide) KRR_CUDA(raise_smem_limit(lim1024, c->device, gram_panel_kernel<T, 1024>, int(psm)));
                 else KRR_CUDA(raise_smem_limit(lim256, c->device, gram_panel_kernel<T, 256>, int(psm)));
             }
-            for (int j0 = 0; j0 < jmax; j0 += kPanel) {
+            for (int j0 = 0, np = 0; j0 < jmax; j0 += kPanel, ++np) {
                 if (wide) { gram_panel_kernel<T, 1024><<<nn, 1024, psm, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid)), ldl); ::krr::count_launch(); }
                 else { gram_panel_kernel<T, 256><<<nn, 256, psm, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid)), ldl); ::krr::count_launch(); }
                 KRR_CUDA(cudaGetLastError());
-                KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
-                                         c->stream));
-                KRR_CUDA(cudaStreamSynchronize(c->stream));
+                if (j0 + kPanel >= jmax) break;
+                // the host reads which nodes finished every fourth panel only;
+                // in between, the update of a node that finished is skipped on
+                // the device (its done flag)
+                if (np % 4 == 3) {
+                    KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
+                                             c->stream));
+                    KRR_CUDA(cudaStreamSynchronize(c->stream));
+                    for (int a = 0; a < nn; ++a) live[a] = !hs[a].done;
+                }
                 // update of the nodes still running: G -= L_p L_p^T (L_p: m x kPanel, column-major)
                 GemmBatch<T> gt;
                 for (int a = 0; a < nn; ++a) {
-                    if (hs[a].done) continue;
                     const NodeDesc &N = lvdesc[a];
+                    if (!live[a] || N.m <= 0) continue;
                     const T *Lp = F + N.w + int64_t(j0) * N.m;
                     gt.add(N.m, N.m, kPanel, T(-1), Lp, N.m, true, Lp, N.m, false, T(1), F + N.drr, N.m);
+                    gt.v.back().skip = &gs.get()[a].done;
                 }
                 if (gt.v.empty()) break;
                 KRR_TRY(gt.launch(c));
