@@ -122,8 +122,19 @@ __global__ void parent_sloc_kernel(const NodeDesc *nd, const NodeDesc *all, int 
     T *Sl = F + N.sloc;
     // gridDim.y CTAs share a node (the top levels have few, large nodes)
     const int64_t t0 = int64_t(blockIdx.y) * blockDim.x + threadIdx.x, step = int64_t(gridDim.y) * blockDim.x;
-    for (int64_t e = t0; e < int64_t(ka) * r; e += step) Sl[e] = F[A.skel + e];
-    for (int64_t e = t0; e < int64_t(kb) * r; e += step) Sl[int64_t(ka) * r + e] = F[B.skel + e];
+    // four loads in flight per thread before its stores
+    const int64_t tot = int64_t(ka + kb) * r, na = int64_t(ka) * r;
+    for (int64_t e0 = t0; e0 < tot; e0 += 4 * step) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t e = e0 + u * step;
+            if (e < tot) v[u] = e < na ? F[A.skel + e] : F[B.skel + (e - na)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e0 + u * step < tot) Sl[e0 + u * step] = v[u];
+    }
     for (int64_t a = t0; a < ka; a += step) I[N.rows + a] = I[A.jsk + a];
     for (int64_t a = t0; a < kb; a += step) I[N.rows + ka + a] = I[B.jsk + a];
 }
@@ -426,39 +437,53 @@ __global__ void __launch_bounds__(256) gram_copy_kernel(const NodeDesc *nd, cons
     const int32_t *piv = I + N.piv;
     const int32_t *pos = I + N.ipiv;
     const int64_t t0 = int64_t(blockIdx.y) * blockDim.x + threadIdx.x, step = int64_t(gridDim.y) * blockDim.x;
+    // Each thread gathers four elements before it stores any (a store
+    // between two loads would order the second load after it), so four
+    // loads are in flight per thread.
+    auto copy4 = [&](int64_t total, auto load, auto store) {
+        for (int64_t e0 = t0; e0 < total; e0 += 4 * step) {
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u * step < total) v[u] = load(e0 + u * step);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e0 + u * step < total) store(e0 + u * step, v[u]);
+        }
+    };
     const T *Sorig = N.is_leaf ? S + int64_t(N.leaf_begin) * ldsr : F + N.sloc;
     const int64_t lds = N.is_leaf ? ldsr : r;
     T *Sk = F + N.skel;
-    for (int64_t e = t0; e < int64_t(k) * r; e += step) {
-        const int a = int(e / r), t = int(e % r);
-        Sk[e] = Sorig[int64_t(piv[a]) * lds + t];
-    }
+    copy4(int64_t(k) * r, [&](int64_t e) { return Sorig[int64_t(piv[e / r]) * lds + e % r]; },
+          [&](int64_t e, T v) { Sk[e] = v; });
     const NodeDesc *A = N.is_leaf ? nullptr : &all[N.child_a];
     const NodeDesc *B = N.is_leaf ? nullptr : &all[N.child_b];
     T *Rg = F + N.rg;
     T *Rh = F + N.rhat;
-    for (int64_t e = t0; e < int64_t(m) * r; e += step) {
-        const int a = int(e / r), t = int(e % r);
-        const int src = piv[a];
-        T v;
-        if (N.is_leaf) v = R[(int64_t(N.leaf_begin) + src) * ldsr + t];
-        else if (src < A->k) v = F[A->rhat + int64_t(src) * r + t];
-        else v = F[B->rhat + int64_t(src - A->k) * r + t];
-        Rg[e] = v;
-        if (a < k) Rh[e] = v;
-    }
+    copy4(int64_t(m) * r,
+          [&](int64_t e) {
+              const int a = int(e / r), t = int(e % r);
+              const int src = piv[a];
+              if (N.is_leaf) return R[(int64_t(N.leaf_begin) + src) * ldsr + t];
+              if (src < A->k) return F[A->rhat + int64_t(src) * r + t];
+              return F[B->rhat + int64_t(src - A->k) * r + t];
+          },
+          [&](int64_t e, T v) {
+              Rg[e] = v;
+              if (e / r < k) Rh[e] = v;
+          });
     T *Lp = F + N.dmat;
-    for (int64_t e = t0; e < int64_t(m) * k; e += step) {  // reads of Lc coalesced over q
-        const int b = int(e / m), q = int(e % m);
-        const int a = pos[q];
-        Lp[int64_t(a) * k + b] = (b <= a) ? Lc[e] : T(0);
-    }
+    copy4(int64_t(m) * k,  // reads of Lc coalesced over q
+          [&](int64_t e) {
+              const int b = int(e / m), a = pos[int(e % m)];
+              return (b <= a) ? Lc[e] : T(0);
+          },
+          [&](int64_t e, T v) { Lp[int64_t(pos[int(e % m)]) * k + e / m] = v; });
     T *Tm = F + N.tmat;
     const int nr = m - k;
-    for (int64_t e = t0; e < int64_t(k) * nr; e += step) {
-        const int a = int(e / nr), c = int(e % nr);
-        Tm[e] = Lc[int64_t(a) * m + piv[k + c]];
-    }
+    if (nr > 0)
+        copy4(int64_t(k) * nr, [&](int64_t e) { return Lc[(e / nr) * m + piv[k + int(e % nr)]]; },
+              [&](int64_t e, T v) { Tm[e] = v; });
 }
 
 // Rows [a0, min(a1, k)) of T: back substitution with the diagonal block of
