@@ -395,4 +395,36 @@ struct GemmBatch {
     }
 };
 
+// A sequence of CUDA-core batches (the steps of a blocked triangular solve,
+// the panels of a blocked factorization) uploaded in one copy and launched
+// one by one without a host-to-device copy or an allocation per step.
+template <class T, int TN = 64>
+struct GemmSeq {
+    std::vector<GemmProb<T>> all;
+    std::vector<int> off, np, tiles;
+    DBuf<GemmProb<T>> d;
+    // appends the batch as the next step (the batch is left empty; no
+    // clearing jobs: every product of a sequence accumulates into C)
+    void add_step(GemmBatch<T, TN> &b) {
+        off.push_back(int(all.size()));
+        np.push_back(int(b.v.size()));
+        tiles.push_back(b.tiles);
+        all.insert(all.end(), b.v.begin(), b.v.end());
+        b.v.clear();
+        b.tiles = 0;
+    }
+    int upload(Ctx *c) {
+        if (all.empty()) return KRR_OK;
+        if (!d.reset(c, all.size())) return fail(KRR_ERR_OOM, "grouped gemm: out of memory");
+        KRR_CUDA(cudaMemcpyAsync(d.get(), all.data(), all.size() * sizeof(GemmProb<T>), cudaMemcpyHostToDevice,
+                                 c->stream));
+        return KRR_OK;
+    }
+    int launch(Ctx *c, int step) const {
+        if (np[step] == 0) return KRR_OK;
+        KRR_CUDA((launch_grouped<T, TN>(c, d.get() + off[step], np[step], tiles[step])));
+        return KRR_OK;
+    }
+};
+
 }  // namespace krr

@@ -1623,7 +1623,6 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
             KRR_CUDA(cudaGetLastError());
             const int jmax = std::min(std::min(mmax, rid), kmax);
             std::vector<GramState<T>> hs(nn);
-            std::vector<char> live(nn, 1);
             int ldl = 0;
             size_t psm = 0;
             gram_panel_smem<T>(mmax, ldl, psm);
@@ -1632,31 +1631,37 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
                 if (wide) KRR_CUDA(raise_smem_limit(lim1024, c->device, gram_panel_kernel<T, 1024>, int(psm)));
                 else KRR_CUDA(raise_smem_limit(lim256, c->device, gram_panel_kernel<T, 256>, int(psm)));
             }
+            // the trailing updates of every panel, uploaded once; a node that
+            // has finished skips its updates on the device (its done flag)
+            GemmSeq<T> pseq;
+            for (int j0 = 0; j0 + kPanel < jmax; j0 += kPanel) {
+                GemmBatch<T> gt;
+                for (int a = 0; a < nn; ++a) {
+                    const NodeDesc &N = lvdesc[a];
+                    if (N.m <= j0) continue;  // rank at most m: finished by then
+                    const T *Lp = F + N.w + int64_t(j0) * N.m;
+                    gt.add(N.m, N.m, kPanel, T(-1), Lp, N.m, true, Lp, N.m, false, T(1), F + N.drr, N.m);
+                    gt.v.back().skip = &gs.get()[a].done;
+                }
+                pseq.add_step(gt);
+            }
+            KRR_TRY(pseq.upload(c));
             for (int j0 = 0, np = 0; j0 < jmax; j0 += kPanel, ++np) {
                 if (wide) { gram_panel_kernel<T, 1024><<<nn, 1024, psm, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid)), ldl); ::krr::count_launch(); }
                 else { gram_panel_kernel<T, 256><<<nn, 256, psm, c->stream>>>(dl.get(), F, H->IA.get(), gs.get(), j0, rid, kmax, T(H->opt.eps_c), T(H->opt.eps_abs), T(H->r11_cap(rid)), ldl); ::krr::count_launch(); }
                 KRR_CUDA(cudaGetLastError());
                 if (j0 + kPanel >= jmax) break;
-                // the host reads which nodes finished every fourth panel only;
-                // in between, the update of a node that finished is skipped on
-                // the device (its done flag)
+                // the host reads which nodes finished every fourth panel only
                 if (np % 4 == 3) {
                     KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
                                              c->stream));
                     KRR_CUDA(cudaStreamSynchronize(c->stream));
-                    for (int a = 0; a < nn; ++a) live[a] = !hs[a].done;
+                    bool any = false;
+                    for (int a = 0; a < nn; ++a) any = any || !hs[a].done;
+                    if (!any) break;
                 }
                 // update of the nodes still running: G -= L_p L_p^T (L_p: m x kPanel, column-major)
-                GemmBatch<T> gt;
-                for (int a = 0; a < nn; ++a) {
-                    const NodeDesc &N = lvdesc[a];
-                    if (!live[a] || N.m <= 0) continue;
-                    const T *Lp = F + N.w + int64_t(j0) * N.m;
-                    gt.add(N.m, N.m, kPanel, T(-1), Lp, N.m, true, Lp, N.m, false, T(1), F + N.drr, N.m);
-                    gt.v.back().skip = &gs.get()[a].done;
-                }
-                if (gt.v.empty()) break;
-                KRR_TRY(gt.launch(c));
+                KRR_TRY(pseq.launch(c, np));
             }
             tr.mark("id_panels", h, nn, mmax);
             KRR_CUDA(cudaMemcpyAsync(hs.data(), gs.get(), nn * sizeof(GramState<T>), cudaMemcpyDeviceToHost,
@@ -1672,11 +1677,10 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
                 nrmx = std::max(nrmx, lvdesc[a].m - hs[a].k);
             }
             const unsigned tcb = unsigned(std::max<int64_t>(1, cdiv(nrmx, kTrsmCols)));
-            for (int a1 = int(round_up(kmx, kTrsmBlock)); a1 > 0; a1 -= kTrsmBlock) {
+            // the update products of every block step, uploaded once
+            GemmSeq<T> useq;
+            for (int a1 = int(round_up(kmx, kTrsmBlock)); a1 > kTrsmBlock; a1 -= kTrsmBlock) {
                 const int a0 = a1 - kTrsmBlock;
-                { gram_trsm_diag_kernel<T><<<dim3(nn, tcb), kTrsmCols, 0, c->stream>>>(dl.get(), gs.get(), F, a0, a1); ::krr::count_launch(); }
-                KRR_CUDA(cudaGetLastError());
-                if (a0 == 0) break;
                 // rows [0, a0) of T -= (L(a0:a1, 0:a0))^T T(a0:a1, :)
                 GemmBatch<T> gu;
                 for (int a = 0; a < nn; ++a) {
@@ -1687,7 +1691,16 @@ int id_sweep(HssImpl *H, bool &need_more, bool keep_going = false) {
                     gu.add(a0, nr, hi - a0, T(-1), F + N.dmat + int64_t(a0) * k, k, true,
                            F + N.tmat + int64_t(a0) * nr, nr, false, T(1), F + N.tmat, nr);
                 }
-                KRR_TRY(gu.launch(c));
+                useq.add_step(gu);
+            }
+            KRR_TRY(useq.upload(c));
+            int step = 0;
+            for (int a1 = int(round_up(kmx, kTrsmBlock)); a1 > 0; a1 -= kTrsmBlock, ++step) {
+                const int a0 = a1 - kTrsmBlock;
+                { gram_trsm_diag_kernel<T><<<dim3(nn, tcb), kTrsmCols, 0, c->stream>>>(dl.get(), gs.get(), F, a0, a1); ::krr::count_launch(); }
+                KRR_CUDA(cudaGetLastError());
+                if (a0 == 0) break;
+                KRR_TRY(useq.launch(c, step));
             }
             tr.mark("id_trsm", h, nn, mmax);
             if (wide) { gram_test_kernel<T, 1024><<<nn, 1024, 0, c->stream>>>(dl.get(), gs.get(), S, H->r_cap, r, F, H->IA.get(), dranks.get(), derr.get()); ::krr::count_launch(); }

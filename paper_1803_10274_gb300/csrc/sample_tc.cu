@@ -169,8 +169,11 @@ __device__ __forceinline__ void tile_mask(const Params &P, int rt, int ct, int g
 
 // Add this warpgroup's half of the row-tile accumulator into S and hand
 // the tensor-memory buffer back to the MMA issuer.
+// A segment that covers its row tile's whole column range is the only
+// contribution to those rows of S (zeroed before the launch): plain stores,
+// no read-modify-write.
 __device__ __forceinline__ void flush_s(const Params &P, uint64_t *bars, volatile int *abort_flag, uint32_t tmem,
-                                     uint32_t lane_off, int64_t seg, int g, int rh, int64_t i) {
+                                     uint32_t lane_off, int64_t seg, int g, int rh, int64_t i, bool whole) {
     using namespace ptx;
     const int lane = threadIdx.x & 31;
     const int sb = P.s_bufs == 2 ? int(seg & 1) : 0;
@@ -185,8 +188,13 @@ __device__ __forceinline__ void flush_s(const Params &P, uint64_t *bars, volatil
             float *dst = P.S + i * P.lds;
             const int cbase = g * rh + cc;
             const int cend = min(32, rh - cc);  // r = 32: each half is 16 columns
-            for (int c = 0; c < cend; ++c)
-                if (cbase + c < P.r_valid) atomicAdd(dst + cbase + c, __uint_as_float(sv[c]));
+            if (whole) {
+                for (int c = 0; c < cend; ++c)
+                    if (cbase + c < P.r_valid) dst[cbase + c] = __uint_as_float(sv[c]);
+            } else {
+                for (int c = 0; c < cend; ++c)
+                    if (cbase + c < P.r_valid) atomicAdd(dst + cbase + c, __uint_as_float(sv[c]));
+            }
         }
     }
     tc_fence_before();
@@ -584,9 +592,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             tmem_ld32(tmem + lane_off + uint32_t(P.dist_col0 + 64 * g), va);
         }
+        bool seg_whole = false;  // the current segment began at its row tile's first column tile
         for (; ok && c.loc < nloc; c.next(P, nloc, 1, ND)) {
             c.flags(nloc);
-            if (c.first) ++c.seg;
+            if (c.first) {
+                ++c.seg;
+                seg_whole = c.ct == c.lo;
+            }
             const uint32_t base = tmem + lane_off + uint32_t(P.dist_col0 + c.db * kBN + 64 * g);
             const int rt = row_tile(c.rt);
             const int64_t i = int64_t(rt) * kBM + 32 * q + lane;
@@ -633,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld32(tmem + lane_off + uint32_t(P.dist_col0 + nd * kBN + 64 * g), va);
                 }
             }
-            if (c.last) flush_s(P, bars, abort_flag, tmem, lane_off, c.seg - 1, g, rh, i);
+            if (c.last) flush_s(P, bars, abort_flag, tmem, lane_off, c.seg - 1, g, rh, i, seg_whole && c.ct == c.hi);
         }
         tmem_wait_ld();
     }
