@@ -2395,7 +2395,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
         // iteration); Gram-Schmidt runs twice (CGS2).  Restarts recompute
         // the true residual with the precise (split-K) fused product.
         const int mres = 30;
-        constexpr double kRelaxSwitch = 0.1 * 2048.0;  // 0.1 / 2^-11
+        constexpr double kRelaxSwitch = 0.03 * 2048.0;  // 0.03 / 2^-11
         const int64_t nn = n * nrhs;
         // dots: the two Gram-Schmidt passes' coefficients (mres + 1 rows of
         // nrhs each) and the new vector's squared norms, read back together
@@ -2458,7 +2458,7 @@ int solve_perm(HssImpl *H, const double *yp, int nrhs, double *ap, double tol, i
                 // Relaxed inner products (inexact Krylov): once the estimated
                 // residual est is small, an operator error of eta est is
                 // allowed with eta ~ tol / est; K rounded to FP16 (2^-11 per
-                // entry) is used where 2^-11 <= 0.1 tol / est.  Restarts and
+                // entry) is used where 2^-11 <= 0.03 tol / est.  Restarts and
                 // the final check use the precise product.
                 const bool precise = est > kRelaxSwitch * tol;
                 KRR_TRY(hss_apply(H, H->Xp32.get(), H->XA.get(), n, Zv.get(), nrhs, nrhs, Wv.get(), nrhs, H->lambda,
