@@ -248,24 +248,36 @@ def krr_random_block(ctx, n, r, col0, seed, precision=KRR_MIXED, device=None):
     return out
 
 
+def check_gemm_args(A, B, C, ta, tb, cuda=True):
+    """Shapes of a batched product C[b] = op(A[b]) op(B[b]): A (batch, M, K)
+    or (batch, K, M) with ta, B (batch, K, N) or (batch, N, K) with tb, C
+    None or (batch, M, N); every tensor 3-D, contiguous float32 (CUDA when
+    cuda).  Returns (batch, M, N, K); raises ValueError otherwise."""
+    for t, name in ((A, "A"), (B, "B"), (C, "C")):
+        if t is None and name == "C":
+            continue
+        if t.dim() != 3 or t.dtype != torch.float32 or (cuda and not t.is_cuda):
+            raise ValueError("%s must be a 3-D %sfloat32 tensor" % (name, "CUDA " if cuda else ""))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    batch = A.shape[0]
+    M, K = (A.shape[2], A.shape[1]) if ta else (A.shape[1], A.shape[2])
+    KB, N = (B.shape[2], B.shape[1]) if tb else (B.shape[1], B.shape[2])
+    if B.shape[0] != batch or KB != K:
+        raise ValueError("krr_gemm_f32_batched: A and B do not conform")
+    if C is not None and tuple(C.shape) != (batch, M, N):
+        raise ValueError("krr_gemm_f32_batched: C must be (batch, M, N)")
+    return batch, M, N, K
+
+
 def krr_gemm_f32_batched(ctx, A, B, C=None, alpha=1.0, beta=0.0, ta=False, tb=False, path=0):
     """C[b] = alpha op(A[b]) op(B[b]) + beta C[b] for 3-D contiguous float32
     CUDA tensors: A (batch, M, K), or (batch, K, M) with ta; B (batch, K, N),
     or (batch, N, K) with tb; C (batch, M, N), allocated when None.  path: 0
     library's choice, 1 tensor cores (three TF32 products), 2 CUDA cores."""
-    _need(A, torch.float32, "A", dims=3)
-    _need(B, torch.float32, "B", dims=3)
-    A, B = A.contiguous(), B.contiguous()
-    batch = A.shape[0]
-    M, K = (A.shape[2], A.shape[1]) if ta else (A.shape[1], A.shape[2])
-    N = B.shape[1] if tb else B.shape[2]
-    if (B.shape[2] if tb else B.shape[1]) != K or B.shape[0] != batch:
-        raise ValueError("krr_gemm_f32_batched: A and B do not conform")
+    batch, M, N, K = check_gemm_args(A, B, C, ta, tb)
     if C is None:
         C = torch.zeros(batch, M, N, dtype=torch.float32, device=A.device)
-    _need(C, torch.float32, "C", dims=3)
-    if tuple(C.shape) != (batch, M, N) or not C.is_contiguous():
-        raise ValueError("krr_gemm_f32_batched: C must be a contiguous (batch, M, N) tensor")
     check(lib().krr_gemm_f32_batched(ctx.h, batch, M, N, K, float(alpha), _ptr(A), A.shape[2], A.stride(0),
                                      int(bool(ta)), _ptr(B), B.shape[2], B.stride(0), int(bool(tb)), float(beta),
                                      _ptr(C), N, C.stride(0), int(path)))

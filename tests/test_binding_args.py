@@ -107,3 +107,32 @@ def test_device_checked_by_default():
     a = _ok()
     with pytest.raises(ValueError, match="CUDA"):
         check_sample_args(a["Xa"], a["Xb"], a["R"], a["S"], None, None, torch.float32)
+
+
+# ------------------------------------------------ krr_gemm_f32_batched
+from paper_1803_10274_gb300.binding import check_gemm_args  # noqa: E402
+
+
+def test_gemm_shapes_and_transposes():
+    A, B, C = torch.zeros(2, 5, 7), torch.zeros(2, 7, 3), torch.zeros(2, 5, 3)
+    assert check_gemm_args(A, B, C, False, False, cuda=False) == (2, 5, 3, 7)
+    assert check_gemm_args(A.transpose(1, 2).contiguous(), B, None, True, False, cuda=False) == (2, 5, 3, 7)
+    assert check_gemm_args(A, B.transpose(1, 2).contiguous(), C, False, True, cuda=False) == (2, 5, 3, 7)
+
+
+@pytest.mark.parametrize("A,B,C", [
+    (torch.zeros(2, 5, 7), torch.zeros(2, 6, 3), None),                  # inner dimensions differ
+    (torch.zeros(2, 5, 7), torch.zeros(3, 7, 3), None),                  # batches differ
+    (torch.zeros(2, 5, 7), torch.zeros(2, 7, 3), torch.zeros(2, 5, 4)),  # wrong C
+    (torch.zeros(2, 5, 7, dtype=torch.float64), torch.zeros(2, 7, 3), None),
+    (torch.zeros(5, 7), torch.zeros(7, 3), None),                        # 2-D, not batched
+    (torch.zeros(2, 7, 5).transpose(1, 2), torch.zeros(2, 7, 3), None),  # not contiguous
+])
+def test_gemm_rejections(A, B, C):
+    with pytest.raises(ValueError):
+        check_gemm_args(A, B, C, False, False, cuda=False)
+
+
+def test_gemm_needs_cuda_tensors():
+    with pytest.raises(ValueError):
+        check_gemm_args(torch.zeros(1, 2, 2), torch.zeros(1, 2, 2), None, False, False, cuda=True)
