@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -44,6 +45,9 @@ constexpr int kMaxIter = 100;
 constexpr int kMaxD = 1024;  // feature dimensions the node state holds
 constexpr int kTB = 256;
 constexpr int kWarpDim = 64;  // from this dimension on, a warp computes one point's distances
+// Coordinates per lane of the wide-row kernels (JS): the smallest of 4, 8,
+// 16, 32 with 32 JS >= d.
+inline int wide_slots(int d) { return d <= 128 ? 4 : d <= 256 ? 8 : d <= 512 ? 16 : 32; }
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {  // b > 0
     return a >= 0 ? a / b : -((-a + b - 1) / b);
@@ -202,11 +206,170 @@ __global__ void seed_kernel(const int64_t *q, int d, const int64_t *nbeg, const 
     }
 }
 
+// seed_kernel for wide rows (d >= kWarpDim), in three launches so that all
+// SMs share the distance pass (the one-block-per-node kernel leaves the
+// top levels' work to a few SMs):
+//   seed_first_wide_kernel   per node: the first representative (same draw)
+//                            into c0, sums cleared, total cleared;
+//   seed_dist_wide_kernel    per row: squared distance to c0 (a warp per
+//                            row, lanes over the coordinates) into dist,
+//                            summed into the node's total;
+//   seed_second_wide_kernel  per node: the same second draw over the
+//                            inclusive prefix sums of dist in row order.
+// The distances, total and target are the same integers as in seed_kernel.
+__global__ void seed_first_wide_kernel(const int64_t *q, int d, const int64_t *nbeg, const int64_t *nsize,
+                                       const int64_t *nbase, NodeState *ns, uint64_t seed,
+                                       unsigned long long *tot) {
+    const int v = blockIdx.x;
+    const int64_t b = nbeg[v], m = nsize[v];
+    NodeState &S = ns[v];
+    const U64x4 w = philox4x64_10(uint64_t(b - nbase[v]), uint64_t(m), 0, 0, seed, kStreamCluster);
+    const int64_t first = b + int64_t(__umul64hi(w.v[0], uint64_t(m)));
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        S.c0[k] = q[first * d + k];
+        S.sum0[k] = S.sum1[k] = 0;
+    }
+    if (threadIdx.x == 0) tot[v] = 0ull;
+}
+
+template <int JS>
+__global__ void __launch_bounds__(kTB) seed_dist_wide_kernel(const int64_t *q, int d, int64_t n,
+                                                             const int32_t *node_of, const NodeState *ns,
+                                                             unsigned long long *dist, unsigned long long *tot,
+                                                             bool narrow) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wbase = int64_t(blockIdx.x) * kTB + (threadIdx.x & ~31);
+    int32_t cur = -1;
+    unsigned long long part = 0;  // the warp's running total for node cur
+#pragma unroll 1
+    for (int pl = 0; pl < 32; ++pl) {
+        const int64_t ip = wbase + pl;
+        const int32_t vp = ip < n ? node_of[ip] : -1;  // the same for every lane
+        if (vp < 0) continue;
+        if (vp != cur) {
+            if (cur >= 0 && lane == 0 && part) atomicAdd(&tot[cur], part);
+            cur = vp;
+            part = 0;
+        }
+        const int64_t *row = q + ip * d;
+        const int64_t *c0 = ns[vp].c0;
+        int64_t x[JS];
+#pragma unroll
+        for (int j = 0; j < JS; ++j) {
+            const int k = lane + 32 * j;
+            int64_t xv = 0;
+            if (k < d) xv = row[k];
+            x[j] = xv;
+        }
+        long long s = 0;
+#pragma unroll
+        for (int j = 0; j < JS; ++j) {
+            const int k = lane + 32 * j;
+            if (k < d) s += sq_diff(x[j], c0[k], narrow);
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) dist[ip] = (unsigned long long)s;
+        part += (unsigned long long)s;
+    }
+    if (cur >= 0 && lane == 0 && part) atomicAdd(&tot[cur], part);
+}
+
+constexpr int kScanPer = 4;  // rows per thread in one step of the second draw's scan
+
+__global__ void seed_second_wide_kernel(const int64_t *q, int d, const int64_t *nbeg, const int64_t *nsize,
+                                        const int64_t *nbase, NodeState *ns, uint64_t seed,
+                                        const unsigned long long *dist, const unsigned long long *tot) {
+    const int v = blockIdx.x;
+    const int64_t b = nbeg[v], m = nsize[v];
+    NodeState &S = ns[v];
+    __shared__ unsigned long long warp_tot[kTB / 32];
+    __shared__ int64_t s_second;
+    const unsigned long long total = tot[v];
+    if (total == 0) {  // all points identical: halves
+        if (threadIdx.x == 0) {
+            S.done = 1;
+            S.halved = 1;
+            S.it = 0;
+            S.first = 0;
+        }
+        return;
+    }
+    const U64x4 w = philox4x64_10(uint64_t(b - nbase[v]), uint64_t(m), 0, 0, seed, kStreamCluster);
+    const unsigned long long target = __umul64hi(w.v[1], total);
+    if (threadIdx.x == 0) s_second = -1;
+    // the first row whose inclusive prefix sum exceeds target: kTB x kScanPer
+    // rows per step, each thread's rows consecutive
+    unsigned long long carry = 0;
+    for (int64_t base = b; base < b + m; base += int64_t(kTB) * kScanPer) {
+        const int64_t r0 = base + int64_t(threadIdx.x) * kScanPer;
+        unsigned long long dv[kScanPer], own = 0;
+#pragma unroll
+        for (int u = 0; u < kScanPer; ++u) {
+            dv[u] = r0 + u < b + m ? dist[r0 + u] : 0ull;
+            own += dv[u];
+        }
+        unsigned long long x = own;  // inclusive scan of the threads' sums
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+        __syncthreads();
+        unsigned long long wpre = 0;
+        for (int k = 0; k < (threadIdx.x >> 5); ++k) wpre += warp_tot[k];
+        unsigned long long incl = carry + wpre + x - own;  // before this thread's rows
+#pragma unroll
+        for (int u = 0; u < kScanPer; ++u) {
+            incl += dv[u];
+            if (r0 + u < b + m && incl > target && incl - dv[u] <= target) s_second = r0 + u;
+        }
+        unsigned long long btot = 0;
+        for (int k = 0; k < kTB / 32; ++k) btot += warp_tot[k];
+        carry += btot;
+        __syncthreads();
+    }
+    const int64_t sec = s_second;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) S.c1[k] = q[sec * d + k];
+    if (threadIdx.x == 0) {
+        S.cnt1 = 0;
+        S.it = 0;
+        S.done = 0;
+        S.changed = 0;
+        S.halved = 0;
+        S.first = 1;
+    }
+}
+
+template <int JS>
+int launch_seed_dist_t(Ctx *c, unsigned grid, const int64_t *q, int d, int64_t n, const int32_t *node_of,
+                       const NodeState *ns, unsigned long long *dist, unsigned long long *tot, bool narrow) {
+    { seed_dist_wide_kernel<JS><<<grid, kTB, 0, c->stream>>>(q, d, n, node_of, ns, dist, tot, narrow); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
+int launch_seed_wide(Ctx *c, int nn, unsigned grid, const int64_t *q, int d, int64_t n, const int64_t *nbeg,
+                     const int64_t *nsize, const int64_t *nbase, const int32_t *node_of, NodeState *ns,
+                     uint64_t seed, unsigned long long *dist, unsigned long long *tot, bool narrow) {
+    { seed_first_wide_kernel<<<nn, kTB, 0, c->stream>>>(q, d, nbeg, nsize, nbase, ns, seed, tot); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    switch (wide_slots(d)) {
+        case 4: KRR_TRY(launch_seed_dist_t<4>(c, grid, q, d, n, node_of, ns, dist, tot, narrow)); break;
+        case 8: KRR_TRY(launch_seed_dist_t<8>(c, grid, q, d, n, node_of, ns, dist, tot, narrow)); break;
+        case 16: KRR_TRY(launch_seed_dist_t<16>(c, grid, q, d, n, node_of, ns, dist, tot, narrow)); break;
+        default: KRR_TRY(launch_seed_dist_t<32>(c, grid, q, d, n, node_of, ns, dist, tot, narrow)); break;
+    }
+    { seed_second_wide_kernel<<<nn, kTB, 0, c->stream>>>(q, d, nbeg, nsize, nbase, ns, seed, dist, tot); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
 // Assign each point of a still-running node to its nearer centre and
-// accumulate the new groups' sums and counts.  When a block's points all
-// belong to one node, the sums are gathered per coordinate in shared
-// memory (int64 atomics, exact and order-free) and added to the node once
-// per coordinate; dynamic shared memory: 2 d int64.
+// accumulate the new groups' sums and counts (narrow rows, d < kWarpDim:
+// one thread per point).  When a block's points all belong to one node,
+// the sums are gathered per coordinate in shared memory (int64 atomics,
+// exact and order-free) and added to the node once per coordinate; dynamic
+// shared memory: 2 d int64.
 __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t *node_of, NodeState *ns,
                               int8_t *label, bool narrow) {
     extern __shared__ unsigned long long s_sum[];  // [2][d]
@@ -227,29 +390,7 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
     const bool uniform = s_uniform != 0;
     bool active = v >= 0 && !ns[v].done;
     int lab = 0;
-    if (d >= kWarpDim) {
-        // wide rows: the warp computes its 32 points' distances one point
-        // at a time, lanes striding over the coordinates (coalesced)
-        const int lane = threadIdx.x & 31;
-        const int64_t wbase = i0 + (threadIdx.x & ~31);
-        for (int pl = 0; pl < 32; ++pl) {
-            const int64_t ip = wbase + pl;
-            const int32_t vp = ip < n ? node_of[ip] : -1;  // the same for every lane
-            if (vp < 0 || ns[vp].done) continue;
-            const NodeState &S = ns[vp];
-            long long d0 = 0, d1 = 0;
-            for (int k = lane; k < d; k += 32) {
-                const int64_t x = q[ip * d + k];
-                d0 += sq_diff(x, S.c0[k], narrow);
-                d1 += sq_diff(x, S.c1[k], narrow);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-            }
-            if (lane == pl) lab = d0 > d1 ? 1 : 0;
-        }
-    } else if (active) {
+    if (active) {
         const NodeState &S = ns[v];
         int64_t d0 = 0, d1 = 0;
         for (int k = 0; k < d; ++k) {
@@ -289,6 +430,144 @@ __global__ void assign_kernel(const int64_t *q, int d, int64_t n, const int32_t 
         for (int k = 0; k < d; ++k)
             atomicAdd(reinterpret_cast<unsigned long long *>(&sum[k]), (unsigned long long)q[i * d + k]);
     }
+}
+
+// assign_kernel for wide rows (d >= kWarpDim, d <= 32 JS).  A block takes
+// kWideRows consecutive points, each of its warps kWidePts of them one at
+// a time, lanes over the coordinates.  Every coordinate of the point is
+// loaded at once into registers (JS per lane, so the loads are all in
+// flight together; as 32-bit words when NARROW: |q| <= 2^29 there, so the
+// low word of the int64 is the value), the two distances are reduced
+// across the warp, and the same registers are then added into the sums of
+// the point's group: in shared memory ([2][d] int64, atomics) when the
+// block's points are all one node, then one add per coordinate into the
+// node; directly into the node's sums otherwise.  Each coordinate is read
+// once per pass; integer sums, so the result is the same for any order.
+// Dynamic shared memory: 2 d int64.
+constexpr int kWidePts = 16;                           // points per warp
+constexpr int kWideRows = (kTB / 32) * kWidePts;       // points per block
+
+template <int JS, bool NARROW>
+__global__ void __launch_bounds__(kTB) assign_wide_kernel(const int64_t *q, int d, int64_t n,
+                                                          const int32_t *node_of, NodeState *ns, int8_t *label) {
+    extern __shared__ unsigned long long s_acc[];  // [2][d]
+    __shared__ int s_uniform;
+    __shared__ int32_t s_node;
+    __shared__ unsigned long long s_c1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = int64_t(blockIdx.x) * kWideRows;
+    if (threadIdx.x == 0) {
+        const int32_t v0 = i0 < n ? node_of[i0] : -1;
+        const int64_t last = min(i0 + kWideRows - 1, n - 1);
+        s_node = v0;
+        s_uniform = (v0 >= 0 && node_of[last] == v0) ? 1 : 0;
+        s_c1 = 0ull;
+    }
+    for (int k = threadIdx.x; k < 2 * d; k += kTB) s_acc[k] = 0ull;
+    __syncthreads();
+    const bool uniform = s_uniform != 0;
+    if (uniform && ns[s_node].done) return;  // the whole block agrees: no thread reaches the barrier below
+    using W = typename std::conditional<NARROW, int32_t, int64_t>::type;
+    const W *qw = reinterpret_cast<const W *>(q);
+    constexpr int kStride = NARROW ? 2 : 1;  // W words per coordinate
+    unsigned long long c1 = 0;               // group-1 points of this warp (uniform blocks)
+    const int64_t wbase = i0 + int64_t(warp) * kWidePts;
+#pragma unroll 1
+    for (int pl = 0; pl < kWidePts; ++pl) {
+        const int64_t ip = wbase + pl;
+        const int32_t vp = ip < n ? node_of[ip] : -1;  // the same for every lane
+        if (vp < 0 || ns[vp].done) continue;
+        NodeState &S = ns[vp];
+        const W *row = qw + ip * d * kStride;
+        W x[JS];
+#pragma unroll
+        for (int j = 0; j < JS; ++j) {
+            const int k = lane + 32 * j;
+            W xv = 0;
+            if (k < d) xv = row[int64_t(k) * kStride];
+            x[j] = xv;
+        }
+        long long d0 = 0, d1 = 0;
+#pragma unroll
+        for (int j = 0; j < JS; ++j) {
+            const int k = lane + 32 * j;
+            if (k < d) {
+                if (NARROW) {
+                    const int32_t a0 = int32_t(x[j]) - int32_t(S.c0[k]), a1 = int32_t(x[j]) - int32_t(S.c1[k]);
+                    d0 += (long long)a0 * a0;
+                    d1 += (long long)a1 * a1;
+                } else {
+                    const int64_t a0 = int64_t(x[j]) - S.c0[k], a1 = int64_t(x[j]) - S.c1[k];
+                    d0 += a0 * a0;
+                    d1 += a1 * a1;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        }
+        const int lab = d0 > d1 ? 1 : 0;  // the same for every lane
+        if (lane == 0) {
+            if (S.first || label[ip] != lab) S.changed = 1;
+            label[ip] = int8_t(lab);
+        }
+        if (uniform) {
+            c1 += unsigned(lab);
+            unsigned long long *a = s_acc + (lab ? d : 0);
+#pragma unroll
+            for (int j = 0; j < JS; ++j) {
+                const int k = lane + 32 * j;
+                if (k < d) atomicAdd(a + k, (unsigned long long)(long long)x[j]);
+            }
+        } else {
+            int64_t *sum = lab ? S.sum1 : S.sum0;
+#pragma unroll
+            for (int j = 0; j < JS; ++j) {
+                const int k = lane + 32 * j;
+                if (k < d) atomicAdd(reinterpret_cast<unsigned long long *>(sum + k), (unsigned long long)(long long)x[j]);
+            }
+            if (lane == 0 && lab) atomicAdd(&S.cnt1, 1ull);
+        }
+    }
+    if (uniform) {
+        if (lane == 0 && c1) atomicAdd(&s_c1, c1);
+        __syncthreads();  // the block's sums are complete
+        NodeState &S = ns[s_node];
+        for (int k = threadIdx.x; k < 2 * d; k += kTB) {
+            const unsigned long long t = s_acc[k];
+            int64_t *dst = k < d ? &S.sum0[k] : &S.sum1[k - d];
+            if (t) atomicAdd(reinterpret_cast<unsigned long long *>(dst), t);
+        }
+        if (threadIdx.x == 0 && s_c1) atomicAdd(&S.cnt1, s_c1);
+    }
+}
+
+template <int JS, bool NARROW>
+int launch_assign_wide_t(Ctx *c, const int64_t *q, int d, int64_t n, const int32_t *node_of, NodeState *ns,
+                         int8_t *label) {
+    const int bytes = 2 * d * int(sizeof(unsigned long long));  // <= 16 KB (d <= 1024)
+    const unsigned grid = unsigned(cdiv(n, kWideRows));
+    { assign_wide_kernel<JS, NARROW><<<grid, kTB, bytes, c->stream>>>(q, d, n, node_of, ns, label); ::krr::count_launch(); }
+    KRR_CUDA(cudaGetLastError());
+    return KRR_OK;
+}
+
+template <bool NARROW>
+int launch_assign_wide_n(Ctx *c, const int64_t *q, int d, int64_t n, const int32_t *node_of, NodeState *ns,
+                         int8_t *label) {
+    switch (wide_slots(d)) {
+        case 4: return launch_assign_wide_t<4, NARROW>(c, q, d, n, node_of, ns, label);
+        case 8: return launch_assign_wide_t<8, NARROW>(c, q, d, n, node_of, ns, label);
+        case 16: return launch_assign_wide_t<16, NARROW>(c, q, d, n, node_of, ns, label);
+        default: return launch_assign_wide_t<32, NARROW>(c, q, d, n, node_of, ns, label);
+    }
+}
+
+int launch_assign_wide(Ctx *c, const int64_t *q, int d, int64_t n, const int32_t *node_of, NodeState *ns,
+                       int8_t *label, bool narrow) {
+    return narrow ? launch_assign_wide_n<true>(c, q, d, n, node_of, ns, label)
+                  : launch_assign_wide_n<false>(c, q, d, n, node_of, ns, label);
 }
 
 // One CTA per node: stop test, centre update (threads over the
@@ -417,6 +696,30 @@ __global__ void partition_kernel(int64_t n, int d, const int32_t *node_of, const
     }
     for (int k = 0; k < d; ++k) q2[dst * d + k] = q[i * d + k];
     perm2[dst] = perm[i];
+}
+
+// partition_kernel for wide rows (d >= kWarpDim): one warp per row, lanes
+// over the coordinates, so each row moves in coalesced 256-byte pieces.
+__global__ void partition_wide_kernel(int64_t n, int d, const int32_t *node_of, const int64_t *nbeg,
+                                      const int64_t *nsize, const int8_t *label, const int64_t *zscan,
+                                      const int32_t *zflag, const int64_t *q, const int32_t *perm, int64_t *q2,
+                                      int32_t *perm2, int64_t *cnt0_out) {
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;  // the same for the whole warp
+    const int32_t v = node_of[i];
+    int64_t dst = i;
+    if (v >= 0) {
+        const int64_t b = nbeg[v];
+        const int64_t zb = zscan[b];
+        const int64_t last = b + nsize[v] - 1;
+        const int64_t c0 = zscan[last] + zflag[last] - zb;
+        const int64_t zi = zscan[i] - zb;
+        dst = label[i] == 0 ? b + zi : b + c0 + (i - b - zi);
+        if (i == b && lane == 0) cnt0_out[v] = c0;
+    }
+    for (int k = lane; k < d; k += 32) q2[dst * d + k] = q[i * d + k];
+    if (lane == 0) perm2[dst] = perm[i];
 }
 
 __global__ void mark_nodes_kernel(int nn, const int64_t *nbeg, const int64_t *nsize, int32_t *node_of) {
@@ -808,6 +1111,9 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
     cudaEvent_t *iter_ev = isync.ev;
     DBuf<int32_t> eqflag;
     if (method == KRR_ORDER_KD && !eqflag.reset(c, n)) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+    DBuf<unsigned long long> sdist;  // wide rows: squared distance of each row to its node's first seed
+    if (method == KRR_ORDER_TWO_MEANS && d >= kWarpDim && !sdist.reset(c, n))
+        return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
     while (!active.empty()) {
         const int nn = int(active.size());
         std::vector<int64_t> hb(nn), hs(nn), hbase(nn);
@@ -828,7 +1134,14 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         const int64_t nblk = cdiv(n, kTB);
         const unsigned gn = unsigned(cdiv(n, kTB)), gv = unsigned(cdiv(nn, 128));
         if (method == KRR_ORDER_TWO_MEANS) {
-            { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed, narrow); ::krr::count_launch(); }
+            if (d >= kWarpDim) {
+                DBuf<unsigned long long> stot(c, nn);
+                if (!stot.get()) return fail(KRR_ERR_OOM, "krr_cluster: out of memory");
+                KRR_TRY(launch_seed_wide(c, nn, gn, qc, d, n, db.get(), ds.get(), dbase.get(), node_of.get(), dns.get(),
+                                         seed, sdist.get(), stot.get(), narrow));
+            } else {
+                { seed_kernel<<<nn, kTB, 0, st>>>(qc, d, db.get(), ds.get(), dbase.get(), dns.get(), seed, narrow); ::krr::count_launch(); }
+            }
             KRR_CUDA(cudaGetLastError());
             // The count of nodes still running is read one iteration late:
             // iteration t + 1 is queued before the host waits for t's count
@@ -836,8 +1149,11 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
             for (int iter = 0; iter <= kMaxIter; ++iter) {
                 const int slot = iter & 1;
                 KRR_CUDA(cudaMemsetAsync(running.get() + slot, 0, 4, st));
-                { assign_kernel<<<gn, kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get(), narrow); ::krr::count_launch(); }
-                { update_kernel<<<nn, 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get() + slot); ::krr::count_launch(); }
+                if (d >= kWarpDim)
+                    KRR_TRY(launch_assign_wide(c, qc, d, n, node_of.get(), dns.get(), label.get(), narrow));
+                else
+                    { assign_kernel<<<gn, kTB, size_t(2) * d * sizeof(unsigned long long), st>>>(qc, d, n, node_of.get(), dns.get(), label.get(), narrow); ::krr::count_launch(); }
+                { update_kernel<<<nn, d >= kWarpDim ? kTB : 128, 0, st>>>(nn, d, ds.get(), dns.get(), running.get() + slot); ::krr::count_launch(); }
                 KRR_CUDA(cudaGetLastError());
                 KRR_CUDA(cudaMemcpyAsync(hrun_pin + slot, running.get() + slot, 4, cudaMemcpyDeviceToHost, st));
                 KRR_CUDA(cudaEventRecord(iter_ev[slot], st));
@@ -916,8 +1232,13 @@ int cluster(Ctx *c, const float *X, int64_t n, int d, int leaf, uint64_t seed, i
         { scan_blocks_kernel<<<unsigned(nblk), kTB, 0, st>>>(zflag.get(), n, zscan.get(), bsum.get()); ::krr::count_launch(); }
         { scan_sums_kernel<<<1, kTB, 0, st>>>(bsum.get(), nblk); ::krr::count_launch(); }
         { scan_add_kernel<<<unsigned(nblk), kTB, 0, st>>>(zscan.get(), n, bsum.get(), nullptr); ::krr::count_launch(); }
-        { partition_kernel<<<unsigned(nblk), kTB, 0, st>>>(n, d, node_of.get(), db.get(), ds.get(), label.get(),
-                                                          zscan.get(), zflag.get(), qc, pc, qn, pn, dcnt0.get()); ::krr::count_launch(); }
+        if (d >= kWarpDim)
+            { partition_wide_kernel<<<unsigned(cdiv(n * 32, kTB)), kTB, 0, st>>>(n, d, node_of.get(), db.get(), ds.get(),
+                                                                              label.get(), zscan.get(), zflag.get(), qc,
+                                                                              pc, qn, pn, dcnt0.get()); ::krr::count_launch(); }
+        else
+            { partition_kernel<<<unsigned(nblk), kTB, 0, st>>>(n, d, node_of.get(), db.get(), ds.get(), label.get(),
+                                                              zscan.get(), zflag.get(), qc, pc, qn, pn, dcnt0.get()); ::krr::count_launch(); }
         KRR_CUDA(cudaGetLastError());
         std::vector<int64_t> hc0(nn);
         KRR_CUDA(cudaMemcpyAsync(hc0.data(), dcnt0.get(), nn * 8, cudaMemcpyDeviceToHost, st));

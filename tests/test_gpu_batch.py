@@ -50,9 +50,10 @@ def _intervals(tree, lo, hi):
     return out
 
 
-def test_batched_clustering_is_each_problem_alone(K, ctx):
+@pytest.mark.parametrize("d", [8, 100])
+def test_batched_clustering_is_each_problem_alone(K, ctx, d):
     sizes, leaf, seed = [300, 1000, 130, 2047, 64, 700], 64, 7
-    Xs, *_ = _problems(sizes, 8, 40)
+    Xs, *_ = _problems(sizes, d, 40)
     off = _offsets(Xs)
     X = np.concatenate(Xs)
     perm, tree = K.krr_cluster_batched(ctx, torch.from_numpy(X).cuda(), off, leaf, seed)

@@ -47,6 +47,22 @@ def test_image_like_d784_bit_exact(K, ctx):
     """MNIST-shaped rows: d = 784, most coordinates exactly zero."""
     X = synth.image_like(1000, 3)[0].astype(np.float32)
     _check(K, ctx, X, 128, 4)
+    X = synth.image_like(3000, 5)[0].astype(np.float32)   # 12 blocks of 256 rows, leaf 256
+    _check(K, ctx, X, 256, 6)
+
+
+@pytest.mark.parametrize("n,d,comp,leaf,seed", [(2500, 64, 5, 100, 11),   # 4 coordinates per lane
+                                                (1700, 200, 6, 64, 12),    # 8
+                                                (1300, 300, 4, 128, 13),   # 16
+                                                (2100, 700, 5, 128, 14),   # 32, shared memory above 48 KB
+                                                (1100, 1024, 3, 64, 15)])  # the largest d
+def test_wide_rows_bit_exact(K, ctx, n, d, comp, leaf, seed):
+    """Rows of 64 or more coordinates (a warp per point, each coordinate
+    read once per Lloyd pass), ragged n: blocks of one node, blocks across
+    nodes, and partial last blocks."""
+    X, *_ = synth.mixture(n, d, comp, 0.7, seed)
+    Z, *_ = prep.standardize(X)
+    _check(K, ctx, Z.astype(np.float32), leaf, seed)
 
 
 def test_full_size_bit_exact(K, ctx):
