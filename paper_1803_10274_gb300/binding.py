@@ -267,6 +267,9 @@ def check_gemm_args(A, B, C, ta, tb, cuda=True):
         raise ValueError("krr_gemm_f32_batched: A and B do not conform")
     if C is not None and tuple(C.shape) != (batch, M, N):
         raise ValueError("krr_gemm_f32_batched: C must be (batch, M, N)")
+    tiles = batch * -(-M // 128) * -(-N // 128)
+    if max(batch, M, N, K, tiles) > 0x7FFFFFFF:
+        raise ValueError("krr_gemm_f32_batched: sizes or the count of 128 x 128 output tiles above 2^31 - 1")
     return batch, M, N, K
 
 

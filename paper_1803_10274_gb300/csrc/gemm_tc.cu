@@ -435,6 +435,9 @@ extern "C" int krr_gemm_f32_batched(krr_ctx *k, int32_t batch, int32_t M, int32_
         (tb != 0 && tb != 1))
         return fail(KRR_ERR_INVALID_ARG, "krr_gemm_f32_batched: bad arguments");
     if (batch == 0 || M == 0 || N == 0) return KRR_OK;
+    // output tiles are counted in int on both paths
+    if (int64_t(batch) * cdiv(M, gtc::kBM) * cdiv(N, gtc::kBN) > 0x7FFFFFFF)
+        return fail(KRR_ERR_INVALID_ARG, "krr_gemm_f32_batched: more than 2^31 - 1 output tiles");
     if (!C || ldc < N || (K > 0 && (!A || !B || lda < (ta ? M : K) || ldb < (tb ? K : N))))
         return fail(KRR_ERR_INVALID_ARG, "krr_gemm_f32_batched: bad pointer or leading dimension");
     Ctx *c = &k->c;

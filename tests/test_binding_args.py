@@ -136,3 +136,14 @@ def test_gemm_rejections(A, B, C):
 def test_gemm_needs_cuda_tensors():
     with pytest.raises(ValueError):
         check_gemm_args(torch.zeros(1, 2, 2), torch.zeros(1, 2, 2), None, False, False, cuda=True)
+
+
+def test_gemm_sizes_within_int32():
+    """Sizes and the count of 128 x 128 output tiles must fit the C ABI's
+    int32 (K = 0 keeps the operands empty)."""
+    with pytest.raises(ValueError):   # 2^17 x 2^17 tiles
+        check_gemm_args(torch.zeros(1, 1 << 24, 0), torch.zeros(1, 0, 1 << 24), None, False, False, cuda=False)
+    with pytest.raises(ValueError):   # M above 2^31 - 1
+        check_gemm_args(torch.zeros(1, 1 << 31, 0), torch.zeros(1, 0, 1), None, False, False, cuda=False)
+    assert check_gemm_args(torch.zeros(3, 1 << 12, 0), torch.zeros(3, 0, 1 << 12), None, False, False,
+                           cuda=False) == (3, 1 << 12, 1 << 12, 0)
