@@ -459,6 +459,31 @@ int krr_heldout_grad(krr_hss *H, const float *Xt, int64_t m, const double *y,
                      double *loss, double *dh, double *dlambda, double *dX,
                      int64_t lddx, double *alpha, double *resid);
 
+/* Block partition of an H matrix over a cluster tree (Section 3.2, the H
+ * matrix representation: only well-separated sub-blocks are compressed,
+ * strong admissibility).  Host only: needs no context and no GPU.
+ *   n_nodes, left, right  the tree in postorder (host int32[n_nodes]; the
+ *          root is n_nodes - 1; left[v] = right[v] = -1 for a leaf, else
+ *          both children have ids below v)
+ *   d, lo, hi  host double n_nodes x d (row-major): each node's bounding box
+ *   eta    admissibility parameter >= 0: (t, s) is admissible when the
+ *          boxes are apart and min(diam t, diam s) <= eta dist(t, s), with
+ *          diam the box diagonal and dist the distance between the boxes
+ *          (sums of squares in coordinate order, one square root)
+ *   near, far  host int32[2 cap_near], int32[2 cap_far]: node pairs (t, s)
+ *          of the dense and of the admissible blocks, in depth-first order
+ *          from (root, root), left child first (a pair that is neither is
+ *          split into its children's pairs: both nodes when both have
+ *          children, else the inner one)
+ *   n_near, n_far  out: numbers of pairs
+ * Returns KRR_ERR_INVALID_ARG for a bad tree or arguments, and when a list
+ * is longer than its capacity (counts still returned; nothing written past
+ * a capacity). */
+int krr_h_partition(int32_t n_nodes, const int32_t *left, const int32_t *right,
+                    int32_t d, const double *lo, const double *hi, double eta,
+                    int32_t *near, int64_t cap_near, int64_t *n_near,
+                    int32_t *far, int64_t cap_far, int64_t *n_far);
+
 typedef struct {
     int64_t n;
     int32_t n_nodes, n_levels, max_rank, samples, rounds, refine_steps;

@@ -62,6 +62,8 @@ SIGNATURES = {
     "krr_probe_rate": (i32, [P, i32, ctypes.POINTER(f64)]),
     "krr_gemm_f32_batched": (i32, [P, i32, i32, i32, i32, ctypes.c_float, P, i64, i64, i32, P, i64, i64, i32,
                                    ctypes.c_float, P, i64, i64, i32]),
+    "krr_h_partition": (i32, [i32, P, P, i32, P, P, f64, P, i64, ctypes.POINTER(i64), P, i64,
+                              ctypes.POINTER(i64)]),
     "krr_standardize": (i32, [P, P, i64, i32, P, i64, P, P]),
     "krr_cluster": (i32, [P, P, i64, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),
     "krr_order": (i32, [P, P, i64, i32, i32, i32, u64, P, i32, krr_tree_arrays, ctypes.POINTER(i32)]),

@@ -17,7 +17,7 @@ from ._lib import (KRR_FP64, KRR_LAMBDA_TOL, KRR_MIXED, KRR_MIXED_F64, KRR_ORDER
 
 __all__ = ["Context", "KRRError", "KRR_MIXED", "KRR_FP64", "KRR_MIXED_F64", "KRR_TRUNCATE_AT_RMAX", "KRR_LAMBDA_TOL", "KRR_ORDER_TWO_MEANS",
            "KRR_ORDER_NATURAL", "KRR_ORDER_KD", "KRR_ORDER_PCA", "krr_order", "krr_standardize", "krr_cluster", "krr_sample",
-           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "krr_one_vs_all", "krr_gemm_f32_batched", "HSS", "hss_compress", "default_options",
+           "krr_sample_f64", "krr_sample_noalloc", "krr_random_block", "krr_one_vs_all", "krr_gemm_f32_batched", "krr_h_partition", "HSS", "hss_compress", "default_options",
            "HeldOutLoss", "krr_heldout_loss", "krr_cluster_batched", "hss_compress_batched", "lib"]
 
 
@@ -285,6 +285,34 @@ def krr_gemm_f32_batched(ctx, A, B, C=None, alpha=1.0, beta=0.0, ta=False, tb=Fa
                                      int(bool(ta)), _ptr(B), B.shape[2], B.stride(0), int(bool(tb)), float(beta),
                                      _ptr(C), N, C.stride(0), int(path)))
     return C
+
+
+def krr_h_partition(left, right, lo, hi, eta):
+    """Near and far blocks of an H matrix over a postorder cluster tree
+    (host arrays: left / right int32[n_nodes], lo / hi float64
+    n_nodes x d); returns (near, far), int32 arrays of node pairs (k x 2)
+    in the library's depth-first order."""
+    import numpy as np
+    left = np.ascontiguousarray(left, dtype=np.int32)
+    right = np.ascontiguousarray(right, dtype=np.int32)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    nn = left.shape[0]
+    if left.ndim != 1 or right.shape != (nn,) or lo.ndim != 2 or lo.shape[0] != nn or hi.shape != lo.shape:
+        raise ValueError("krr_h_partition: left, right int32[n_nodes]; lo, hi float64 n_nodes x d")
+    cn, cf = 4 * nn, 4 * nn
+    while True:
+        near = np.empty((cn, 2), np.int32)
+        far = np.empty((cf, 2), np.int32)
+        n_near, n_far = ctypes.c_int64(0), ctypes.c_int64(0)
+        code = lib().krr_h_partition(nn, left.ctypes.data, right.ctypes.data, lo.shape[1], lo.ctypes.data,
+                                     hi.ctypes.data, float(eta), near.ctypes.data, cn, ctypes.byref(n_near),
+                                     far.ctypes.data, cf, ctypes.byref(n_far))
+        if code != 0 and (n_near.value > cn or n_far.value > cf):
+            cn, cf = max(cn, n_near.value), max(cf, n_far.value)
+            continue
+        check(code)
+        return near[:n_near.value].copy(), far[:n_far.value].copy()
 
 
 def krr_one_vs_all(ctx, cls, c):
