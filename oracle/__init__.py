@@ -19,6 +19,12 @@ Plain, slow and written to be checked against the paper by eye:
                   step 2), prediction and accuracy (Algorithm 1 steps 3-4,
                   Eq. (2)), relative residual.
 
-Parity unpinned: the ranks and memory of an HSS built with a given
-tolerance (the paper prints such figures only for its real data sets).
+* ``hmatrix``     H-matrix sampler (Section 3.2, H matrix representation):
+                  strong admissibility, block partition, ACA, H product.
+
+Parity unpinned: the ranks and memory of an HSS built with an
+intermediate tolerance on the synthetic data (the paper prints such
+figures only for its real data sets); the limits are pinned (h -> 0:
+rank 0, memory of the diagonal blocks; h -> infinity: rank 1, memory by
+formula).
 """

@@ -59,3 +59,42 @@ def test_error_is_order_eps():
         err = np.linalg.norm(hss.densify(H) - A) / np.linalg.norm(A)
         assert err < 10 * eps
         assert H.max_rank() < 600
+
+
+def _leaves(t):
+    return [v for v in range(len(t["begin"])) if t["left"][v] < 0]
+
+
+def test_rank_one_limit_h_to_infinity():
+    """K -> all ones as h -> infinity (Eq. (1)): every off-diagonal block has
+    rank exactly 1, so every node's rank is 1, each skeleton is the node's
+    first row (pivoting takes the first of equal columns), and the memory is
+    the leaves' D blocks plus one column per leaf, two entries per inner
+    non-root node and one B entry per inner node."""
+    _, t = _setup(400, 32)
+    n, lam = 400, 2.0
+    A = np.ones((n, n)) + lam * np.eye(n)
+    H = hss.build_explicit(A, t, 1e-8)
+    root = len(t["begin"]) - 1
+    ranks = H.ranks()
+    assert all(ranks[v] == 1 for v in range(root))
+    leaves = _leaves(t)
+    assert all(H.J[v].tolist() == [t["begin"][v]] for v in leaves)
+    inner = [v for v in range(len(t["begin"])) if t["left"][v] >= 0]
+    m = [int(t["end"][v] - t["begin"][v]) for v in leaves]
+    expect = sum(x * x for x in m) + sum(m) + 2 * (len(inner) - 1) + len(inner)
+    assert H.memory_entries() == expect
+    np.testing.assert_allclose(hss.densify(H), A, rtol=0, atol=1e-13)
+
+
+def test_rank_zero_limit_h_to_zero():
+    """K -> I as h -> 0: the off-diagonal blocks vanish, every rank is 0 and
+    the HSS is its leaves' diagonal blocks."""
+    _, t = _setup(300, 32)
+    n, lam = 300, 0.5
+    A = (1.0 + lam) * np.eye(n)
+    H = hss.build_explicit(A, t, 1e-8)
+    assert H.max_rank() == 0
+    m = [int(t["end"][v] - t["begin"][v]) for v in _leaves(t)]
+    assert H.memory_entries() == sum(x * x for x in m)
+    assert np.array_equal(hss.densify(H), A)
