@@ -38,7 +38,7 @@ WL = dict(n=65536, d=8, comps=16, sigma=0.7, seed=2, h=1.0, lam=4.0, leaf=128, e
 WORKLOAD = ("SUSY-shaped synthetic Gaussian mixture (16 components, d=8, standardized), n=65536 train / 4096 test; "
             "h=1, lambda=4, leaf 128, eps=1e-4 (GMRES to relative residual 5e-4 <= 10 eps), HSS eps_c=0.05, "
             "r0=64 adaptive, 10 right-hand sides")
-CPU_SAMPLE_N = 8192
+CPU_SAMPLE_N = 16384  # about 10-20 s of the oracle on 8-16 host cores
 
 
 def _peaks():
