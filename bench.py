@@ -886,6 +886,7 @@ def main():
                     help="skip the gradient workload and the million-point product")
     ap.add_argument("--image", action="store_true", help="with --sample-only: MNIST-shaped rows (d=784)")
     ap.add_argument("--batch-only", action="store_true", help="only run the MNIST-shaped and batched-problems workloads")
+    ap.add_argument("--image-only", action="store_true", help="only run the MNIST-shaped workload (for profilers)")
     ap.add_argument("--orderings-only", action="store_true", help="only run the comparison of the orderings")
     ap.add_argument("--gemm-only", type=int, metavar="NB",
                     help="only run NB batched 128 x 128 x 2032 Gram products on both GEMM paths (for profilers)")
@@ -900,6 +901,13 @@ def main():
     args = ap.parse_args()
     if args.sample_only:
         sample_only(*args.sample_only, image=args.image)
+    elif args.image_only:
+        import torch
+        import paper_1803_10274_gb300 as K
+        torch.cuda.set_device(0)
+        ctx = K.Context()
+        l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        print(json.dumps({"image_d784": bench_image(K, ctx, l2)}), flush=True)
     elif args.batch_only:
         import torch
         import paper_1803_10274_gb300 as K
